@@ -1,0 +1,244 @@
+/*
+ * ssi.h -- C ABI of libssi, a GB300 (sm_103a) implementation of the hot path of
+ * covariance-driven stochastic subspace identification with randomized SVD
+ * (RSVD-CoV-SSI, arXiv 2411.05510).
+ *
+ * Conventions shared by every entry point
+ *   - Every call returns an ssi_status; nothing throws across the ABI.
+ *     ssi_last_error() returns a thread-local message for the last failure.
+ *   - "device" pointers are CUDA device memory owned by the caller unless a
+ *     comment says otherwise; "host" pointers are ordinary host memory.
+ *   - Device work is enqueued on `stream` (a cudaStream_t passed as void*,
+ *     NULL = legacy default stream) and is asynchronous: outputs are valid once
+ *     the stream has been synchronised.  Entry points do not synchronise the
+ *     stream unless stated.
+ *   - Scratch memory comes from the context's workspace, which grows on demand
+ *     within the context's HBM budget (SSI_E_NOMEM beyond it).  One context must
+ *     not run two calls at the same time from different host threads, except
+ *     through the serving calls (ssi_submit / ssi_poll), which are thread safe.
+ *   - Matrices are row-major unless stated.
+ *   - Invalid shapes or parameters return SSI_E_INVALID before any work is
+ *     enqueued.  A CUDA error returns SSI_E_CUDA.  A device-side bounded wait
+ *     that ran out returns SSI_E_TIMEOUT (checked at the next synchronising
+ *     call); per-realisation non-convergence of eig(A) is reported per pole
+ *     (SSI_POLE_NOTCONV) and does not fail the call.
+ */
+#ifndef SSI_H
+#define SSI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SSI_OK = 0,
+  SSI_E_INVALID = 1,       /* bad argument or shape */
+  SSI_E_NOMEM = 2,         /* HBM budget or device allocation exhausted */
+  SSI_E_CUDA = 3,          /* CUDA runtime / driver error */
+  SSI_E_TIMEOUT = 4,       /* a bounded device wait ran out, or ssi_poll timed out */
+  SSI_E_NOTCONVERGED = 5,  /* an iteration hit its cap */
+  SSI_E_BUSY = 6,          /* serving: no free slot / budget right now */
+  SSI_E_NOTFOUND = 7       /* serving: unknown job id */
+} ssi_status;
+
+/* Arithmetic of the two dense contractions (lag GEMMs and Toeplitz sketch GEMMs). */
+typedef enum {
+  SSI_PREC_FP32 = 0,       /* plain FP32 FMA on the CUDA cores */
+  SSI_PREC_SPLIT_BF16 = 1  /* tcgen05 tensor cores, x = hi + lo in BF16, products
+                              hi*hi + hi*lo + lo*hi accumulated in FP32 */
+} ssi_precision;
+
+typedef struct ssi_ctx ssi_ctx;
+
+/* Context bound to CUDA device `device`.  hbm_budget_bytes caps the device memory
+ * the context may hold (0 = half of the free memory at creation). */
+ssi_status ssi_create(ssi_ctx** ctx, int device, size_t hbm_budget_bytes);
+/* Frees the context and everything it owns; waits for its outstanding work. */
+void ssi_destroy(ssi_ctx* ctx);
+/* Thread-local description of the last failure on this thread ("" if none). */
+const char* ssi_last_error(void);
+/* Library version, 100*major + minor. */
+int ssi_version(void);
+/* Device memory currently held by the context (bytes). */
+size_t ssi_memory_in_use(const ssi_ctx* ctx);
+
+/* ------------------------------------------------------------------------------
+ * Stage (a): output covariances, Sec. 2.1 ("R_1 .. R_{2jb-1} derived directly
+ * from the records").
+ *   R_k = 1/(N-k) * sum_{t=0}^{N-k-1} y_{t+k} y_t^T,  k = 1..max_lag.
+ * Y       device, float32, l x N, channel-major (row c holds channel c, samples
+ *         contiguous).
+ * R       device, float64, max_lag x l x l; R_k at offset (k-1)*l*l, entry
+ *         [a][b] = E[y_{t+k,a} y_{t,b}].
+ * prec    SSI_PREC_SPLIT_BF16 (tensor cores) or SSI_PREC_FP32 (CUDA cores).
+ *         Both accumulate FP32 partial sums over time chunks and add the chunks
+ *         in FP64.
+ * Limits: 1 <= l <= 1024, 1 <= max_lag < N, N < 2^31.
+ * ---------------------------------------------------------------------------- */
+ssi_status ssi_covariances(ssi_ctx* ctx, const float* Y, int l, int64_t N, int max_lag,
+                           ssi_precision prec, double* R, void* stream);
+
+/* ------------------------------------------------------------------------------
+ * Gaussian test matrix Omega of Sec. 2.2 (Eq. Y = A Omega, Algorithm 1, line 1).
+ * omega   device, float32, rows x cols row-major.  Entry (r, c) comes from the
+ *         Philox4x32-10 counter (r, c, 0, 0) with key (seed & 0xffffffff,
+ *         seed >> 32): outputs x0, x1 -> u = (x + 0.5)/2^32,
+ *         z = sqrt(-2 ln u0) cos(2 pi u1).
+ * ---------------------------------------------------------------------------- */
+ssi_status ssi_gaussian_omega(ssi_ctx* ctx, int rows, int cols, uint64_t seed, float* omega,
+                              void* stream);
+
+/* ------------------------------------------------------------------------------
+ * Stages (a)+(b): block-Toeplitz T_{1|i} (Eq. Toeplitz: block (a,b) = R_{i+a-b})
+ * and its randomized SVD (Sec. 2.2, Algorithm 1, with oversampling and power
+ * iterations re-orthonormalised by QR after every product).
+ * T is never formed: its tiles are read from the covariances by lag index.
+ *   Omega = gaussian(L, k+oversample, seed);  Q = qr(T Omega);
+ *   repeat q times: Q = qr(T qr(T^T Q));      P = Q^T T;
+ *   (U~, S) = svd(P);                          U = Q U~[:, :k].
+ * R       device, float64, (2i-1) x l x l as produced by ssi_covariances (more
+ *         lags may be present; only R_1..R_{2i-1} are read).
+ * U       device, float32, L x k row-major, L = l*i (left singular vectors).
+ * S       device, float32, k singular values, descending.
+ * Limits: i >= 2, 1 <= k, k + oversample <= min(L, 512), l <= 1024.
+ * ---------------------------------------------------------------------------- */
+ssi_status ssi_toeplitz_rsvd(ssi_ctx* ctx, const double* R, int l, int i, int k, int oversample,
+                             int q, uint64_t seed, ssi_precision prec, float* U, float* S,
+                             void* stream);
+
+/* ------------------------------------------------------------------------------
+ * Stage (c): realisation for every (lag, order) of a stabilization diagram,
+ * Sec. 2.1 (O = U S^{1/2}; C = first l rows; A = O^to+ O^bo; A = Psi M Psi^-1;
+ * lambda = ln(mu)/dt; f = |lambda|/(2 pi); xi = -Re(lambda)/|lambda|; Phi = C Psi).
+ * The S^{1/2} column scaling is a similarity transform of A and is not applied:
+ * eig((U^to)+ U^bo) equals eig((O^to)+ O^bo) and C Psi = U[:l,:n] Psi~.
+ * One pole per complex-conjugate eigenvalue pair (Im mu > 0); real eigenvalues
+ * give no pole.
+ *
+ * lags     host, n_lags block counts i_t (each >= 2).
+ * U        host array of n_lags device pointers; U[t] is (l*lags[t]) x k float32.
+ * orders   host, n_orders even model orders, ascending, 2 <= order <= k.
+ * poles    device, ssi_pole_slots(n_orders, orders) * n_lags records.  Slot
+ *          (t, m, j) = t*slots_per_lag + sum_{m'<m} orders[m']/2 + j; the poles of
+ *          one realisation come first, ascending in frequency; unused slots have
+ *          flags == 0.
+ * phi      device, float32 complex (re, im interleaved), l values per slot,
+ *          unit 2-norm, largest-modulus component real and positive.
+ * ---------------------------------------------------------------------------- */
+typedef struct {
+  float f_hz;      /* natural frequency [Hz] */
+  float xi;        /* damping ratio */
+  float mu_re;     /* discrete eigenvalue */
+  float mu_im;
+  float mpc;       /* modal phase collinearity in [0, 1] */
+  float mpd;       /* mean phase deviation in [0, 1] (degrees / 90) */
+  int32_t lag;     /* block count i of the Toeplitz matrix */
+  int32_t order;   /* model order n */
+  uint32_t flags;  /* SSI_POLE_* bits */
+  int32_t index;   /* pole index within its realisation */
+} ssi_pole;
+
+#define SSI_POLE_HC_XI    1u   /* fails xi <= xi_max (or xi <= 0, |mu| >= 1) */
+#define SSI_POLE_HC_MPC   2u   /* fails MPC > mpc_min */
+#define SSI_POLE_HC_MPD   4u   /* fails MPD < mpd_max */
+#define SSI_POLE_HC       8u   /* passes every hard criterion */
+#define SSI_POLE_ORDER   16u   /* stable along model orders */
+#define SSI_POLE_LAG     32u   /* stable along time lags */
+#define SSI_POLE_VALID   64u   /* slot holds a pole */
+#define SSI_POLE_NOTCONV 128u  /* eig(A) of this realisation hit its iteration cap */
+
+/* Number of pole slots of one lag: sum over orders of order/2. */
+int64_t ssi_pole_slots(int n_orders, const int* orders);
+
+ssi_status ssi_realize_batch(ssi_ctx* ctx, int n_lags, const int* lags, const float* const* U,
+                             int l, int k, const int* orders, int n_orders, double dt,
+                             ssi_pole* poles, float* phi, void* stream);
+
+/* ------------------------------------------------------------------------------
+ * Stage (d): hard criteria and the soft criteria of Eq. (stabcriteria3D).
+ * HC: xi <= xi_max (and xi > 0, |mu| < 1), MPC > mpc_min, MPD < mpd_max.
+ * SC: a pole passing HC at (lag t, order m) gets SSI_POLE_ORDER if some
+ * HC-passing pole at (t, m-1) has |df|/max(f) <= a_f, |dxi|/max(xi) <= a_xi and
+ * 1 - MAC <= a_mac; SSI_POLE_LAG likewise with (t-1, m) when use_lag_axis.
+ * Indices m-1 and t-1 are the previous entries of the order and lag grids.
+ * poles / phi  device, as written by ssi_realize_batch (flags updated in place).
+ * ---------------------------------------------------------------------------- */
+typedef struct {
+  double xi_max, mpc_min, mpd_max;   /* e.g. 0.10, 0.6, 0.5 */
+  double a_f, a_xi, a_mac;           /* e.g. 0.01, 0.03, 0.02 */
+  int32_t use_lag_axis;              /* 1: 3D diagram, 0: orders only */
+  int32_t reserved;
+} ssi_stab_params;
+
+ssi_status ssi_stabilize(ssi_ctx* ctx, int n_lags, int n_orders, const int* orders, int l,
+                         ssi_pole* poles, const float* phi, const ssi_stab_params* params,
+                         void* stream);
+
+/* ------------------------------------------------------------------------------
+ * One complete solve (stages a-d) of one record: covariances up to 2*max(lags)-1,
+ * then per lag the Toeplitz RSVD, then the realisations of every (lag, order)
+ * and the stability checks.  All work is enqueued on `stream`; nothing is
+ * synchronised.  Y may be device memory (y_on_host = 0) or host memory
+ * (y_on_host = 1, pinned for overlap), in which case it is copied in on `stream`.
+ * ---------------------------------------------------------------------------- */
+typedef struct {
+  const float* Y;          /* l x N, channel-major */
+  int32_t y_on_host;
+  int32_t l;
+  int64_t N;
+  double fs;               /* sampling frequency [Hz] */
+  int32_t n_lags;
+  const int32_t* lags;     /* host, ascending */
+  int32_t n_orders;
+  const int32_t* orders;   /* host, ascending, even */
+  int32_t k, oversample, q;
+  int32_t prec;            /* ssi_precision */
+  uint64_t seed;
+  ssi_stab_params stab;
+} ssi_job_desc;
+
+/* Output sizes of a job: total pole slots and the matching phi length (floats). */
+ssi_status ssi_job_sizes(const ssi_job_desc* job, int64_t* n_slots, int64_t* phi_floats);
+
+/* poles/phi: device buffers of ssi_job_sizes() size.  S_out (optional, device):
+ * n_lags x k singular values. */
+ssi_status ssi_solve(ssi_ctx* ctx, const ssi_job_desc* job, ssi_pole* poles, float* phi,
+                     float* S_out, void* stream);
+
+/* ------------------------------------------------------------------------------
+ * Serving: continuous batching of solves.  ssi_submit copies the descriptor
+ * (and the host record, when y_on_host) and returns at once; a scheduler thread
+ * admits queued jobs when a slot and enough of the HBM budget are free, runs
+ * each admitted job on its own stream so their kernels overlap, and keeps the
+ * job's covariances, sketches and results resident until ssi_release.
+ * ssi_submit returns SSI_E_BUSY when the queue is full.
+ * ssi_poll waits up to timeout_ms (0 = just test, <0 = forever) for job_id and
+ * then returns host pointers owned by the context (valid until ssi_release):
+ * the pole records and phi values, and the job's latency in microseconds from
+ * submission to completion.
+ * ---------------------------------------------------------------------------- */
+ssi_status ssi_serve_config(ssi_ctx* ctx, int max_slots, int max_queue);
+ssi_status ssi_submit(ssi_ctx* ctx, const ssi_job_desc* job, uint64_t* job_id);
+ssi_status ssi_poll(ssi_ctx* ctx, uint64_t job_id, int timeout_ms, const ssi_pole** poles,
+                    const float** phi, int64_t* n_slots, double* latency_us);
+ssi_status ssi_release(ssi_ctx* ctx, uint64_t job_id);
+
+/* ------------------------------------------------------------------------------
+ * Parameter rules of Sec. 3 (host functions, no device work).
+ * Eq. (empirical_formula): kbar(T) = max(30 - 0.00156 T, 25) percent; k = ceil(kbar T / 100).
+ * Eq. (jb), Eq. (jb_3D): jb = ceil(10 fs/(2 f0)), jb_min = ceil(9 fs/(2 f0)),
+ * jb_max = ceil(beta jb_min); int() is read as the ceiling.
+ * Eq. (tlag): tau = (2 jb - 1)/fs.
+ * ---------------------------------------------------------------------------- */
+ssi_status ssi_rank_rule(int64_t T_size, double* kbar_percent, int64_t* k);
+ssi_status ssi_lag_rule(double fs, double f0, double beta, int* jb, int* jb_min, int* jb_max);
+double ssi_time_lag(int jb, double fs);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SSI_H */

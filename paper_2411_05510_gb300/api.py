@@ -1,0 +1,204 @@
+"""Python entry points with the C ABI's names, on PyTorch device tensors.
+
+Argument marshalling only: tensors are checked for device, dtype and layout,
+their pointers and the current CUDA stream are passed to libssi, and outputs
+are allocated with torch.  No step of the method runs here.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Sequence
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import SSI_PREC_FP32, SSI_PREC_SPLIT_BF16, SsiJobDesc, SsiStabParams, check, lib
+
+__all__ = [
+    "Context", "PREC", "ssi_covariances", "ssi_gaussian_omega", "ssi_toeplitz_rsvd",
+    "ssi_realize_batch", "ssi_stabilize", "ssi_solve", "ssi_pole_slots", "poles_to_numpy",
+    "stab_params", "job_desc", "ssi_rank_rule", "ssi_lag_rule", "ssi_time_lag",
+]
+
+PREC = {"fp32": SSI_PREC_FP32, "split_bf16": SSI_PREC_SPLIT_BF16}
+
+
+def _prec(p) -> int:
+    return PREC[p] if isinstance(p, str) else int(p)
+
+
+def _stream(device=None) -> ctypes.c_void_p:
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _need(t: torch.Tensor, dtype, name: str):
+    if not (t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+        raise ValueError(f"{name}: need a contiguous CUDA {dtype} tensor, got "
+                         f"{t.dtype} on {t.device} contiguous={t.is_contiguous()}")
+
+
+class Context:
+    """An ssi_ctx bound to one CUDA device with an HBM budget (0 = half the free memory)."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0):
+        self.device = device
+        self.ptr = ctypes.c_void_p()
+        check(lib.ssi_create(ctypes.byref(self.ptr), device, hbm_budget_bytes), "ssi_create")
+
+    def close(self):
+        if self.ptr:
+            lib.ssi_destroy(self.ptr)
+            self.ptr = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def memory_in_use(self) -> int:
+        return int(lib.ssi_memory_in_use(self.ptr))
+
+
+def ssi_covariances(ctx: Context, Y: torch.Tensor, max_lag: int, prec="split_bf16",
+                    out: torch.Tensor | None = None) -> torch.Tensor:
+    """R_k, k = 1..max_lag (float64, max_lag x l x l) from Y (l x N float32, channel-major)."""
+    _need(Y, torch.float32, "Y")
+    l, N = Y.shape
+    R = out if out is not None else torch.empty((max_lag, l, l), dtype=torch.float64, device=Y.device)
+    _need(R, torch.float64, "R")
+    check(lib.ssi_covariances(ctx.ptr, ctypes.c_void_p(Y.data_ptr()), l, N, max_lag, _prec(prec),
+                              ctypes.c_void_p(R.data_ptr()), _stream(Y.device)), "ssi_covariances")
+    return R
+
+
+def ssi_gaussian_omega(ctx: Context, rows: int, cols: int, seed: int, device="cuda") -> torch.Tensor:
+    out = torch.empty((rows, cols), dtype=torch.float32, device=device)
+    check(lib.ssi_gaussian_omega(ctx.ptr, rows, cols, seed, ctypes.c_void_p(out.data_ptr()),
+                                 _stream(out.device)), "ssi_gaussian_omega")
+    return out
+
+
+def ssi_toeplitz_rsvd(ctx: Context, R: torch.Tensor, l: int, i: int, k: int, oversample: int = 0,
+                      q: int = 0, seed: int = 0, prec="split_bf16"):
+    """(U, S): U (l*i x k float32), S (k float32) of the block-Toeplitz T_{1|i} built from R."""
+    _need(R, torch.float64, "R")
+    U = torch.empty((l * i, k), dtype=torch.float32, device=R.device)
+    S = torch.empty((k,), dtype=torch.float32, device=R.device)
+    check(lib.ssi_toeplitz_rsvd(ctx.ptr, ctypes.c_void_p(R.data_ptr()), l, i, k, oversample, q, seed,
+                                _prec(prec), ctypes.c_void_p(U.data_ptr()),
+                                ctypes.c_void_p(S.data_ptr()), _stream(R.device)),
+          "ssi_toeplitz_rsvd")
+    return U, S
+
+
+def _int_array(xs: Sequence[int]):
+    arr = (ctypes.c_int * len(xs))(*[int(x) for x in xs])
+    return arr
+
+
+def ssi_pole_slots(orders: Sequence[int]) -> int:
+    return int(lib.ssi_pole_slots(len(orders), _int_array(orders)))
+
+
+def ssi_realize_batch(ctx: Context, lags: Sequence[int], Us: Sequence[torch.Tensor], l: int, k: int,
+                      orders: Sequence[int], dt: float):
+    """Pole records (uint8 tensor, n_lags*slots x 40 bytes) and phi (float32, slots x l x 2)."""
+    slots = ssi_pole_slots(orders) * len(lags)
+    dev = Us[0].device
+    poles = torch.zeros((slots, _lib.POLE_BYTES), dtype=torch.uint8, device=dev)
+    phi = torch.zeros((slots, l, 2), dtype=torch.float32, device=dev)
+    for U in Us:
+        _need(U, torch.float32, "U")
+    uptrs = (ctypes.c_void_p * len(Us))(*[U.data_ptr() for U in Us])
+    check(lib.ssi_realize_batch(ctx.ptr, len(lags), _int_array(lags), uptrs, l, k, _int_array(orders),
+                                len(orders), dt, ctypes.c_void_p(poles.data_ptr()),
+                                ctypes.c_void_p(phi.data_ptr()), _stream(dev)), "ssi_realize_batch")
+    return poles, phi
+
+
+def stab_params(xi_max=0.10, mpc_min=0.6, mpd_max=0.5, a_f=0.01, a_xi=0.03, a_mac=0.02,
+                use_lag_axis=True) -> SsiStabParams:
+    return SsiStabParams(xi_max, mpc_min, mpd_max, a_f, a_xi, a_mac, 1 if use_lag_axis else 0, 0)
+
+
+def ssi_stabilize(ctx: Context, n_lags: int, orders: Sequence[int], l: int, poles: torch.Tensor,
+                  phi: torch.Tensor, params: SsiStabParams | None = None):
+    params = params or stab_params()
+    check(lib.ssi_stabilize(ctx.ptr, n_lags, len(orders), _int_array(orders), l,
+                            ctypes.c_void_p(poles.data_ptr()), ctypes.c_void_p(phi.data_ptr()),
+                            ctypes.byref(params), _stream(poles.device)), "ssi_stabilize")
+    return poles
+
+
+def job_desc(Y, fs: float, lags: Sequence[int], orders: Sequence[int], k: int, oversample: int = 0,
+             q: int = 0, prec="split_bf16", seed: int = 0, stab: SsiStabParams | None = None):
+    """An ssi_job_desc for a device tensor or a (pinned) host tensor / numpy array Y (l x N)."""
+    keep = []
+    if isinstance(Y, torch.Tensor):
+        if Y.dtype != torch.float32 or not Y.is_contiguous():
+            raise ValueError("Y must be contiguous float32")
+        ptr, on_host = Y.data_ptr(), 0 if Y.is_cuda else 1
+    else:
+        Y = np.ascontiguousarray(Y, dtype=np.float32)
+        ptr, on_host = Y.ctypes.data, 1
+    keep.append(Y)
+    l, N = Y.shape
+    lag_arr = (ctypes.c_int32 * len(lags))(*lags)
+    ord_arr = (ctypes.c_int32 * len(orders))(*orders)
+    keep += [lag_arr, ord_arr]
+    d = SsiJobDesc(ptr, on_host, l, N, fs, len(lags), lag_arr, len(orders), ord_arr, k, oversample,
+                   q, _prec(prec), seed, stab or stab_params(use_lag_axis=len(lags) > 1))
+    d._keep = keep
+    return d
+
+
+def ssi_job_sizes(desc: SsiJobDesc):
+    n, p = ctypes.c_int64(), ctypes.c_int64()
+    check(lib.ssi_job_sizes(ctypes.byref(desc), ctypes.byref(n), ctypes.byref(p)), "ssi_job_sizes")
+    return n.value, p.value
+
+
+def ssi_solve(ctx: Context, desc: SsiJobDesc, device="cuda", with_s: bool = True):
+    """Full solve; returns (poles uint8 tensor, phi float32 tensor, S float32 tensor or None)."""
+    n_slots, phi_floats = ssi_job_sizes(desc)
+    poles = torch.zeros((n_slots, _lib.POLE_BYTES), dtype=torch.uint8, device=device)
+    phi = torch.zeros((phi_floats,), dtype=torch.float32, device=device)
+    S = torch.zeros((desc.n_lags, desc.k), dtype=torch.float32, device=device) if with_s else None
+    check(lib.ssi_solve(ctx.ptr, ctypes.byref(desc), ctypes.c_void_p(poles.data_ptr()),
+                        ctypes.c_void_p(phi.data_ptr()),
+                        ctypes.c_void_p(S.data_ptr() if S is not None else 0),
+                        _stream(torch.device(device))), "ssi_solve")
+    return poles, phi, S
+
+
+_POLE_DTYPE = np.dtype([("f_hz", "<f4"), ("xi", "<f4"), ("mu_re", "<f4"), ("mu_im", "<f4"),
+                        ("mpc", "<f4"), ("mpd", "<f4"), ("lag", "<i4"), ("order", "<i4"),
+                        ("flags", "<u4"), ("index", "<i4")])
+
+
+def poles_to_numpy(poles) -> np.ndarray:
+    """Pole records (uint8 tensor or bytes) -> numpy structured array."""
+    if isinstance(poles, torch.Tensor):
+        raw = poles.detach().cpu().contiguous().numpy().tobytes()
+    else:
+        raw = bytes(poles)
+    return np.frombuffer(raw, dtype=_POLE_DTYPE).copy()
+
+
+def ssi_rank_rule(T_size: int):
+    kbar, k = ctypes.c_double(), ctypes.c_int64()
+    check(lib.ssi_rank_rule(T_size, ctypes.byref(kbar), ctypes.byref(k)), "ssi_rank_rule")
+    return kbar.value, k.value
+
+
+def ssi_lag_rule(fs: float, f0: float, beta: float = 1.5):
+    a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    check(lib.ssi_lag_rule(fs, f0, beta, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+          "ssi_lag_rule")
+    return a.value, b.value, c.value
+
+
+def ssi_time_lag(jb: int, fs: float) -> float:
+    return float(lib.ssi_time_lag(jb, fs))

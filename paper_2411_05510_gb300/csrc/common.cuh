@@ -1,0 +1,144 @@
+// Internal declarations shared by the libssi translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cstdint>
+#include <cstddef>
+#include <cstdio>
+#include <string>
+#include <mutex>
+#include <vector>
+
+#include "../../include/ssi.h"
+
+namespace ssi {
+
+// ---------------------------------------------------------------------------
+// error handling
+// ---------------------------------------------------------------------------
+void set_error(const char* fmt, ...);
+ssi_status cuda_fail(cudaError_t e, const char* what, const char* file, int line);
+
+#define SSI_CUDA(call)                                                        \
+  do {                                                                        \
+    cudaError_t e_ = (call);                                                  \
+    if (e_ != cudaSuccess) return ::ssi::cuda_fail(e_, #call, __FILE__, __LINE__); \
+  } while (0)
+
+#define SSI_CHECK(cond, ...)                                                  \
+  do {                                                                        \
+    if (!(cond)) { ::ssi::set_error(__VA_ARGS__); return SSI_E_INVALID; }     \
+  } while (0)
+
+#define SSI_TRY(call)                                                         \
+  do {                                                                        \
+    ssi_status s_ = (call);                                                   \
+    if (s_ != SSI_OK) return s_;                                              \
+  } while (0)
+
+// device status word bits (written by kernels, read by the host)
+enum : int {
+  DEV_TIMEOUT = 1,        // a bounded wait ran out
+  DEV_NOTCONVERGED = 2,   // an iteration hit its cap
+  DEV_BADSHAPE = 4,       // a kernel met a shape it cannot handle
+};
+
+// ---------------------------------------------------------------------------
+// workspace: a bump allocator over one device buffer owned by the context
+// ---------------------------------------------------------------------------
+struct Workspace {
+  char* base = nullptr;
+  size_t cap = 0;
+  size_t off = 0;
+  void reset() { off = 0; }
+  template <typename T>
+  T* take(size_t count) {
+    size_t bytes = (count * sizeof(T) + 255) & ~size_t(255);
+    if (off + bytes > cap) return nullptr;
+    T* p = reinterpret_cast<T*>(base + off);
+    off += bytes;
+    return p;
+  }
+};
+
+// byte-size accumulator that mirrors Workspace::take for planning
+struct WsPlan {
+  size_t bytes = 0;
+  template <typename T>
+  void add(size_t count) { bytes += (count * sizeof(T) + 255) & ~size_t(255); }
+};
+
+struct Serving;  // runtime.cpp
+
+}  // namespace ssi
+
+struct ssi_ctx {
+  int device = 0;
+  int num_sms = 0;
+  size_t budget = 0;
+  size_t in_use = 0;
+  std::mutex mem_mu;
+  ssi::Workspace ws;        // workspace of the direct (non-serving) calls
+  int* dev_status = nullptr;  // device status word of the direct calls
+  ssi::Serving* serving = nullptr;
+};
+
+namespace ssi {
+
+// memory accounting against the context budget
+ssi_status ctx_alloc(ssi_ctx* ctx, void** p, size_t bytes);
+void ctx_free(ssi_ctx* ctx, void* p, size_t bytes);
+// grow `ws` to at least `bytes` (synchronises `stream` before freeing the old buffer)
+ssi_status ws_reserve(ssi_ctx* ctx, Workspace& ws, size_t bytes, cudaStream_t stream);
+// read and clear a device status word (synchronises `stream`)
+ssi_status check_dev_status(int* dev_status, cudaStream_t stream);
+
+// ---------------------------------------------------------------------------
+// stage entry points with explicit workspace (used by the ABI wrappers, by
+// ssi_solve and by the serving scheduler)
+// ---------------------------------------------------------------------------
+struct CovPlan {
+  int l, l_pad, max_lag, n_nt, nb;    // channel padding, N tiles of the tensor-core kernel
+  int64_t N, n_rows;
+  int rows_per_split, n_split;
+  size_t ws_bytes;
+};
+CovPlan cov_plan(int l, int64_t N, int max_lag, ssi_precision prec, int num_sms);
+ssi_status covariances_ws(ssi_ctx* ctx, Workspace& ws, const CovPlan& plan, const float* Y,
+                          ssi_precision prec, double* R, int* dev_status, cudaStream_t stream);
+
+struct RsvdPlan {
+  int l, l_pad, i, k, K, Kp, q, L, L_pad;
+  size_t ws_bytes;
+};
+RsvdPlan rsvd_plan(int l, int i, int k, int oversample, int q, int num_sms);
+ssi_status toeplitz_rsvd_ws(ssi_ctx* ctx, Workspace& ws, const RsvdPlan& plan, const double* R,
+                            uint64_t seed, ssi_precision prec, float* U, float* S,
+                            int* dev_status, cudaStream_t stream);
+
+struct RealizePlan {
+  int n_lags, l, k, n_orders, max_order;
+  int64_t slots_per_lag;
+  size_t ws_bytes;
+};
+RealizePlan realize_plan(int n_lags, const int* lags, int l, int k, const int* orders,
+                         int n_orders);
+ssi_status realize_ws(ssi_ctx* ctx, Workspace& ws, const RealizePlan& plan, const int* lags,
+                      const float* const* U, const int* orders, double dt, ssi_pole* poles,
+                      float* phi, int* dev_status, cudaStream_t stream);
+
+ssi_status stabilize_ws(ssi_ctx* ctx, Workspace& ws, int n_lags, int n_orders, const int* orders,
+                        int l, ssi_pole* poles, const float* phi, const ssi_stab_params* p,
+                        cudaStream_t stream);
+size_t stabilize_ws_bytes(int n_lags, int n_orders);
+
+ssi_status gaussian_omega_launch(int rows, int cols, int ld, uint64_t seed, float* out,
+                                 __nv_bfloat16* hi, __nv_bfloat16* lo, cudaStream_t stream);
+
+// shared launch helpers
+int device_sms(int device);
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+inline int64_t round_up(int64_t a, int64_t b) { return ceil_div(a, b) * b; }
+
+}  // namespace ssi
