@@ -118,9 +118,10 @@ ssi_status ssi_toeplitz_rsvd(ssi_ctx* ctx, const double* R, int l, int i, int k,
  * One pole per complex-conjugate eigenvalue pair (Im mu > 0); real eigenvalues
  * give no pole.
  *
- * lags     host, n_lags block counts i_t (each >= 2).
+ * lags     host, n_lags block counts i_t (each >= 2), n_lags <= 64.
  * U        host array of n_lags device pointers; U[t] is (l*lags[t]) x k float32.
- * orders   host, n_orders even model orders, ascending, 2 <= order <= k.
+ * orders   host, n_orders even model orders, ascending, 2 <= order <= min(k, 224),
+ *          n_orders <= 512; k <= 232.
  * poles    device, ssi_pole_slots(n_orders, orders) * n_lags records.  Slot
  *          (t, m, j) = t*slots_per_lag + sum_{m'<m} orders[m']/2 + j; the poles of
  *          one realisation come first, ascending in frequency; unused slots have
@@ -207,6 +208,11 @@ ssi_status ssi_job_sizes(const ssi_job_desc* job, int64_t* n_slots, int64_t* phi
  * n_lags x k singular values. */
 ssi_status ssi_solve(ssi_ctx* ctx, const ssi_job_desc* job, ssi_pole* poles, float* phi,
                      float* S_out, void* stream);
+
+/* Synchronise `stream` and report device-side status raised by earlier asynchronous
+ * calls of this context on it (SSI_E_TIMEOUT for a bounded wait that ran out,
+ * SSI_E_NOTCONVERGED for an iteration cap).  Clears the status. */
+ssi_status ssi_sync_status(ssi_ctx* ctx, void* stream);
 
 /* ------------------------------------------------------------------------------
  * Serving: continuous batching of solves.  ssi_submit copies the descriptor

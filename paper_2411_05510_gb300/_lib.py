@@ -70,6 +70,7 @@ PROTOTYPES = {
     "ssi_job_sizes": (_c.c_int, [_c.POINTER(SsiJobDesc), _c.POINTER(_c.c_int64),
                                  _c.POINTER(_c.c_int64)]),
     "ssi_solve": (_c.c_int, [_P, _c.POINTER(SsiJobDesc), _P, _P, _P, _P]),
+    "ssi_sync_status": (_c.c_int, [_P, _P]),
     "ssi_serve_config": (_c.c_int, [_P, _c.c_int, _c.c_int]),
     "ssi_submit": (_c.c_int, [_P, _c.POINTER(SsiJobDesc), _c.POINTER(_c.c_uint64)]),
     "ssi_poll": (_c.c_int, [_P, _c.c_uint64, _c.c_int, _c.POINTER(_P), _c.POINTER(_P),

@@ -18,7 +18,8 @@ from ._lib import SSI_PREC_FP32, SSI_PREC_SPLIT_BF16, SsiJobDesc, SsiStabParams,
 __all__ = [
     "Context", "PREC", "ssi_covariances", "ssi_gaussian_omega", "ssi_toeplitz_rsvd",
     "ssi_realize_batch", "ssi_stabilize", "ssi_solve", "ssi_pole_slots", "poles_to_numpy",
-    "stab_params", "job_desc", "ssi_rank_rule", "ssi_lag_rule", "ssi_time_lag",
+    "stab_params", "job_desc", "ssi_rank_rule", "ssi_lag_rule", "ssi_time_lag", "check_sync",
+    "ssi_job_sizes",
 ]
 
 PREC = {"fp32": SSI_PREC_FP32, "split_bf16": SSI_PREC_SPLIT_BF16}
@@ -152,6 +153,11 @@ def job_desc(Y, fs: float, lags: Sequence[int], orders: Sequence[int], k: int, o
                    q, _prec(prec), seed, stab or stab_params(use_lag_axis=len(lags) > 1))
     d._keep = keep
     return d
+
+
+def check_sync(ctx: Context, device=None) -> None:
+    """Synchronise the current stream and raise if a kernel reported a device-side status."""
+    check(lib.ssi_sync_status(ctx.ptr, _stream(device)), "ssi_sync_status")
 
 
 def ssi_job_sizes(desc: SsiJobDesc):

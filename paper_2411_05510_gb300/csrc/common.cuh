@@ -69,7 +69,8 @@ struct WsPlan {
   void add(size_t count) { bytes += (count * sizeof(T) + 255) & ~size_t(255); }
 };
 
-struct Serving;  // runtime.cpp
+struct Serving;     // serving.cpp
+struct JobBuffers;  // pipeline.h
 
 }  // namespace ssi
 
@@ -82,6 +83,7 @@ struct ssi_ctx {
   ssi::Workspace ws;        // workspace of the direct (non-serving) calls
   int* dev_status = nullptr;  // device status word of the direct calls
   ssi::Serving* serving = nullptr;
+  ssi::JobBuffers* solve = nullptr;  // buffers of ssi_solve
 };
 
 namespace ssi {

@@ -1,0 +1,178 @@
+// One complete solve (stages a-d) of one record, enqueued on one stream, and the
+// planning of its device memory.  Used directly by ssi_solve and by the serving
+// scheduler (serving.cpp).
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+#include "pipeline.h"
+
+namespace ssi {
+
+ssi_status validate_job(const ssi_job_desc* j) {
+  SSI_CHECK(j, "job: null descriptor");
+  SSI_CHECK(j->Y, "job: null record");
+  SSI_CHECK(j->l >= 1 && j->l <= 1024, "job: l=%d out of range", j->l);
+  SSI_CHECK(j->fs > 0, "job: fs must be positive");
+  SSI_CHECK(j->n_lags >= 1 && j->n_lags <= 64 && j->lags, "job: 1 <= n_lags <= 64");
+  SSI_CHECK(j->n_orders >= 1 && j->n_orders <= 512 && j->orders, "job: 1 <= n_orders <= 512");
+  SSI_CHECK(j->k >= 2 && j->oversample >= 0 && j->q >= 0, "job: bad k / oversample / q");
+  SSI_CHECK(j->k <= 224 && j->k + j->oversample <= 512, "job: need k <= 224, k + oversample <= 512");
+  SSI_CHECK(j->prec == SSI_PREC_FP32 || j->prec == SSI_PREC_SPLIT_BF16, "job: bad precision");
+  for (int t = 0; t < j->n_lags; ++t) {
+    SSI_CHECK(j->lags[t] >= 2, "job: lag %d < 2", j->lags[t]);
+    SSI_CHECK(t == 0 || j->lags[t] > j->lags[t - 1], "job: lags must ascend");
+    SSI_CHECK((int64_t)j->l * j->lags[t] >= j->k + j->oversample, "job: l*i < k + oversample");
+  }
+  const int max_lag = 2 * j->lags[j->n_lags - 1] - 1;
+  SSI_CHECK(j->N > max_lag, "job: N=%lld must exceed 2*max(lags)-1=%d", (long long)j->N, max_lag);
+  SSI_CHECK(j->N < (1LL << 31) - 1024, "job: N too large");
+  for (int m = 0; m < j->n_orders; ++m) {
+    SSI_CHECK(j->orders[m] >= 2 && j->orders[m] % 2 == 0 && j->orders[m] <= j->k,
+              "job: order %d must be even and in [2, k]", j->orders[m]);
+    SSI_CHECK(j->orders[m] <= 224, "job: order %d > 224 not supported", j->orders[m]);
+    SSI_CHECK(m == 0 || j->orders[m] > j->orders[m - 1], "job: orders must ascend");
+  }
+  return SSI_OK;
+}
+
+JobPlan plan_job(const ssi_job_desc* j, int num_sms) {
+  JobPlan p{};
+  p.max_lag = 2 * j->lags[j->n_lags - 1] - 1;
+  p.cov = cov_plan(j->l, j->N, p.max_lag, (ssi_precision)j->prec, num_sms);
+  size_t ws = p.cov.ws_bytes;
+  for (int t = 0; t < j->n_lags; ++t) {
+    p.rs.push_back(rsvd_plan(j->l, j->lags[t], j->k, j->oversample, j->q, num_sms));
+    ws = std::max(ws, p.rs.back().ws_bytes);
+  }
+  std::vector<int> lags(j->lags, j->lags + j->n_lags), orders(j->orders, j->orders + j->n_orders);
+  p.rz = realize_plan(j->n_lags, lags.data(), j->l, j->k, orders.data(), j->n_orders);
+  ws = std::max(ws, p.rz.ws_bytes);
+  p.ws_bytes = ws;
+  WsPlan b;
+  b.add<double>((size_t)p.max_lag * j->l * j->l);             // R
+  for (int t = 0; t < j->n_lags; ++t) b.add<float>((size_t)j->l * j->lags[t] * j->k);  // U_t
+  b.add<float>((size_t)j->n_lags * j->k);                      // S
+  if (j->y_on_host) b.add<float>((size_t)j->l * j->N);        // device copy of Y
+  b.add<int>(64);                                              // device status word
+  p.buf_bytes = b.bytes;
+  p.n_slots = p.rz.slots_per_lag * j->n_lags;
+  p.phi_floats = p.n_slots * 2 * j->l;
+  return p;
+}
+
+ssi_status run_job(ssi_ctx* ctx, const ssi_job_desc* j, const JobPlan& p, JobBuffers& B,
+                   ssi_pole* poles, float* phi, float* S_out, cudaStream_t stream) {
+  // carve the job buffers
+  Workspace carve;
+  carve.base = static_cast<char*>(B.buf);
+  carve.cap = B.buf_cap;
+  double* R = carve.take<double>((size_t)p.max_lag * j->l * j->l);
+  std::vector<float*> U(j->n_lags);
+  for (int t = 0; t < j->n_lags; ++t) U[t] = carve.take<float>((size_t)j->l * j->lags[t] * j->k);
+  float* S = carve.take<float>((size_t)j->n_lags * j->k);
+  float* Ydev = j->y_on_host ? carve.take<float>((size_t)j->l * j->N) : nullptr;
+  int* status = carve.take<int>(64);
+  if (!R || !S || !status || (j->y_on_host && !Ydev)) {
+    set_error("solve: job buffers too small");
+    return SSI_E_NOMEM;
+  }
+  B.status = status;
+  const float* Y = j->Y;
+  if (j->y_on_host) {
+    SSI_CUDA(cudaMemcpyAsync(Ydev, j->Y, sizeof(float) * (size_t)j->l * j->N, cudaMemcpyHostToDevice,
+                             stream));
+    Y = Ydev;
+  }
+  if (!B.status_cleared) {
+    SSI_CUDA(cudaMemsetAsync(status, 0, 64 * sizeof(int), stream));
+    B.status_cleared = true;
+  }
+  SSI_TRY(covariances_ws(ctx, B.ws, p.cov, Y, (ssi_precision)j->prec, R, status, stream));
+  for (int t = 0; t < j->n_lags; ++t)
+    SSI_TRY(toeplitz_rsvd_ws(ctx, B.ws, p.rs[t], R, j->seed, (ssi_precision)j->prec, U[t],
+                             S + (size_t)t * j->k, status, stream));
+  std::vector<int> lags(j->lags, j->lags + j->n_lags), orders(j->orders, j->orders + j->n_orders);
+  std::vector<const float*> Uc(U.begin(), U.end());
+  SSI_TRY(realize_ws(ctx, B.ws, p.rz, lags.data(), Uc.data(), orders.data(), 1.0 / j->fs, poles, phi,
+                     status, stream));
+  SSI_TRY(stabilize_ws(ctx, B.ws, j->n_lags, j->n_orders, orders.data(), j->l, poles, phi, &j->stab,
+                       stream));
+  if (S_out)
+    SSI_CUDA(cudaMemcpyAsync(S_out, S, sizeof(float) * (size_t)j->n_lags * j->k,
+                             cudaMemcpyDeviceToDevice, stream));
+  return SSI_OK;
+}
+
+ssi_status buffers_reserve(ssi_ctx* ctx, JobBuffers& B, const JobPlan& p, cudaStream_t stream) {
+  if (B.buf_cap < p.buf_bytes) {
+    if (B.buf) {
+      SSI_CUDA(cudaStreamSynchronize(stream));
+      ctx_free(ctx, B.buf, B.buf_cap);
+      B.buf = nullptr;
+      B.buf_cap = 0;
+    }
+    size_t want = (p.buf_bytes + (1u << 20) - 1) & ~size_t((1u << 20) - 1);
+    SSI_TRY(ctx_alloc(ctx, &B.buf, want));
+    B.buf_cap = want;
+    B.status_cleared = false;
+  }
+  return ws_reserve(ctx, B.ws, p.ws_bytes, stream);
+}
+
+void buffers_free(ssi_ctx* ctx, JobBuffers& B) {
+  if (B.buf) ctx_free(ctx, B.buf, B.buf_cap);
+  if (B.ws.base) ctx_free(ctx, B.ws.base, B.ws.cap);
+  B = JobBuffers{};
+}
+
+JobBuffers& ctx_solve_buffers(ssi_ctx* ctx) {
+  if (!ctx->solve) ctx->solve = new JobBuffers();
+  return *ctx->solve;
+}
+
+void solve_buffers_destroy(ssi_ctx* ctx) {
+  if (ctx->solve) {
+    buffers_free(ctx, *ctx->solve);
+    delete ctx->solve;
+    ctx->solve = nullptr;
+  }
+}
+
+}  // namespace ssi
+
+using namespace ssi;
+
+extern "C" ssi_status ssi_job_sizes(const ssi_job_desc* job, int64_t* n_slots, int64_t* phi_floats) {
+  SSI_TRY(validate_job(job));
+  int64_t s = 0;
+  for (int m = 0; m < job->n_orders; ++m) s += job->orders[m] / 2;
+  s *= job->n_lags;
+  if (n_slots) *n_slots = s;
+  if (phi_floats) *phi_floats = s * 2 * job->l;
+  return SSI_OK;
+}
+
+extern "C" ssi_status ssi_solve(ssi_ctx* ctx, const ssi_job_desc* job, ssi_pole* poles, float* phi,
+                                float* S_out, void* stream) {
+  SSI_CHECK(ctx && poles && phi, "ssi_solve: null pointer");
+  SSI_TRY(validate_job(job));
+  SSI_CUDA(cudaSetDevice(ctx->device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  JobPlan p = plan_job(job, ctx->num_sms);
+  JobBuffers& B = ctx_solve_buffers(ctx);
+  SSI_TRY(buffers_reserve(ctx, B, p, s));
+  return run_job(ctx, job, p, B, poles, phi, S_out, s);
+}
+
+extern "C" ssi_status ssi_sync_status(ssi_ctx* ctx, void* stream) {
+  SSI_CHECK(ctx, "ssi_sync_status: null context");
+  SSI_CUDA(cudaSetDevice(ctx->device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  SSI_CUDA(cudaStreamSynchronize(s));
+  ssi_status st = check_dev_status(ctx->dev_status, s);
+  if (st != SSI_OK) return st;
+  JobBuffers& B = ctx_solve_buffers(ctx);
+  if (B.status) return check_dev_status(B.status, s);
+  return SSI_OK;
+}

@@ -1,0 +1,36 @@
+// Job planning and execution shared by ssi_solve and the serving scheduler.
+#pragma once
+
+#include <vector>
+
+#include "common.cuh"
+
+namespace ssi {
+
+struct JobPlan {
+  int max_lag;
+  CovPlan cov;
+  std::vector<RsvdPlan> rs;
+  RealizePlan rz;
+  size_t ws_bytes;     // scratch (shared by the stages, which run in sequence)
+  size_t buf_bytes;    // R, U per lag, S, device Y copy, status word
+  int64_t n_slots, phi_floats;
+};
+
+struct JobBuffers {
+  void* buf = nullptr;
+  size_t buf_cap = 0;
+  Workspace ws;
+  int* status = nullptr;
+  bool status_cleared = false;
+};
+
+ssi_status validate_job(const ssi_job_desc* j);
+JobPlan plan_job(const ssi_job_desc* j, int num_sms);
+ssi_status buffers_reserve(ssi_ctx* ctx, JobBuffers& B, const JobPlan& p, cudaStream_t stream);
+void buffers_free(ssi_ctx* ctx, JobBuffers& B);
+ssi_status run_job(ssi_ctx* ctx, const ssi_job_desc* j, const JobPlan& p, JobBuffers& B,
+                   ssi_pole* poles, float* phi, float* S_out, cudaStream_t stream);
+JobBuffers& ctx_solve_buffers(ssi_ctx* ctx);
+
+}  // namespace ssi

@@ -134,6 +134,7 @@ bool make_tmap_bf16_2d(CUtensorMap* tm, const void* base, uint64_t rows, uint64_
 }
 
 void serving_destroy(ssi_ctx* ctx);  // serving.cpp
+void solve_buffers_destroy(ssi_ctx* ctx);  // pipeline.cpp
 
 }  // namespace ssi
 
@@ -183,6 +184,7 @@ void ssi_destroy(ssi_ctx* ctx) {
   cudaSetDevice(ctx->device);
   serving_destroy(ctx);
   cudaDeviceSynchronize();
+  solve_buffers_destroy(ctx);
   if (ctx->ws.base) ctx_free(ctx, ctx->ws.base, ctx->ws.cap);
   ctx_free(ctx, ctx->dev_status, 256);
   delete ctx;

@@ -1,0 +1,189 @@
+"""Parity of stages (b)-(d) and of a complete solve against the FP64 oracle.
+
+Tolerances (fixed by the gates of the method's parity set): leading singular values
+<= 1e-4 relative; pole frequency <= 1e-4 relative, damping <= 2e-3 absolute,
+MAC >= 0.999.  Omega: the GPU and the oracle evaluate the same Philox4x32-10 counters;
+the Box-Muller transform runs in FP32 on the GPU and FP64 in the oracle, so entries
+agree to ~1e-6 absolute (bound 2e-5).
+"""
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import ssi_synth as S
+from parity import compare_parity_set, gpu_cells
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import paper_2411_05510_gb300 as P
+    return P
+
+
+@pytest.fixture(scope="module")
+def ctx(P):
+    c = P.Context(0)
+    yield c
+    c.close()
+
+
+def test_omega_matches_oracle_philox(P, ctx):
+    for rows, cols, seed in [(300, 37, 0), (1000, 220, 11), (5, 5, (7 << 32) | 9)]:
+        g = P.ssi_gaussian_omega(ctx, rows, cols, seed).cpu().numpy()
+        o = O.gaussian_omega(rows, cols, seed)
+        assert np.abs(g - o).max() < 2e-5
+
+
+def _rsvd_case(P, ctx, R, l, i, k, p, q, seed, prec):
+    Rd = torch.from_numpy(np.ascontiguousarray(R)).cuda()
+    U, Sv = P.ssi_toeplitz_rsvd(ctx, Rd, l, i, k, p, q, seed, prec)
+    torch.cuda.synchronize()
+    return U.cpu().numpy().astype(np.float64), Sv.cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("prec", ["split_bf16", "fp32"])
+def test_rsvd_full_width_equals_full_svd_on_chain(P, ctx, prec):
+    """4-channel chain, i = 20: k = L = 80 with no sketching reduces RSVD to the SVD."""
+    Y, *_ = S.record(S.workload("chain4_tiny"))
+    R = O.covariances(Y, 39)
+    T = O.block_toeplitz(R, 20)
+    _, s_ref = O.full_svd(T)
+    U, s = _rsvd_case(P, ctx, R, 4, 20, 80, 0, 0, 3, prec)
+    assert np.allclose(s[:8], s_ref[:8], rtol=1e-4)
+    assert np.abs(U[:, :8].T @ U[:, :8] - np.eye(8)).max() < 1e-4
+
+
+@pytest.mark.parametrize("prec", ["split_bf16", "fp32"])
+@pytest.mark.parametrize("l,i,k,p,q", [(24, 10, 40, 10, 2), (70, 7, 60, 20, 1), (9, 30, 30, 6, 3)])
+def test_rsvd_matches_oracle_rsvd(P, ctx, prec, l, i, k, p, q):
+    """Same Omega (Philox) on both sides: leading singular values agree to 1e-4."""
+    rec = S.bridge_record(l, 8, 1.0, 12.0, 50.0, 40000, 0.05, seed=l + i)
+    R = O.covariances(rec.Y, 2 * i - 1)
+    T = O.block_toeplitz(R, i)
+    _, s_ref = O.rsvd(T, k, p, q, seed=5)
+    U, s = _rsvd_case(P, ctx, R, l, i, k, p, q, 5, prec)
+    lead = 16
+    assert np.allclose(s[:lead], s_ref[:lead], rtol=1e-4), np.abs(s[:lead] / s_ref[:lead] - 1).max()
+    G = U.T @ U
+    assert np.abs(G - np.eye(k)).max() < 2e-4
+
+
+def _realize(P, ctx, Us, lags, l, k, orders, dt):
+    Ud = [torch.from_numpy(np.ascontiguousarray(U, dtype=np.float32)).cuda() for U in Us]
+    poles, phi = P.ssi_realize_batch(ctx, lags, Ud, l, k, orders, dt)
+    torch.cuda.synchronize()
+    return P.poles_to_numpy(poles), phi.cpu().numpy()
+
+
+def test_realize_recovers_exact_modes_from_model_covariances(P, ctx):
+    model = S.chain_model(S.workload("chain4_tiny"))
+    T = O.block_toeplitz(S.model_covariances(model, 39)[1:], 20)
+    U, s = O.full_svd(T)
+    rec, phi = _realize(P, ctx, [U[:, :8]], [20], 4, 8, [2, 4, 6, 8], model.dt)
+    cells = gpu_cells(rec, phi, [20], [2, 4, 6, 8], 4)
+    c8 = cells[0][3]
+    assert len(c8["f"]) == 4
+    assert np.allclose(c8["f"], model.f_true, rtol=2e-5)
+    assert np.allclose(c8["xi"], model.xi_true, atol=2e-4)
+    for j in range(4):
+        assert O.mac(c8["Phi"][:, j], model.phi_true[:, j]) > 0.9999
+
+
+def test_realize_matches_oracle_on_noisy_chain(P, ctx):
+    w = S.workload("chain4_tiny")
+    Y, f_true, *_ = S.record(w)
+    T = O.block_toeplitz(O.covariances(Y, 39), 20)
+    U, s = O.full_svd(T)
+    orders = list(range(2, 41, 2))
+    rec, phi = _realize(P, ctx, [U[:, :40]], [20], 4, 40, orders, 0.01)
+    gpu = gpu_cells(rec, phi, [20], orders, 4)
+    ora = [[]]
+    for n in orders:
+        mu, f, xi, Phi, _ = O.realize(U, s, 4, 20, n, 0.01)
+        cell = dict(mu=mu, f=f, xi=xi, Phi=Phi)
+        mpcs, mpds, fail = O.hard_criteria(mu, f, xi, Phi)
+        cell["flags"] = np.where(fail == 0, 8, 0)
+        ora[0].append(cell)
+    # GPU cells carry HC bits only after ssi_stabilize: apply the same HC to their values
+    for row in gpu:
+        for c in row:
+            ok = (c["xi"] > 0) & (c["xi"] <= 0.1) & (c["mpc"] > 0.6) & (c["mpd"] < 0.5) & (np.abs(c["mu"]) < 1)
+            c["flags"] = np.where(ok, 8, 0)
+    n, worst = compare_parity_set(gpu, ora, f_true, orders, 4, min_matches=40)
+
+
+def test_stabilize_flags_match_oracle_on_shared_poles(P, ctx):
+    """Identical pole sets on both sides (oracle poles uploaded): flags must agree."""
+    w = S.workload("chain4_tiny")
+    Y, *_ = S.record(w)
+    T = O.block_toeplitz(O.covariances(Y, 39), 20)
+    U, s = O.full_svd(T)
+    orders = list(range(2, 21, 2))
+    lags = [20, 21]
+    diag = []
+    for _ in lags:
+        row = []
+        for n in orders:
+            mu, f, xi, Phi, _ = O.realize(U, s, 4, 20, n, 0.01)
+            row.append(dict(mu=mu, f=f, xi=xi, Phi=np.stack([O.normalize_shape(Phi[:, j]) for j in
+                                                            range(Phi.shape[1])], 1) if len(f) else Phi))
+        diag.append(row)
+    # perturb the second lag slightly so the lag axis has non-trivial decisions
+    for c in diag[1]:
+        c["f"] = c["f"] * 1.004
+        c["xi"] = c["xi"] * 1.02
+    l = 4
+    slots = sum(n // 2 for n in orders)
+    rec = np.zeros(slots * len(lags), dtype=P.api._POLE_DTYPE)
+    phi = np.zeros((slots * len(lags), l, 2), np.float32)
+    off = 0
+    for t, row in enumerate(diag):
+        for m, n in enumerate(orders):
+            c = row[m]
+            for j in range(len(c["f"])):
+                e = rec[off + j]
+                e["f_hz"], e["xi"] = c["f"][j], c["xi"][j]
+                e["mu_re"], e["mu_im"] = c["mu"][j].real, c["mu"][j].imag
+                e["mpc"], e["mpd"] = O.mpc(c["Phi"][:, j]), O.mpd(c["Phi"][:, j])
+                e["lag"], e["order"], e["flags"], e["index"] = lags[t], n, 64, j
+                phi[off + j, :, 0] = c["Phi"][:, j].real
+                phi[off + j, :, 1] = c["Phi"][:, j].imag
+                rec[off + j] = e
+            off += n // 2
+    pd = torch.from_numpy(np.frombuffer(rec.tobytes(), np.uint8).reshape(len(rec), -1).copy()).cuda()
+    fd = torch.from_numpy(phi).cuda()
+    P.ssi_stabilize(ctx, len(lags), orders, l, pd, fd, P.stab_params())
+    torch.cuda.synchronize()
+    g = P.poles_to_numpy(pd)
+    O.stability(diag)
+    off = 0
+    n_checked = 0
+    for t, row in enumerate(diag):
+        for m, n in enumerate(orders):
+            for j in range(len(row[m]["f"])):
+                assert int(g["flags"][off + j]) & 63 == int(row[m]["flags"][j]) & 63, (t, n, j)
+                n_checked += 1
+            off += n // 2
+    assert n_checked > 50
+
+
+@pytest.mark.parametrize("prec", ["split_bf16", "fp32"])
+def test_full_solve_chain_matches_oracle(P, ctx, prec):
+    """Complete solve of the 4-channel chain record (i = 20, full width k = 80, orders 2..40)."""
+    w = S.workload("chain4_tiny")
+    Y, f_true, *_ = S.record(w, np.float32)
+    orders = w["orders"]
+    desc = P.job_desc(torch.from_numpy(Y).cuda(), w["fs"], w["lags"], orders, k=40, oversample=40,
+                      q=0, prec=prec, seed=1)
+    poles, phi, Sg = P.ssi_solve(ctx, desc)
+    P.check_sync(ctx)
+    rec = P.poles_to_numpy(poles)
+    gpu = gpu_cells(rec, phi.cpu().numpy(), w["lags"], orders, 4)
+    ora, sv = O.ssi_solve(Y.astype(np.float64), w["fs"], w["lags"], orders, full_svd_=True)
+    assert np.allclose(Sg.cpu().numpy()[0, :8], sv[0][:8], rtol=1e-4)
+    compare_parity_set(gpu, ora, f_true, orders, 4, min_matches=40)
