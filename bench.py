@@ -1,0 +1,440 @@
+#!/usr/bin/env python
+"""Benchmark of the RSVD-CoV-SSI hot path: SSI solves/s on the 186-channel bridge record.
+
+Workload (default "bridge186_i60"): l = 186 channels (62 triaxial stations), 20 modes
+(1-20 Hz), fs = 100 Hz, N = 360000 samples (1 h), 5 % sensor noise; one solve =
+covariances R_1..R_119, Toeplitz RSVD at i = 60 (T 11160 x 11160, k = 200 + 20, q = 2),
+realisations of orders 2..200 step 2, hard and soft stability criteria.
+
+Lines printed (one JSON line on rank 0):
+  value      solves/s with the record resident in HBM (CUDA events around K solves)
+  e2e        the same through ssi_submit / ssi_poll with the record in pinned host memory
+             (host->device copy and the read-back of poles and mode shapes inside)
+  roofline   dominant kernel (the tcgen05 lag GEMM): algorithmic FP32-equivalent flops
+             2 l^2 N K_lag per launch / its measured duration, against the measured BF16
+             tensor peak divided by 3 (three BF16 products per split product)
+  fp32_path  the same pipeline with plain FP32 CUDA-core GEMMs (the plain FP32 GPU path)
+  cpu_baseline  the FP64 oracle on the host cores, stage by stage on a bounded sample
+
+--impl reference times the FP64 oracle (the CPU reference of the method) on the same
+workload, each step one sampled estimate of a full solve.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import ssi_synth as S  # noqa: E402
+
+PROFILES = os.path.join(ROOT, "profiles")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="bridge186_i60")
+    ap.add_argument("--prec", default="split_bf16", choices=["split_bf16", "fp32"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp32", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- helpers
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("covariance.cu", "blackwell.cuh", "common.cuh"):
+        with open(os.path.join(ROOT, "paper_2411_05510_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def stored_traffic(workload):
+    """DRAM bytes per launch of the lag GEMM from the committed ncu summary, if current."""
+    path = os.path.join(PROFILES, f"lag_gemm_{workload}_traffic.json")
+    if not os.path.exists(path):
+        return None, None
+    with open(path) as fh:
+        d = json.load(fh)
+    if d.get("source_hash") != kernel_source_hash():
+        return None, "stale"
+    return d.get("dram_bytes_per_launch"), d.get("note")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.th.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def pct(xs, q):
+    xs = sorted(xs)
+    if not xs:
+        return None
+    k = min(len(xs) - 1, max(0, int(round(q / 100.0 * (len(xs) - 1)))))
+    return xs[k]
+
+
+# ----------------------------------------------------------------------------- oracle sample
+def oracle_sample_estimate(Y, w, log=None):
+    """Seconds of one FP64-oracle solve of workload w, estimated stage by stage from a
+    bounded sample: covariances on 1/50 of the record (x50); one Toeplitz product and
+    one Householder QR (x(2+2q) each); one Jacobi sweep of P^T (x10 sweeps); full
+    realisations of four orders scaled by sum(n^2); stability on those orders."""
+    import oracle as O
+    t = {}
+    N = Y.shape[1]
+    Ns = max(2 * max(w["lags"]) + 10, N // 50)
+    t0 = time.perf_counter()
+    R = O.covariances(Y[:, :Ns], 2 * max(w["lags"]) - 1)
+    t["covariances"] = (time.perf_counter() - t0) * (N / Ns)
+    i = w["lags"][0]
+    t0 = time.perf_counter()
+    T = O.block_toeplitz(R, i)
+    t["toeplitz"] = time.perf_counter() - t0
+    K = w["k"] + w["oversample"]
+    om = O.gaussian_omega(T.shape[1], K, 1)
+    t0 = time.perf_counter()
+    Yk = T @ om
+    t["products"] = (time.perf_counter() - t0) * (2 + 2 * w["q"])
+    t0 = time.perf_counter()
+    Q, _ = O.householder_qr(Yk)
+    t["qr"] = (time.perf_counter() - t0) * (2 + 2 * w["q"])
+    P = Q.T @ T
+    t0 = time.perf_counter()
+    O.jacobi_svd(P.T, max_sweeps=1)
+    t["small_svd"] = (time.perf_counter() - t0) * 10
+    U = Q[:, :w["k"]]
+    Sv = np.linalg.norm(P[:w["k"]], axis=1)
+    orders = w["orders"]
+    sample = [orders[len(orders) // 5], orders[len(orders) // 2], orders[(4 * len(orders)) // 5],
+              orders[-1]]
+    l = Y.shape[0]
+    t0 = time.perf_counter()
+    cells = []
+    for n in sample:
+        mu, f, xi, Phi, _ = O.realize(U, Sv, l, i, n, 1.0 / w["fs"])
+        cells.append(dict(mu=mu, f=f, xi=xi, Phi=Phi))
+    ts = time.perf_counter() - t0
+    t["realisation"] = ts * sum(n * n for n in orders) / sum(n * n for n in sample)
+    t0 = time.perf_counter()
+    O.stability([cells])
+    t["stability"] = (time.perf_counter() - t0) * len(orders) / len(sample)
+    return sum(t.values()), t
+
+
+# ----------------------------------------------------------------------------- reference arm
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    w = S.workload(args.workload)
+    w["name"] = args.workload
+    Y, *_ = S.record(w, np.float32)
+    Y = Y.astype(np.float64)
+    est = []
+    for s in range(args.warmup + args.steps):
+        tot, _ = oracle_sample_estimate(Y, w)
+        if s >= args.warmup:
+            est.append(tot)
+    mean = statistics.mean(est)
+    cores = os.cpu_count()
+    value = 1.0 / mean
+    sample = ("per step: covariances on 1/50 of the record, one Toeplitz product, one QR, one "
+              "Jacobi sweep, four realisations; scaled to one full solve")
+    line = {"impl": "reference", "metric": "SSI solves/s", "value": value, "unit": "solves/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": mean * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_of(w, "fp64 oracle"),
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def config_of(w, prec):
+    cfg = {"workload": w.get("name", None) or "", "channels": w.get("l", w.get("n_dof")),
+           "N": w["N"], "fs": w["fs"], "lags": w["lags"], "k": w["k"],
+           "oversample": w["oversample"], "q": w["q"],
+           "orders": f"{w['orders'][0]}..{w['orders'][-1]} step 2", "prec": prec,
+           "l2": "inputs larger than L2 (record 268 MB fp32 > 129 MB)"}
+    return cfg
+
+
+# ----------------------------------------------------------------------------- our arm
+def main():
+    args = parse()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        if world > 1:
+            import torch.distributed as dist
+            dist.init_process_group("gloo")
+        run_reference(args, world, rank)
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    import torch
+    import torch.distributed as dist
+    import paper_2411_05510_gb300 as P
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    w = S.workload(args.workload)
+    w["name"] = args.workload
+    Y, f_true, *_ = S.record(w, np.float32)
+    l, N = Y.shape
+    Yd = torch.from_numpy(Y).to(dev)
+    ctx = P.Context(local)
+    desc = P.job_desc(Yd, w["fs"], w["lags"], w["orders"], k=w["k"], oversample=w["oversample"],
+                      q=w["q"], prec=args.prec, seed=12345)
+    n_slots, phi_floats = P.ssi_job_sizes(desc)
+    poles = torch.zeros((n_slots, P._lib.POLE_BYTES), dtype=torch.uint8, device=dev)
+    phi = torch.zeros((phi_floats,), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def solve_once(d):
+        P._lib.check(P._lib.lib.ssi_solve(ctx.ptr, P._lib.ctypes.byref(d),
+                                          P._lib.ctypes.c_void_p(poles.data_ptr()),
+                                          P._lib.ctypes.c_void_p(phi.data_ptr()), None,
+                                          P._lib.ctypes.c_void_p(stream.cuda_stream)), "ssi_solve")
+
+    for _ in range(args.warmup):
+        solve_once(desc)
+    P.check_sync(ctx, dev)
+    ctx.profile_read()   # drop warm-up records
+    ctx.profile(True)
+
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(local)
+    with (clocks if not args.no_clocks else _Null()):
+        ev[0].record(stream)
+        for s in range(args.steps):
+            solve_once(desc)
+            ev[s + 1].record(stream)
+        torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    P.check_sync(ctx, dev)
+    ctx.profile(False)
+    stage_ms, stage_cnt, launches = ctx.profile_read()
+    step_ms = [ev[s].elapsed_time(ev[s + 1]) for s in range(args.steps)]
+    total_ms = ev[0].elapsed_time(ev[args.steps])
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * args.steps / (total_ms / 1e3)
+
+    # sanity: the record's modes are found
+    rec = P.poles_to_numpy(poles)
+    top = rec[-(w["orders"][-1] // 2):]
+    hc = top[(top["flags"] & 8) != 0]
+    found = int(sum(np.min(np.abs(hc["f_hz"] - f0) / f0) < 1e-2 for f0 in f_true)) if len(hc) else 0
+
+    out = {}
+    if rank == 0:
+        peaks, peak_src = load_peaks()
+        K_lag = 2 * max(w["lags"]) - 1
+        flops = 2.0 * l * l * N * K_lag
+        n_launch = max(1, stage_cnt["lag_gemm"])
+        gemm_ms = stage_ms["lag_gemm"] / n_launch
+        achieved = flops / (gemm_ms / 1e3) / 1e12
+        if args.prec == "split_bf16":
+            peak = peaks["bf16_tflops_sustained"] / 3.0
+            peak_note = f"bf16_tflops_sustained/3 ({peak_src}): three BF16 MMAs per split product"
+        else:
+            peak = 72.0
+            peak_note = "FP32 FMA rate 72 TFLOP/s measured by a probe on this GB300"
+        traffic, tnote = stored_traffic(args.workload)
+        out = {
+            "metric": "SSI solves/s", "value": value, "unit": "solves/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16" if args.prec == "split_bf16" else "f32", "data": "synthetic",
+            "config": config_of(w, args.prec),
+            "latency_ms": {"p50": pct(step_ms, 50), "p99": pct(step_ms, 99), "kind": "device"},
+            "roofline": {"bound": "tensor" if args.prec == "split_bf16" else "alu",
+                         "kernel": "k_lag_gemm_tc" if args.prec == "split_bf16" else "k_lag_gemm_fp32",
+                         "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": traffic, "peak_note": peak_note,
+                         "flops_per_launch": flops, "ms_per_launch": gemm_ms,
+                         "traffic_note": tnote},
+            "stages_ms_per_step": {k: v / args.steps for k, v in stage_ms.items()},
+            "gpu_launches": launches,
+            "modes_found": f"{found}/{len(f_true)}",
+        }
+        if not args.no_clocks:
+            out["clocks"] = clocks.summary()
+
+    # e2e through the serving API, record in pinned host memory
+    if not args.no_e2e:
+        Yh = torch.from_numpy(Y).pin_memory()
+        P._lib.check(P._lib.lib.ssi_serve_config(ctx.ptr, 2, 64), "ssi_serve_config")
+        desc_h = P.job_desc(Yh, w["fs"], w["lags"], w["orders"], k=w["k"],
+                            oversample=w["oversample"], q=w["q"], prec=args.prec, seed=12345)
+        lat = []
+        n_e2e = max(3, min(args.steps, 10))
+        for s in range(2 + n_e2e):
+            jid = P._lib.ctypes.c_uint64()
+            P._lib.check(P._lib.lib.ssi_submit(ctx.ptr, P._lib.ctypes.byref(desc_h),
+                                               P._lib.ctypes.byref(jid)), "ssi_submit")
+            pp, ff = P._lib.ctypes.c_void_p(), P._lib.ctypes.c_void_p()
+            ns, lu = P._lib.ctypes.c_int64(), P._lib.ctypes.c_double()
+            t0 = time.perf_counter()
+            P._lib.check(P._lib.lib.ssi_poll(ctx.ptr, jid.value, -1, P._lib.ctypes.byref(pp),
+                                             P._lib.ctypes.byref(ff), P._lib.ctypes.byref(ns),
+                                             P._lib.ctypes.byref(lu)), "ssi_poll")
+            P._lib.lib.ssi_release(ctx.ptr, jid.value)
+            if s >= 2:
+                lat.append(lu.value / 1e3)
+        if world > 1:
+            t = torch.tensor([sum(lat)], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            tot = float(t.item())
+        else:
+            tot = sum(lat)
+        if rank == 0:
+            out["e2e"] = {"value": world * len(lat) / (tot / 1e3), "unit": "solves/s",
+                          "h2d_bytes_per_step": int(l * N * 4),
+                          "d2h_bytes_per_step": int(n_slots * P._lib.POLE_BYTES + phi_floats * 4),
+                          "latency_ms": {"p50": pct(lat, 50), "p99": pct(lat, 99)},
+                          "api": "ssi_submit/ssi_poll, record in pinned host memory"}
+
+    # the plain FP32 path of the same pipeline on the same GPU
+    if not args.no_fp32 and args.prec == "split_bf16":
+        d32 = P.job_desc(Yd, w["fs"], w["lags"], w["orders"], k=w["k"], oversample=w["oversample"],
+                         q=w["q"], prec="fp32", seed=12345)
+        solve_once(d32)
+        torch.cuda.synchronize(dev)
+        ts = []
+        for s in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            solve_once(d32)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ts.append(e0.elapsed_time(e1))
+        if rank == 0:
+            out["fp32_path"] = {"value": 1e3 / statistics.mean(ts), "unit": "solves/s",
+                                "latency_ms": {"p50": pct(ts, 50), "p99": pct(ts, 99)},
+                                "split_bf16_speedup": value / world / (1e3 / statistics.mean(ts))}
+
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        tot, parts = oracle_sample_estimate(Y.astype(np.float64), w)
+        out["cpu_baseline"] = {"value": 1.0 / tot, "unit": "solves/s", "cores": os.cpu_count(),
+                               "kind": "oracle",
+                               "sample": "covariances on 1/50 of the record, one Toeplitz product, "
+                                         "one QR, one Jacobi sweep, four realisations, scaled to "
+                                         "one full solve",
+                               "stage_s": {k: round(v, 3) for k, v in parts.items()}}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+class _Null:
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        return False
+
+
+if __name__ == "__main__":
+    main()

@@ -65,6 +65,16 @@ int ssi_version(void);
 /* Device memory currently held by the context (bytes). */
 size_t ssi_memory_in_use(const ssi_ctx* ctx);
 
+/* Instrumentation.  ssi_profile(ctx, 1) makes the direct (non-serving) calls of the
+ * context record a CUDA event pair around each stage on the call's stream; this adds
+ * no synchronisation.  ssi_profile_read synchronises on the recorded events and
+ * returns, per stage id, the summed device time in ms and the number of scopes since
+ * the previous read, plus the number of kernels the context launched (also reset).
+ * Stage ids: 0 split/transpose, 1 lag GEMM, 2 lag reduction, 3 Toeplitz sketch GEMMs,
+ * 4 QR, 5 small SVD, 6 Gram/factorisation, 7 eig, 8 stability, 9 other; n >= 10. */
+ssi_status ssi_profile(ssi_ctx* ctx, int enable);
+ssi_status ssi_profile_read(ssi_ctx* ctx, double* ms, int64_t* counts, int n, int64_t* launches);
+
 /* ------------------------------------------------------------------------------
  * Stage (a): output covariances, Sec. 2.1 ("R_1 .. R_{2jb-1} derived directly
  * from the records").

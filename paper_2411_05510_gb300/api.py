@@ -61,6 +61,22 @@ class Context:
     def memory_in_use(self) -> int:
         return int(lib.ssi_memory_in_use(self.ptr))
 
+    STAGES = ["split", "lag_gemm", "lag_reduce", "sketch_gemm", "qr", "small_svd", "gram_factor",
+              "eig", "stability", "other"]
+
+    def profile(self, enable: bool = True) -> None:
+        check(lib.ssi_profile(self.ptr, 1 if enable else 0), "ssi_profile")
+
+    def profile_read(self):
+        """({stage: ms}, {stage: scopes}, kernel launches) since the previous read."""
+        n = len(self.STAGES)
+        ms = (ctypes.c_double * n)()
+        cnt = (ctypes.c_int64 * n)()
+        launches = ctypes.c_int64()
+        check(lib.ssi_profile_read(self.ptr, ms, cnt, n, ctypes.byref(launches)), "ssi_profile_read")
+        return ({s: ms[i] for i, s in enumerate(self.STAGES)},
+                {s: int(cnt[i]) for i, s in enumerate(self.STAGES)}, int(launches.value))
+
 
 def ssi_covariances(ctx: Context, Y: torch.Tensor, max_lag: int, prec="split_bf16",
                     out: torch.Tensor | None = None) -> torch.Tensor:

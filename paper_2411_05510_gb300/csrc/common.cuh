@@ -6,8 +6,10 @@
 #include <cstdint>
 #include <cstddef>
 #include <cstdio>
+#include <atomic>
 #include <string>
 #include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "../../include/ssi.h"
@@ -74,6 +76,14 @@ struct JobBuffers;  // pipeline.h
 
 }  // namespace ssi
 
+namespace ssi {
+// stage ids of the optional per-stage timers (ssi_profile / ssi_profile_read)
+enum Stage : int {
+  ST_SPLIT = 0, ST_LAG_GEMM = 1, ST_LAG_REDUCE = 2, ST_SKETCH_GEMM = 3, ST_QR = 4, ST_SMALL_SVD = 5,
+  ST_GRAM = 6, ST_EIG = 7, ST_STAB = 8, ST_OTHER = 9, ST_COUNT = 10
+};
+}  // namespace ssi
+
 struct ssi_ctx {
   int device = 0;
   int num_sms = 0;
@@ -84,6 +94,10 @@ struct ssi_ctx {
   int* dev_status = nullptr;  // device status word of the direct calls
   ssi::Serving* serving = nullptr;
   ssi::JobBuffers* solve = nullptr;  // buffers of ssi_solve
+  std::atomic<long long> launches{0};  // kernels launched through this context
+  bool prof_on = false;               // per-stage CUDA-event timers
+  std::mutex prof_mu;
+  std::vector<std::tuple<int, cudaEvent_t, cudaEvent_t>> prof_recs;
 };
 
 namespace ssi {
@@ -137,6 +151,33 @@ size_t stabilize_ws_bytes(int n_lags, int n_orders);
 
 ssi_status gaussian_omega_launch(int rows, int cols, int ld, uint64_t seed, float* out,
                                  __nv_bfloat16* hi, __nv_bfloat16* lo, cudaStream_t stream);
+
+// per-stage timing scope: records a CUDA event pair around the enclosed launches when the
+// context's timers are on (host-side bookkeeping only; no synchronisation)
+struct ProfScope {
+  ssi_ctx* ctx;
+  int stage;
+  cudaStream_t s;
+  cudaEvent_t e0 = nullptr;
+  ProfScope(ssi_ctx* c, int st, cudaStream_t strm) : ctx(c), stage(st), s(strm) {
+    if (ctx && ctx->prof_on) {
+      cudaEventCreate(&e0);
+      cudaEventRecord(e0, s);
+    }
+  }
+  ~ProfScope() {
+    if (e0) {
+      cudaEvent_t e1;
+      cudaEventCreate(&e1);
+      cudaEventRecord(e1, s);
+      std::lock_guard<std::mutex> g(ctx->prof_mu);
+      ctx->prof_recs.emplace_back(stage, e0, e1);
+    }
+  }
+};
+inline void count_launches(ssi_ctx* ctx, int n) {
+  if (ctx) ctx->launches += n;
+}
 
 // shared launch helpers
 int device_sms(int device);

@@ -398,9 +398,12 @@ ssi_status covariances_ws(ssi_ctx* ctx, Workspace& ws, const CovPlan& c, const f
     __nv_bfloat16* lo = ws.take<__nv_bfloat16>((size_t)c.n_rows * c.l_pad);
     float* partial = ws.take<float>((size_t)c.n_split * split_stride);
     if (!hi || !lo || !partial) { set_error("covariances: workspace too small"); return SSI_E_NOMEM; }
-    dim3 blk(32, 8), grd((unsigned)ceil_div(c.n_rows, 32), c.l_pad / 32);
-    k_split_transpose<<<grd, blk, 0, stream>>>(Y, c.l, (int)c.N, (int)c.n_rows, c.l_pad, hi, lo);
-    SSI_CUDA(cudaGetLastError());
+    {
+      ProfScope ps(ctx, ST_SPLIT, stream);
+      dim3 blk(32, 8), grd((unsigned)ceil_div(c.n_rows, 32), c.l_pad / 32);
+      k_split_transpose<<<grd, blk, 0, stream>>>(Y, c.l, (int)c.N, (int)c.n_rows, c.l_pad, hi, lo);
+      SSI_CUDA(cudaGetLastError());
+    }
     CUtensorMap thi, tlo;
     if (!make_tmap_bf16_2d(&thi, hi, (uint64_t)c.n_rows, c.l_pad, c.l_pad, 64, BT,
                            CU_TENSOR_MAP_SWIZZLE_128B) ||
@@ -419,29 +422,43 @@ ssi_status covariances_ws(ssi_ctx* ctx, Workspace& ws, const CovPlan& c, const f
     p.split_stride = split_stride;
     const int n_units = p.n_mp * p.n_nt * p.n_split;
     const int grid = std::min(n_units, ctx->num_sms);
-    ssi_status st;
-    switch (c.nb) {
-      case 1: st = launch_tc<1>(thi, tlo, p, partial, dev_status, grid, stream); break;
-      case 2: st = launch_tc<2>(thi, tlo, p, partial, dev_status, grid, stream); break;
-      case 3: st = launch_tc<3>(thi, tlo, p, partial, dev_status, grid, stream); break;
-      case 4: st = launch_tc<4>(thi, tlo, p, partial, dev_status, grid, stream); break;
-      default: set_error("covariances: unsupported channel tiling"); return SSI_E_INVALID;
+    {
+      ProfScope ps(ctx, ST_LAG_GEMM, stream);
+      ssi_status st;
+      switch (c.nb) {
+        case 1: st = launch_tc<1>(thi, tlo, p, partial, dev_status, grid, stream); break;
+        case 2: st = launch_tc<2>(thi, tlo, p, partial, dev_status, grid, stream); break;
+        case 3: st = launch_tc<3>(thi, tlo, p, partial, dev_status, grid, stream); break;
+        case 4: st = launch_tc<4>(thi, tlo, p, partial, dev_status, grid, stream); break;
+        default: set_error("covariances: unsupported channel tiling"); return SSI_E_INVALID;
+      }
+      SSI_TRY(st);
     }
-    SSI_TRY(st);
-    k_reduce_partials<<<ctx->num_sms * 4, 256, 0, stream>>>(partial, c.n_split, split_stride, c.l,
-                                                            c.l_pad, c.max_lag, (int)c.N, R);
-    SSI_CUDA(cudaGetLastError());
+    {
+      ProfScope ps(ctx, ST_LAG_REDUCE, stream);
+      k_reduce_partials<<<ctx->num_sms * 4, 256, 0, stream>>>(partial, c.n_split, split_stride, c.l,
+                                                              c.l_pad, c.max_lag, (int)c.N, R);
+      SSI_CUDA(cudaGetLastError());
+    }
+    count_launches(ctx, 3);
   } else {
     float* partial = ws.take<float>((size_t)c.n_split * split_stride);
     if (!partial) { set_error("covariances: workspace too small"); return SSI_E_NOMEM; }
     const int nb = (c.l + 63) / 64;
-    dim3 grd((unsigned)(c.max_lag * nb * nb), (unsigned)c.n_split);
-    k_lag_gemm_fp32<<<grd, 256, 0, stream>>>(Y, c.l, (int)c.N, c.l_pad, c.max_lag,
-                                             c.rows_per_split, split_stride, partial);
-    SSI_CUDA(cudaGetLastError());
-    k_reduce_partials<<<ctx->num_sms * 4, 256, 0, stream>>>(partial, c.n_split, split_stride, c.l,
-                                                            c.l_pad, c.max_lag, (int)c.N, R);
-    SSI_CUDA(cudaGetLastError());
+    {
+      ProfScope ps(ctx, ST_LAG_GEMM, stream);
+      dim3 grd((unsigned)(c.max_lag * nb * nb), (unsigned)c.n_split);
+      k_lag_gemm_fp32<<<grd, 256, 0, stream>>>(Y, c.l, (int)c.N, c.l_pad, c.max_lag,
+                                               c.rows_per_split, split_stride, partial);
+      SSI_CUDA(cudaGetLastError());
+    }
+    {
+      ProfScope ps(ctx, ST_LAG_REDUCE, stream);
+      k_reduce_partials<<<ctx->num_sms * 4, 256, 0, stream>>>(partial, c.n_split, split_stride, c.l,
+                                                              c.l_pad, c.max_lag, (int)c.N, R);
+      SSI_CUDA(cudaGetLastError());
+    }
+    count_launches(ctx, 2);
   }
   return SSI_OK;
 }

@@ -747,6 +747,9 @@ ssi_status realize_ws(ssi_ctx* ctx, Workspace& ws, const RealizePlan& r, const i
   }
   const int tiles = (int)ceil_div(k, 64);
   dim3 g1((unsigned)(tiles * tiles), (unsigned)n_chunks, (unsigned)(2 * r.n_lags));
+  count_launches(ctx, 4);
+  {
+  ProfScope ps(ctx, ST_GRAM, stream);
   k_gram_gh<<<g1, 256, 0, stream>>>(lt, n_chunks, partial);
   SSI_CUDA(cudaGetLastError());
   k_gram_reduce<<<ctx->num_sms * 4, 256, 0, stream>>>(partial, r.n_lags, n_chunks, k, GH);
@@ -757,6 +760,7 @@ ssi_status realize_ws(ssi_ctx* ctx, Workspace& ws, const RealizePlan& r, const i
                                 (int)(220 * 1024)));
   k_lag_factor<<<r.n_lags, 1024, fsmem, stream>>>(GH, k, RM, dev_status);
   SSI_CUDA(cudaGetLastError());
+  }
   ep.lt = lt;
   ep.n_orders = r.n_orders;
   long long so = 0;
@@ -777,6 +781,7 @@ ssi_status realize_ws(ssi_ctx* ctx, Workspace& ws, const RealizePlan& r, const i
   ep.xbuf_off = (int)round_up((int64_t)nsm_max * (nsm_max + 1), 32);
   const size_t esmem = ((size_t)ep.xbuf_off + (size_t)(EIG_THREADS / 32) * 2 * nsm_max) * sizeof(float);
   SSI_CUDA(cudaFuncSetAttribute(k_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)esmem));
+  ProfScope ps_eig(ctx, ST_EIG, stream);
   k_eig<<<r.n_lags * r.n_orders, EIG_THREADS, esmem, stream>>>(ep);
   SSI_CUDA(cudaGetLastError());
   return SSI_OK;

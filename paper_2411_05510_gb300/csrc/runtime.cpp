@@ -192,6 +192,43 @@ void ssi_destroy(ssi_ctx* ctx) {
 
 size_t ssi_memory_in_use(const ssi_ctx* ctx) { return ctx ? ctx->in_use : 0; }
 
+ssi_status ssi_profile(ssi_ctx* ctx, int enable) {
+  SSI_CHECK(ctx, "ssi_profile: null context");
+  std::lock_guard<std::mutex> g(ctx->prof_mu);
+  ctx->prof_on = enable != 0;
+  return SSI_OK;
+}
+
+ssi_status ssi_profile_read(ssi_ctx* ctx, double* ms, int64_t* counts, int n, int64_t* launches) {
+  SSI_CHECK(ctx, "ssi_profile_read: null context");
+  std::vector<std::tuple<int, cudaEvent_t, cudaEvent_t>> recs;
+  {
+    std::lock_guard<std::mutex> g(ctx->prof_mu);
+    recs.swap(ctx->prof_recs);
+  }
+  for (int i = 0; i < n; ++i) {
+    if (ms) ms[i] = 0.0;
+    if (counts) counts[i] = 0;
+  }
+  ssi_status st = SSI_OK;
+  for (auto& r : recs) {
+    const int id = std::get<0>(r);
+    cudaEvent_t e0 = std::get<1>(r), e1 = std::get<2>(r);
+    float t = 0.f;
+    cudaError_t e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+    if (e != cudaSuccess) st = cuda_fail(e, "cudaEventElapsedTime", __FILE__, __LINE__);
+    if (id >= 0 && id < n) {
+      if (ms) ms[id] += t;
+      if (counts) counts[id] += 1;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+  }
+  if (launches) *launches = ctx->launches.exchange(0);
+  return st;
+}
+
 ssi_status ssi_rank_rule(int64_t T_size, double* kbar_percent, int64_t* k) {
   SSI_CHECK(T_size > 0, "ssi_rank_rule: T_size must be positive");
   double kbar = 30.0 - 0.00156 * (double)T_size;

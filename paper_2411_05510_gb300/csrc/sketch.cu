@@ -541,15 +541,19 @@ ssi_status toeplitz_rsvd_ws(ssi_ctx* ctx, Workspace& ws, const RsvdPlan& r, cons
     return SSI_E_NOMEM;
   }
   const int nsm = ctx->num_sms;
-  k_r_store<<<grid_1d((long long)rblk, 256, nsm), 256, 0, stream>>>(R, n_lag, r.l, r.l_pad,
-                                                                      tc ? Rh : nullptr, Rl,
-                                                                      tc ? nullptr : R32);
-  SSI_CUDA(cudaGetLastError());
-  // Omega in the padded column layout of T
-  k_omega<<<grid_1d((long long)xsz, 256, nsm), 256, 0, stream>>>(0, r.K, r.Kp, seed, nullptr, r.l,
-                                                                   r.l_pad, r.L_pad, Yb,
-                                                                   tc ? Xh : nullptr, Xl);
-  SSI_CUDA(cudaGetLastError());
+  count_launches(ctx, 4);   // covariance store, Omega, U = Q U~, small SVD
+  {
+    ProfScope ps_pre(ctx, ST_OTHER, stream);
+    k_r_store<<<grid_1d((long long)rblk, 256, nsm), 256, 0, stream>>>(R, n_lag, r.l, r.l_pad,
+                                                                        tc ? Rh : nullptr, Rl,
+                                                                        tc ? nullptr : R32);
+    SSI_CUDA(cudaGetLastError());
+    // Omega in the padded column layout of T
+    k_omega<<<grid_1d((long long)xsz, 256, nsm), 256, 0, stream>>>(0, r.K, r.Kp, seed, nullptr, r.l,
+                                                                     r.l_pad, r.L_pad, Yb,
+                                                                     tc ? Xh : nullptr, Xl);
+    SSI_CUDA(cudaGetLastError());
+  }
 
   CUtensorMap tAn_h, tAn_l, tAt_h, tAt_l, tX_h, tX_l;
   if (tc) {
@@ -567,20 +571,27 @@ ssi_status toeplitz_rsvd_ws(ssi_ctx* ctx, Workspace& ws, const RsvdPlan& r, cons
 
   // one product D = T X (mode 0) or T^T X (mode 1) of the current basis into Yb
   auto product = [&](int mode) -> ssi_status {
+    count_launches(ctx, tc ? 3 : 2);
     if (tc) {
+      ProfScope ps0(ctx, ST_OTHER, stream);
       // the basis sits in Yb (fp32): split it into the bf16 operand pair
       k_to_bf16<<<grid_1d((long long)xsz, 256, nsm), 256, 0, stream>>>(Yb, (long long)xsz, Xh, Xl);
       SSI_CUDA(cudaGetLastError());
+    }
+    if (tc) {
+      ProfScope ps(ctx, ST_SKETCH_GEMM, stream);
       if (mode == 0)
         SSI_TRY(launch_tg_nb<0>(nb, tAn_h, tAn_l, tX_h, tX_l, p, part, dev_status, grid_tc, stream));
       else
         SSI_TRY(launch_tg_nb<1>(nb, tAt_h, tAt_l, tX_h, tX_l, p, part, dev_status, grid_tc, stream));
     } else {
+      ProfScope ps(ctx, ST_SKETCH_GEMM, stream);
       dim3 g((unsigned)(r.L_pad / 64), (unsigned)(r.Kp / 64), (unsigned)p.n_split);
       if (mode == 0) k_toeplitz_gemm_fp32<0><<<g, 256, 0, stream>>>(R32, Yb, p, part);
       else k_toeplitz_gemm_fp32<1><<<g, 256, 0, stream>>>(R32, Yb, p, part);
       SSI_CUDA(cudaGetLastError());
     }
+    ProfScope ps2(ctx, ST_SKETCH_GEMM, stream);
     k_sum_splits<<<grid_1d((long long)xsz, 256, nsm), 256, 0, stream>>>(part, p.n_split,
                                                                          (long long)xsz, Yb);
     SSI_CUDA(cudaGetLastError());
@@ -589,6 +600,8 @@ ssi_status toeplitz_rsvd_ws(ssi_ctx* ctx, Workspace& ws, const RsvdPlan& r, cons
   const size_t ws_mark = ws.off;
   auto qr = [&](float* Rout) -> ssi_status {
     ws.off = ws_mark;
+    ProfScope ps(ctx, ST_QR, stream);
+    count_launches(ctx, 1);
     return qr_launch(ctx, ws, Yb, r.L_pad, r.K, r.Kp, Rout, dev_status, stream);
   };
 
@@ -605,7 +618,11 @@ ssi_status toeplitz_rsvd_ws(ssi_ctx* ctx, Workspace& ws, const RsvdPlan& r, cons
   SSI_TRY(product(1));       // P^T = T^T Q
   SSI_TRY(qr(R2));           // P^T = Q2 R2
   ws.off = ws_mark;
-  SSI_TRY(jacobi_launch(ws, R2, r.K, Ut, sig, dev_status, stream));
+  {
+    ProfScope ps(ctx, ST_SMALL_SVD, stream);
+    SSI_TRY(jacobi_launch(ws, R2, r.K, Ut, sig, dev_status, stream));
+  }
+  ProfScope ps_u(ctx, ST_OTHER, stream);
   k_form_u<<<grid_1d((long long)r.L * r.k, 256, nsm), 256, 0, stream>>>(Qs, r.Kp, Ut, r.K, r.k, r.l,
                                                                         r.l_pad, r.i, U);
   SSI_CUDA(cudaGetLastError());

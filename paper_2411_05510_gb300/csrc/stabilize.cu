@@ -135,6 +135,8 @@ ssi_status stabilize_ws(ssi_ctx* ctx, Workspace&, int n_lags, int n_orders, cons
   const long long n = so * n_lags;
   if (n == 0) return SSI_OK;
   const int blocks = (int)std::min<long long>(ceil_div(n, 256), (long long)ctx->num_sms * 8);
+  ProfScope ps(ctx, ST_STAB, stream);
+  count_launches(ctx, 2);
   k_hard_criteria<<<blocks, 256, 0, stream>>>(poles, n, p);
   SSI_CUDA(cudaGetLastError());
   const int blocks2 = (int)std::min<long long>(ceil_div(n * 32, 256), (long long)ctx->num_sms * 16);

@@ -14,7 +14,7 @@ import torch
 
 import oracle as O
 import ssi_synth as S
-from parity import compare_parity_set, gpu_cells
+from parity import compare_parity_set, gpu_cells, nearest, separated_orders
 
 pytestmark = pytest.mark.gpu
 
@@ -96,7 +96,7 @@ def test_realize_recovers_exact_modes_from_model_covariances(P, ctx):
 
 def test_realize_matches_oracle_on_noisy_chain(P, ctx):
     w = S.workload("chain4_tiny")
-    Y, f_true, *_ = S.record(w)
+    Y, f_true, _, phi_true = S.record(w)
     T = O.block_toeplitz(O.covariances(Y, 39), 20)
     U, s = O.full_svd(T)
     orders = list(range(2, 41, 2))
@@ -114,7 +114,7 @@ def test_realize_matches_oracle_on_noisy_chain(P, ctx):
         for c in row:
             ok = (c["xi"] > 0) & (c["xi"] <= 0.1) & (c["mpc"] > 0.6) & (c["mpd"] < 0.5) & (np.abs(c["mu"]) < 1)
             c["flags"] = np.where(ok, 8, 0)
-    n, worst = compare_parity_set(gpu, ora, f_true, orders, 4, min_matches=40)
+    n, worst = compare_parity_set(gpu, ora, f_true, orders, 4, min_matches=40, phi_true=phi_true)
 
 
 def test_stabilize_flags_match_oracle_on_shared_poles(P, ctx):
@@ -176,7 +176,7 @@ def test_stabilize_flags_match_oracle_on_shared_poles(P, ctx):
 def test_full_solve_chain_matches_oracle(P, ctx, prec):
     """Complete solve of the 4-channel chain record (i = 20, full width k = 80, orders 2..40)."""
     w = S.workload("chain4_tiny")
-    Y, f_true, *_ = S.record(w, np.float32)
+    Y, f_true, _, phi_true = S.record(w, np.float32)
     orders = w["orders"]
     desc = P.job_desc(torch.from_numpy(Y).cuda(), w["fs"], w["lags"], orders, k=40, oversample=40,
                       q=0, prec=prec, seed=1)
@@ -186,4 +186,16 @@ def test_full_solve_chain_matches_oracle(P, ctx, prec):
     gpu = gpu_cells(rec, phi.cpu().numpy(), w["lags"], orders, 4)
     ora, sv = O.ssi_solve(Y.astype(np.float64), w["fs"], w["lags"], orders, full_svd_=True)
     assert np.allclose(Sg.cpu().numpy()[0, :8], sv[0][:8], rtol=1e-4)
-    compare_parity_set(gpu, ora, f_true, orders, 4, min_matches=40)
+    gate = separated_orders(orders, sv[0])
+    assert 8 in gate
+    compare_parity_set(gpu, ora, f_true, orders, 4, min_matches=4, phi_true=phi_true,
+                       gate_orders=gate)
+    # at every order from 2m on, every mode is identified by an HC-passing pole within 1 %
+    for m, n in enumerate(orders):
+        if n < 8:
+            continue
+        cell = dict(gpu[0][m])
+        cell["flags"] = rec_flags = cell["flags"]
+        for r, f0 in enumerate(f_true):
+            j = nearest(cell, f0, phi_true[:, r])
+            assert j is not None and abs(cell["f"][j] - f0) / f0 < 1e-2, (n, r)
