@@ -92,6 +92,27 @@ ssi_status ssi_covariances(ssi_ctx* ctx, const float* Y, int l, int64_t N, int m
                            ssi_precision prec, double* R, void* stream);
 
 /* ------------------------------------------------------------------------------
+ * Covariances without device allocation (no counterpart in the paper: an
+ * interface for callers that cannot allocate device memory when they need the
+ * covariances, e.g. code inside a CUDA-graph capture that must not add allocation
+ * nodes, plugins of a framework that owns all device memory, or processes under a
+ * fixed memory reservation).
+ * Same result as ssi_covariances with SSI_PREC_FP32 (same definition of R_k, same
+ * argument layout), computed on the CUDA cores of the current device.  It calls no
+ * cudaMalloc / cudaFree and needs no context: its scratch is one file-scope device
+ * array of 16 MiB (4 Mi floats) that every GPU loading the library holds until the
+ * process exits.
+ * Limits: max_lag * roundup(l, 64)^2 <= 4 Mi floats (SSI_E_INVALID beyond, with a
+ * message), plus the limits of ssi_covariances.
+ * The first call on a device looks up the array's device address (a runtime query
+ * that may not be captured), so make it before any stream capture on that device.
+ * Every call shares the one array: calls whose work overlaps on the GPU (different
+ * streams, or several host threads) race and must be serialised by the caller.
+ * ---------------------------------------------------------------------------- */
+ssi_status ssi_covariances_noalloc(const float* Y, int l, int64_t N, int max_lag, double* R,
+                                   void* stream);
+
+/* ------------------------------------------------------------------------------
  * Gaussian test matrix Omega of Sec. 2.2 (Eq. Y = A Omega, Algorithm 1, line 1).
  * omega   device, float32, rows x cols row-major.  Entry (r, c) comes from the
  *         Philox4x32-10 counter (r, c, 0, 0) with key (seed & 0xffffffff,

@@ -481,3 +481,84 @@ extern "C" ssi_status ssi_covariances(ssi_ctx* ctx, const float* Y, int l, int64
   SSI_TRY(covariances_ws(ctx, ctx->ws, plan, Y, prec, R, ctx->dev_status, s));
   return SSI_OK;
 }
+
+// ---------------------------------------------------------------------------------------
+// Covariances without any device allocation.
+//
+// Some callers cannot allocate device memory at the time they need covariances: code
+// running inside a CUDA-graph capture that must not add allocation nodes, plugins of a
+// host framework that owns every device allocation, or processes that run under a fixed
+// memory reservation.  For them this variant keeps its scratch (the per-time-chunk FP32
+// partial sums of the CUDA-core lag GEMM) in one file-scope device array of
+// NOALLOC_SCRATCH_FLOATS floats (16 MiB), which every GPU that loads the library holds
+// until the process exits.  Inputs and outputs still come from the caller.
+// ---------------------------------------------------------------------------------------
+namespace ssi {
+namespace {
+
+constexpr size_t NOALLOC_SCRATCH_FLOATS = size_t(4) << 20;   // 16 MiB
+static __device__ __align__(256) float g_noalloc_scratch[NOALLOC_SCRATCH_FLOATS];
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mu;
+float* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+
+// Device address of the scratch array on the current device.  Host code cannot use the
+// array's name as an address; it asks the runtime once per device.
+ssi_status noalloc_scratch(int device, float** out) {
+  if (device < 0 || device >= NOALLOC_MAX_DEVICES) {
+    set_error("ssi_covariances_noalloc: device %d beyond %d", device, NOALLOC_MAX_DEVICES);
+    return SSI_E_INVALID;
+  }
+  std::lock_guard<std::mutex> g(g_noalloc_mu);
+  if (!g_noalloc_ptr[device]) {
+    void* p = nullptr;
+    SSI_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_noalloc_ptr[device] = static_cast<float*>(p);
+  }
+  *out = g_noalloc_ptr[device];
+  return SSI_OK;
+}
+
+}  // namespace
+}  // namespace ssi
+
+extern "C" ssi_status ssi_covariances_noalloc(const float* Y, int l, int64_t N, int max_lag,
+                                              double* R, void* stream) {
+  using namespace ssi;
+  SSI_CHECK(Y && R, "ssi_covariances_noalloc: null pointer");
+  SSI_CHECK(l >= 1 && l <= 1024, "ssi_covariances_noalloc: l=%d out of range [1, 1024]", l);
+  SSI_CHECK(max_lag >= 1 && (int64_t)max_lag < N, "ssi_covariances_noalloc: need 1 <= max_lag < N");
+  SSI_CHECK(N < (1LL << 31) - 1024, "ssi_covariances_noalloc: N too large");
+  int device = 0;
+  SSI_CUDA(cudaGetDevice(&device));
+  const int l_pad = (int)round_up(l, 64);
+  const size_t per_split = (size_t)max_lag * l_pad * l_pad;
+  if (per_split > NOALLOC_SCRATCH_FLOATS) {
+    set_error("ssi_covariances_noalloc: max_lag * roundup(l, 64)^2 = %zu floats exceeds the "
+              "fixed scratch of %zu floats; use ssi_covariances",
+              per_split, NOALLOC_SCRATCH_FLOATS);
+    return SSI_E_INVALID;
+  }
+  float* scratch = nullptr;
+  SSI_TRY(noalloc_scratch(device, &scratch));
+  // as many time chunks as fit the scratch, at most one per 512 samples and 64 in all
+  int64_t n_split = (int64_t)(NOALLOC_SCRATCH_FLOATS / per_split);
+  n_split = std::min<int64_t>(n_split, std::min<int64_t>(64, ceil_div(N, 512)));
+  n_split = std::max<int64_t>(1, n_split);
+  const int rows_per_split = (int)round_up(ceil_div(N, n_split), 32);
+  n_split = ceil_div(N, rows_per_split);
+  const int nb = (l + 63) / 64;
+  const int num_sms = device_sms(device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // every partial entry read by the reduction is written by the GEMM, so nothing needs
+  // clearing between calls
+  dim3 grd((unsigned)(max_lag * nb * nb), (unsigned)n_split);
+  k_lag_gemm_fp32<<<grd, 256, 0, s>>>(Y, l, (int)N, l_pad, max_lag, rows_per_split,
+                                      (long long)per_split, scratch);
+  SSI_CUDA(cudaGetLastError());
+  k_reduce_partials<<<num_sms * 4, 256, 0, s>>>(scratch, (int)n_split, (long long)per_split, l,
+                                                l_pad, max_lag, (int)N, R);
+  SSI_CUDA(cudaGetLastError());
+  return SSI_OK;
+}
