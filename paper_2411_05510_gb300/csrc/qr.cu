@@ -37,6 +37,7 @@ struct QrParams {
   unsigned* bar;       // [2] arrival counter, generation
   int* status;
   int* abort_flag;
+  int lds;             // leading dimension of the rows staged in shared memory (0: not staged)
 };
 
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
@@ -80,49 +81,102 @@ __device__ bool grid_sync(const QrParams& p, GridBar& gb) {
   return ok_s != 0;
 }
 
-// In-place FP64 Cholesky of the w x w matrix G (row-major, lower part used), executed by
-// one warp; returns the upper factor R (R^T R = G) in Rm and its inverse in Ri.
-__device__ void chol_inv_warp(const double* G, int w, double* Rm, double* Ri, int lane) {
-  // R computed row by row: R[j][j] = sqrt(G[j][j] - sum_k<j R[k][j]^2),
-  // R[j][c] = (G[j][c] - sum_k<j R[k][j] R[k][c]) / R[j][j]
-  double gmax = 0.0;
-  for (int j = 0; j < w; ++j) gmax = fmax(gmax, G[j * PB + j]);
-  const double floor_v = fmax(gmax * 1e-14, 1e-300);
-  for (int j = 0; j < w; ++j) {
-    double d = G[j * PB + j];
-    for (int k = 0; k < j; ++k) d -= Rm[k * PB + j] * Rm[k * PB + j];
-    d = sqrt(fmax(d, floor_v));
-    __syncwarp();
-    for (int c = lane; c < w; c += 32) {
-      if (c == j) Rm[j * PB + j] = d;
-      else if (c > j) {
-        double s = G[j * PB + c];
-        for (int k = 0; k < j; ++k) s -= Rm[k * PB + j] * Rm[k * PB + c];
-        Rm[j * PB + c] = s / d;
-      } else {
-        Rm[j * PB + c] = 0.0;
-      }
+// Sum over the P per-CTA partials of entries [e0, e1) (stride `stride` between partials):
+// this CTA's threads split the partials of each entry, then combine in shared memory.
+template <typename T>
+__device__ void slice_reduce(const T* part, size_t stride, int P, int e0, int e1, T* out) {
+  __shared__ double red[QR_THREADS];
+  const int E = e1 - e0;
+  if (E <= 0) return;
+  const int per = max(1, QR_THREADS / E);       // threads per entry
+  const int tid = threadIdx.x;
+  for (int base = 0; base < E; base += QR_THREADS / per) {
+    const int le = base + tid / per, sub = tid % per;
+    double s = 0.0;
+    if (tid / per < QR_THREADS / per && le < E)
+      for (int c = sub; c < P; c += per) s += (double)part[(size_t)c * stride + e0 + le];
+    red[tid] = s;
+    __syncthreads();
+    if (sub == 0 && tid / per < QR_THREADS / per && le < E) {
+      double t = 0.0;
+      for (int q = 0; q < per; ++q) t += red[tid + q];
+      out[e0 + le] = (T)t;
     }
-    __syncwarp();
+    __syncthreads();
   }
-  // inverse of the upper triangular R by column back substitution: lane = column
-  for (int c = lane; c < w; c += 32) {
-    for (int r = w - 1; r >= 0; --r) {
-      double s = (r == c) ? 1.0 : 0.0;
-      for (int k = r + 1; k <= c; ++k) s -= Rm[r * PB + k] * Ri[k * PB + c];
-      Ri[r * PB + c] = (r <= c) ? s / Rm[r * PB + r] : 0.0;
+}
+
+// FP32 Cholesky of a well-conditioned w x w Gram matrix by one warp (lane c holds column c):
+// used by the second Cholesky-QR pass, whose Gram matrix is the identity up to O(eps).
+__device__ void chol_warp_f32(const double* G, int w, double* R, double* rdiag, int lane) {
+  float col[PB];
+#pragma unroll
+  for (int a = 0; a < PB; ++a) col[a] = (a < w && lane < w && a <= lane) ? (float)G[a * PB + lane] : 0.f;
+#pragma unroll
+  for (int j = 0; j < PB; ++j) {
+    if (j >= w) break;
+    // R[j][j] = sqrt(col_j[j]); R[j][c] = col_c[j] / R[j][j]
+    const float djj = __shfl_sync(0xffffffffu, col[j], j);
+    const float rs = rsqrtf(fmaxf(djj, 1e-30f));
+    const float rjc = (lane >= j) ? col[j] * rs : 0.f;   // lane == j: sqrt(d)
+    R[j * PB + lane] = (lane < w) ? (double)rjc : 0.0;
+    if (lane == j) rdiag[j] = (double)rs;
+    // trailing update: col_c[a] -= R[j][a] R[j][c] for j < a <= c
+#pragma unroll
+    for (int a = 0; a < PB; ++a) {
+      const float rja = __shfl_sync(0xffffffffu, rjc, a);
+      if (a > j && a <= lane) col[a] = fmaf(-rja, rjc, col[a]);
     }
   }
   __syncwarp();
 }
 
+// Cholesky of the w x w Gram matrix G (FP64, upper triangle used) by the whole CTA:
+// R[j][j] = sqrt(d_j), R[j][c] = G'[j][c] / R[j][j], trailing update of the upper triangle.
+// Reciprocal square roots replace divisions (FP64 division and square root are long
+// instruction sequences on this part).  Writes R (upper) and 1 / R[j][j].
+__device__ void chol_cta(double* G, int w, double* R, double* rdiag) {
+  const int tid = threadIdx.x;
+  __shared__ double s_floor;
+  if (tid == 0) {
+    double gmax = 0.0;
+    for (int j = 0; j < w; ++j) gmax = fmax(gmax, G[j * PB + j]);
+    s_floor = fmax(gmax * 1e-14, 1e-300);
+  }
+  for (int e = tid; e < PB * PB; e += QR_THREADS) R[e] = 0.0;
+  __syncthreads();
+  for (int j = 0; j < w; ++j) {
+    if (tid == 0) {
+      // 1/sqrt(d): FP32 seed and one Newton step in FP64 (relative error ~1e-14); the FP64
+      // library square root and division are long instruction sequences on this part
+      const double d = fmax(G[j * PB + j], s_floor);
+      double y = (double)rsqrtf((float)d);
+      y = y * (1.5 - 0.5 * d * y * y);
+      y = y * (1.5 - 0.5 * d * y * y);
+      rdiag[j] = y;
+      R[j * PB + j] = d * y;
+    }
+    __syncthreads();
+    const double rs = rdiag[j];
+    for (int c = j + 1 + tid; c < w; c += QR_THREADS) R[j * PB + c] = G[j * PB + c] * rs;
+    __syncthreads();
+    const int m = w - j - 1;
+    for (int e = tid; e < m * m; e += QR_THREADS) {
+      const int a = j + 1 + e / m, c = j + 1 + e % m;
+      if (c >= a) G[a * PB + c] -= R[j * PB + a] * R[j * PB + c];
+    }
+    __syncthreads();
+  }
+}
+
 __global__ void __launch_bounds__(QR_THREADS)
     k_qr_bcgs2(QrParams p) {
+  extern __shared__ float s_rows[];     // this CTA's rows (when they fit), leading dim p.lds
   __shared__ double sG[PB * PB];
   __shared__ double sR[2][PB * PB];     // R1, R2 of the current panel
-  __shared__ double sRi[PB * PB];
-  __shared__ float sRif[PB * PB];
-  __shared__ float sW[64][PB + 1];      // staging for local row updates
+  __shared__ double sRd[PB];            // 1 / R[j][j] of the current factor
+  __shared__ float sRf[PB * PB];        // current factor in FP32
+  __shared__ float sRdf[PB];
   GridBar gb;
   gb.gen = *(volatile unsigned*)&p.bar[1];
 
@@ -130,8 +184,19 @@ __global__ void __launch_bounds__(QR_THREADS)
   const int rows_per = (p.rows + P - 1) / P;
   const int r0 = blockIdx.x * rows_per;
   const int r1 = min(p.rows, r0 + rows_per);
+  const int nr = max(0, r1 - r0);
   const int tid = threadIdx.x;
-  const int warp = tid >> 5, lane = tid & 31;
+  // local rows: shared memory when they fit, else the matrix itself
+  float* Ab = p.lds ? s_rows : p.A + (size_t)r0 * p.ld;
+  const int ldb = p.lds ? p.lds : p.ld;
+  float* sC = p.lds ? s_rows + (size_t)rows_per * p.lds : nullptr;   // projection (j0 x PB)
+  if (p.lds) {
+    for (int e = tid; e < nr * p.ncols; e += QR_THREADS) {
+      const int rr = e / p.ncols, c = e % p.ncols;
+      Ab[rr * ldb + c] = p.A[(size_t)(r0 + rr) * p.ld + c];
+    }
+    __syncthreads();
+  }
 
   for (int j0 = 0; j0 < p.ncols; j0 += PB) {
     const int w = min(PB, p.ncols - j0);
@@ -144,49 +209,45 @@ __global__ void __launch_bounds__(QR_THREADS)
           const int a = e / PB, b = e % PB;
           float s = 0.f;
           if (b < w)
-            for (int r = r0; r < r1; ++r) s = fmaf(p.A[(size_t)r * p.ld + a], p.A[(size_t)r * p.ld + j0 + b], s);
+            for (int rr = 0; rr < nr; ++rr) s = fmaf(Ab[rr * ldb + a], Ab[rr * ldb + j0 + b], s);
           myC[e] = s;
         }
         if (!grid_sync(p, gb)) return;
-        for (int e = blockIdx.x * QR_THREADS + tid; e < nC; e += P * QR_THREADS) {
-          float s = 0.f;
-          for (int c = 0; c < P; ++c) s += p.red_c[(size_t)c * p.ncols * PB + e];
-          p.fin_c[e] = s;
+        {
+          const int per_cta = (nC + P - 1) / P;
+          const int e0 = blockIdx.x * per_cta, e1 = min(nC, e0 + per_cta);
+          slice_reduce<float>(p.red_c, (size_t)p.ncols * PB, P, e0, e1, p.fin_c);
         }
         if (!grid_sync(p, gb)) return;
-        // ---- W -= Q[:, :j0] C on local rows
-        for (int rb = r0; rb < r1; rb += 64) {
-          const int nr = min(64, r1 - rb);
-          for (int e = tid; e < nr * PB; e += QR_THREADS) {
-            const int rr = e / PB, b = e % PB;
-            float s = 0.f;
-            if (b < w) {
-              const float* qrow = p.A + (size_t)(rb + rr) * p.ld;
-              for (int a = 0; a < j0; ++a) s = fmaf(qrow[a], p.fin_c[a * PB + b], s);
-            }
-            sW[rr][b] = s;
-          }
+        const float* C = p.fin_c;
+        if (sC) {
+          for (int e = tid; e < nC; e += QR_THREADS) sC[e] = p.fin_c[e];
           __syncthreads();
-          for (int e = tid; e < nr * PB; e += QR_THREADS) {
-            const int rr = e / PB, b = e % PB;
-            if (b < w) p.A[(size_t)(rb + rr) * p.ld + j0 + b] -= sW[rr][b];
-          }
-          __syncthreads();
+          C = sC;
+        }
+        // ---- W -= Q[:, :j0] C on local rows (a warp shares its row; lanes take columns)
+        for (int e = tid; e < nr * PB; e += QR_THREADS) {
+          const int rr = e / PB, b = e % PB;
+          if (b >= w) continue;
+          float s = 0.f;
+          for (int a = 0; a < j0; ++a) s = fmaf(Ab[rr * ldb + a], C[a * PB + b], s);
+          Ab[rr * ldb + j0 + b] -= s;
         }
         if (p.Rout && blockIdx.x == 0) {
-          // R[:j0, j0+b] accumulates C1 + C2 R1 (pass 1 adds C2 * R1 later)
+          // R[:j0, j0+b] accumulates C1 + C2 R1
           for (int e = tid; e < j0 * PB; e += QR_THREADS) {
             const int a = e / PB, b = e % PB;
             if (b >= w) continue;
             if (pass == 0) {
-              p.Rout[(size_t)a * p.ncols + j0 + b] = p.fin_c[e];
+              p.Rout[(size_t)a * p.ncols + j0 + b] = C[e];
             } else {
               float s = 0.f;
-              for (int c = 0; c <= b; ++c) s = fmaf(p.fin_c[a * PB + c], (float)sR[0][c * PB + b], s);
+              for (int c = 0; c <= b; ++c) s = fmaf(C[a * PB + c], (float)sR[0][c * PB + b], s);
               p.Rout[(size_t)a * p.ncols + j0 + b] += s;
             }
           }
         }
+        __syncthreads();
       }
       // ---- Gram G = W^T W in double-FP32 over local rows
       {
@@ -195,9 +256,9 @@ __global__ void __launch_bounds__(QR_THREADS)
           const int a = e / PB, b = e % PB;
           float sh = 0.f, sl = 0.f;
           if (a < w && b < w && a <= b) {
-            for (int r = r0; r < r1; ++r) {
-              const float x = p.A[(size_t)r * p.ld + j0 + a];
-              const float y = p.A[(size_t)r * p.ld + j0 + b];
+            for (int rr = 0; rr < nr; ++rr) {
+              const float x = Ab[rr * ldb + j0 + a];
+              const float y = Ab[rr * ldb + j0 + b];
               const float pr = x * y;
               const float pe = fmaf(x, y, -pr);
               float s, e2;
@@ -209,42 +270,45 @@ __global__ void __launch_bounds__(QR_THREADS)
           myG[e] = (double)sh + (double)sl;
         }
         if (!grid_sync(p, gb)) return;
-        for (int e = blockIdx.x * QR_THREADS + tid; e < PB * PB; e += P * QR_THREADS) {
-          double s = 0.0;
-          for (int c = 0; c < P; ++c) s += p.red_g[(size_t)c * PB * PB + e];
-          p.fin_g[e] = s;
+        {
+          const int per_cta = (PB * PB + P - 1) / P;
+          const int e0 = blockIdx.x * per_cta, e1 = min(PB * PB, e0 + per_cta);
+          slice_reduce<double>(p.red_g, (size_t)PB * PB, P, e0, e1, p.fin_g);
         }
         if (!grid_sync(p, gb)) return;
       }
-      // ---- Cholesky (FP64, one warp, every CTA) and W <- W R^{-1}
+      // ---- Cholesky (FP64, whole CTA, every CTA) and W <- W R^{-1} row by row (FP32)
       for (int e = tid; e < PB * PB; e += QR_THREADS) {
         const int a = e / PB, b = e % PB;
-        const double g = (a <= b) ? p.fin_g[a * PB + b] : p.fin_g[b * PB + a];
-        sG[e] = (a < w && b < w) ? g : 0.0;
-        sR[pass][e] = 0.0;
-        sRi[e] = 0.0;
+        sG[e] = (a < w && b < w && a <= b) ? p.fin_g[e] : 0.0;
       }
       __syncthreads();
-      if (warp == 0) chol_inv_warp(sG, w, sR[pass], sRi, lane);
-      __syncthreads();
-      for (int e = tid; e < PB * PB; e += QR_THREADS) sRif[e] = (float)sRi[e];
-      __syncthreads();
-      for (int rb = r0; rb < r1; rb += 64) {
-        const int nr = min(64, r1 - rb);
-        for (int e = tid; e < nr * PB; e += QR_THREADS) {
-          const int rr = e / PB, b = e % PB;
-          sW[rr][b] = (b < w) ? p.A[(size_t)(rb + rr) * p.ld + j0 + b] : 0.f;
-        }
-        __syncthreads();
-        for (int e = tid; e < nr * PB; e += QR_THREADS) {
-          const int rr = e / PB, b = e % PB;
-          if (b >= w) continue;
-          float s = 0.f;
-          for (int a = 0; a <= b; ++a) s = fmaf(sW[rr][a], sRif[a * PB + b], s);
-          p.A[(size_t)(rb + rr) * p.ld + j0 + b] = s;
-        }
+      if (pass == 0) {
+        chol_cta(sG, w, sR[pass], sRd);
+      } else {
+        if (tid < 32) chol_warp_f32(sG, w, sR[pass], sRd, tid);
         __syncthreads();
       }
+      for (int e = tid; e < PB * PB; e += QR_THREADS) sRf[e] = (float)sR[pass][e];
+      for (int e = tid; e < PB; e += QR_THREADS) sRdf[e] = (float)sRd[e];
+      __syncthreads();
+      for (int rr = tid; rr < nr; rr += QR_THREADS) {
+        float x[PB];
+#pragma unroll
+        for (int b = 0; b < PB; ++b) x[b] = (b < w) ? Ab[rr * ldb + j0 + b] : 0.f;
+        // solve x_new R = x (forward substitution over columns)
+#pragma unroll
+        for (int b = 0; b < PB; ++b) {
+          float s = x[b];
+#pragma unroll
+          for (int a = 0; a < b; ++a) s = fmaf(-x[a], sRf[a * PB + b], s);
+          x[b] = s * sRdf[b];
+        }
+#pragma unroll
+        for (int b = 0; b < PB; ++b)
+          if (b < w) Ab[rr * ldb + j0 + b] = x[b];
+      }
+      __syncthreads();
     }
     if (p.Rout && blockIdx.x == 0) {
       // diagonal block R2 R1
@@ -255,12 +319,14 @@ __global__ void __launch_bounds__(QR_THREADS)
         for (int c = a; c <= b; ++c) s += sR[1][a * PB + c] * sR[0][c * PB + b];
         p.Rout[(size_t)(j0 + a) * p.ncols + j0 + b] = (float)s;
       }
-      for (int e = tid; e < PB * p.ncols; e += QR_THREADS) {
-        const int a = e / p.ncols, b = e % p.ncols;
-        if (a < w && b < j0) p.Rout[(size_t)(j0 + a) * p.ncols + b] = 0.f;
-      }
     }
     __syncthreads();
+  }
+  if (p.lds) {
+    for (int e = tid; e < nr * p.ncols; e += QR_THREADS) {
+      const int rr = e / p.ncols, c = e % p.ncols;
+      p.A[(size_t)(r0 + rr) * p.ld + c] = Ab[rr * ldb + c];
+    }
   }
 }
 
@@ -289,10 +355,16 @@ ssi_status qr_launch(ssi_ctx* ctx, Workspace& ws, float* A, int rows, int ncols,
   p.ncols = ncols;
   p.ld = ld;
   p.Rout = Rout;
-  int per_sm = 0;
-  SSI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_qr_bcgs2, QR_THREADS, 0));
-  int P = std::min<int>(ctx->num_sms * std::max(per_sm, 1), ctx->num_sms);
-  P = std::max(1, std::min<int>(P, (int)ceil_div(rows, 32)));
+  int P = std::max(1, std::min<int>(ctx->num_sms, (int)ceil_div(rows, 32)));
+  const int rows_per = (int)ceil_div(rows, P);
+  const int lds = ncols | 1;   // odd leading dimension: rows of a warp fall in distinct banks
+  size_t smem = ((size_t)rows_per * lds + (size_t)ncols * PB) * sizeof(float);
+  if (smem > 160 * 1024) {
+    smem = 0;   // rows stay in global memory
+  } else {
+    p.lds = lds;
+  }
+  SSI_CUDA(cudaFuncSetAttribute(k_qr_bcgs2, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
   p.red_c = ws.take<float>((size_t)ctx->num_sms * ncols * PB);
   p.fin_c = ws.take<float>((size_t)ncols * PB);
   p.red_g = ws.take<double>((size_t)ctx->num_sms * PB * PB);
@@ -310,7 +382,7 @@ ssi_status qr_launch(ssi_ctx* ctx, Workspace& ws, float* A, int rows, int ncols,
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(P);
   cfg.blockDim = dim3(QR_THREADS);
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = smem;
   cfg.stream = stream;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;

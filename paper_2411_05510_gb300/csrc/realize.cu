@@ -33,6 +33,10 @@ constexpr int EIG_THREADS = 256;
 constexpr int GR_ROWS = 512;      // rows per Gram chunk
 constexpr int SMEM_N_MAX = 224;   // largest order whose A fits shared memory
 
+constexpr int WN = 32;                       // window of the bulge chase
+constexpr int WB = WN - 3;                   // bulge steps per window
+__device__ __forceinline__ int warp_id_of(int tid) { return tid >> 5; }   // reflectors staged per chunk in the back transformation
+
 struct LagTable {
   int n_lags;
   int l, k;
@@ -146,21 +150,52 @@ __global__ void __launch_bounds__(1024)
     }
     __syncthreads();
   }
-  // Rinv by column back substitution: thread c owns column c
-  for (int c = tid; c < k; c += nth) {
-    for (int r = k - 1; r >= 0; --r) {
-      if (r > c) { Rinv[(size_t)r * k + c] = 0.f; continue; }
-      float s = (r == c) ? 1.f : 0.f;
-      for (int j = r + 1; j <= c; ++j) s -= sR[r * k + j] * Rinv[(size_t)j * k + c];
-      Rinv[(size_t)r * k + c] = s / sR[r * k + r];
+  // Rinv by column back substitution and M = R^{-T} H by forward substitution; one warp
+  // per column, the column held in registers across the lanes (entry j on lane j % 32)
+  const int warp = tid >> 5, lane = tid & 31, nwarps = nth >> 5;
+  constexpr int KJ = 8;   // k <= 256
+  for (int c = warp; c < k; c += nwarps) {
+    float x[KJ];
+#pragma unroll
+    for (int q = 0; q < KJ; ++q) x[q] = 0.f;
+    for (int r = c; r >= 0; --r) {
+      float part = 0.f;
+#pragma unroll
+      for (int q = 0; q < KJ; ++q) {
+        const int j = lane + 32 * q;
+        if (j > r && j <= c) part = fmaf(sR[r * k + j], x[q], part);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+      const float v = ((r == c) ? 1.f - part : -part) / sR[r * k + r];
+      if (lane == (r & 31)) x[r >> 5] = v;
+    }
+#pragma unroll
+    for (int q = 0; q < KJ; ++q) {
+      const int j = lane + 32 * q;
+      if (j < k) Rinv[(size_t)j * k + c] = (j <= c) ? x[q] : 0.f;
     }
   }
-  // M = R^{-T} H: forward substitution R^T M = H, thread c owns column c
-  for (int c = tid; c < k; c += nth) {
+  for (int c = warp; c < k; c += nwarps) {
+    float x[KJ];
+#pragma unroll
+    for (int q = 0; q < KJ; ++q) x[q] = 0.f;
     for (int r = 0; r < k; ++r) {
-      float s = H[(size_t)r * k + c];
-      for (int j = 0; j < r; ++j) s -= sR[j * k + r] * M[(size_t)j * k + c];
-      M[(size_t)r * k + c] = s / sR[r * k + r];
+      float part = 0.f;
+#pragma unroll
+      for (int q = 0; q < KJ; ++q) {
+        const int j = lane + 32 * q;
+        if (j < r) part = fmaf(sR[j * k + r], x[q], part);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+      const float v = (H[(size_t)r * k + c] - part) / sR[r * k + r];
+      if (lane == (r & 31)) x[r >> 5] = v;
+    }
+#pragma unroll
+    for (int q = 0; q < KJ; ++q) {
+      const int j = lane + 32 * q;
+      if (j < k) M[(size_t)j * k + c] = x[q];
     }
   }
 }
@@ -177,6 +212,7 @@ struct EigParams {
   long long work_off[512];   // offset of order m's scratch within a lag's scratch
   long long work_per_lag;
   int xbuf_off;              // floats: start of the per-warp eigenvector buffers in shared memory
+  int log_off;               // floats: start of the reflector staging buffer in shared memory
   int nmax;                  // largest order of the launch
   double dt;
   ssi_pole* poles;
@@ -185,9 +221,12 @@ struct EigParams {
 };
 
 // scratch of one realisation of order n: Hessenberg v's (n*n), reflector log, X (n*n)
-__host__ __device__ inline long long qr_log_cap(int n) { return 3LL * n * n + 64LL * n + 64; }
-__host__ __device__ inline long long eig_work_floats(int n) {
-  return (long long)n * n + 8 * qr_log_cap(n) + (long long)n * n + 2LL * n + 64;
+// scratch of one realisation of order n: Hessenberg reflectors (n*n), the log of window
+// transformations (zlog_cap(n) entries of ZREC floats), eigenvector matrix X (n*n)
+constexpr int ZREC = 32 * 32 + 8;   // one window: b, e, then the 32 x 32 factor row-major
+__host__ __device__ inline long long zlog_cap(int n) { return (long long)n * n / 16 + 2LL * n + 64; }
+__host__ __device__ inline long long eig_work_floats(int n, int) {
+  return (long long)n * n + zlog_cap(n) * ZREC + (long long)n * n + 64;
 }
 
 __device__ __forceinline__ float sgnf(float a, float b) { return b >= 0.f ? fabsf(a) : -fabsf(a); }
@@ -205,8 +244,8 @@ __global__ void __launch_bounds__(EIG_THREADS)
   const int ld = n + 1;   // padded leading dimension against bank conflicts
   float* work = p.work + (size_t)t * p.work_per_lag + p.work_off[mi];
   float* hv = work;                           // Hessenberg reflectors: n x n (v, beta in [j*n + n-1])
-  float* qlog = hv + (size_t)n * n;           // QR reflector log, 8 floats per entry
-  float* X = qlog + 8 * qr_log_cap(n);        // eigenvector matrix, n x (2 m)
+  float* zlog = hv + (size_t)n * n;           // window transformations of the QR sweeps
+  float* X = zlog + zlog_cap(n) * ZREC;       // eigenvector matrix, n x (2 m)
   float* A = smem;                            // n x (n+1), orders <= SMEM_N_MAX
   __shared__ float sh[16];
   __shared__ int shi[16];
@@ -219,210 +258,398 @@ __global__ void __launch_bounds__(EIG_THREADS)
   float* phi_out = p.phi + ((size_t)t * p.slots_per_lag + p.slot_off[mi]) * 2 * l;
   const int n_slots = n / 2;
 
-  // ---- 1. A~_n = Rinv[:n,:n] M[:n,:n]
-  for (int e = tid; e < n * n; e += nth) {
-    const int r = e / n, c = e % n;
-    float s = 0.f;
-    for (int j = r; j < n; ++j) s = fmaf(Rinv[(size_t)r * k + j], M[(size_t)j * k + c], s);
-    A[r * ld + c] = s;
+  // ---- 1. A~_n = Rinv[:n,:n] M[:n,:n] (Rinv upper triangular); 1 x 4 strips per thread
+  {
+    const int n4 = (n + 3) / 4;
+    for (int e = tid; e < n * n4; e += nth) {
+      const int r = e / n4, c0 = (e % n4) * 4;
+      float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+      const float* rrow = Rinv + (size_t)r * k;
+      for (int j = r; j < n; ++j) {
+        const float a = rrow[j];
+        const float* mrow = M + (size_t)j * k + c0;
+        s0 = fmaf(a, mrow[0], s0);
+        if (c0 + 1 < n) s1 = fmaf(a, mrow[1], s1);
+        if (c0 + 2 < n) s2 = fmaf(a, mrow[2], s2);
+        if (c0 + 3 < n) s3 = fmaf(a, mrow[3], s3);
+      }
+      A[r * ld + c0] = s0;
+      if (c0 + 1 < n) A[r * ld + c0 + 1] = s1;
+      if (c0 + 2 < n) A[r * ld + c0 + 2] = s2;
+      if (c0 + 3 < n) A[r * ld + c0 + 3] = s3;
+    }
   }
   __syncthreads();
 
-  // ---- 2. Householder reduction to upper Hessenberg form
+  // ---- 2. Householder reduction to upper Hessenberg form (v kept in shared memory and
+  //         logged to global memory for the back transformation)
+  float* sv = smem + p.xbuf_off;   // n floats (the eigenvector buffers are not in use yet)
+  __shared__ float s_part[EIG_THREADS / 32];
   for (int j = 0; j + 2 < n; ++j) {
     const int len = n - j - 1;
     float* v = hv + (size_t)j * n;
-    // norm of A[j+1:, j] (thread 0; len <= 224)
+    float ss = 0.f;
+    for (int r = tid; r < len; r += nth) {
+      const float x = A[(j + 1 + r) * ld + j];
+      ss = fmaf(x, x, ss);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    if ((tid & 31) == 0) s_part[tid >> 5] = ss;
+    __syncthreads();
     if (tid == 0) {
-      float ss = 0.f;
-      for (int r = 0; r < len; ++r) ss = fmaf(A[(j + 1 + r) * ld + j], A[(j + 1 + r) * ld + j], ss);
+      float tot = 0.f;
+      for (int w2 = 0; w2 < nth / 32; ++w2) tot += s_part[w2];
       const float x0 = A[(j + 1) * ld + j];
-      const float nx = sqrtf(ss);
+      const float nx = sqrtf(tot);
       const float alpha = x0 >= 0.f ? -nx : nx;
-      const float vv = ss - x0 * x0 + (x0 - alpha) * (x0 - alpha);
+      const float vv = tot - x0 * x0 + (x0 - alpha) * (x0 - alpha);
       sh[0] = alpha;
       sh[1] = (nx > 0.f && vv > 0.f) ? 2.f / vv : 0.f;
       sh[2] = x0 - alpha;
     }
     __syncthreads();
     const float beta = sh[1];
-    for (int r = tid; r < len; r += nth) v[r] = (r == 0) ? sh[2] : A[(j + 1 + r) * ld + j];
+    for (int r = tid; r < len; r += nth) {
+      const float vr = (r == 0) ? sh[2] : A[(j + 1 + r) * ld + j];
+      sv[r] = vr;
+      v[r] = vr;
+    }
     if (tid == 0) v[n - 1] = beta;   // v has len <= n-2 entries; beta stored at the end
     __syncthreads();
     if (beta != 0.f) {
-      // left: A[j+1:, c] -= beta v (v^T A[j+1:, c]) for c >= j
-      for (int c = j + tid; c < n; c += nth) {
-        float s = 0.f;
-        for (int r = 0; r < len; ++r) s = fmaf(v[r], A[(j + 1 + r) * ld + c], s);
-        s *= beta;
-        for (int r = 0; r < len; ++r) A[(j + 1 + r) * ld + c] -= s * v[r];
+      float* __restrict__ Ar = A;
+      const float* __restrict__ vr = sv;
+      // left: A[j+1:, c] -= beta v (v^T A[j+1:, c]) for c > j (column j is set below)
+      for (int c = j + 1 + tid; c < n; c += nth) {
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+        int r = 0;
+        for (; r + 3 < len; r += 4) {
+          s0 = fmaf(vr[r], Ar[(j + 1 + r) * ld + c], s0);
+          s1 = fmaf(vr[r + 1], Ar[(j + 2 + r) * ld + c], s1);
+          s2 = fmaf(vr[r + 2], Ar[(j + 3 + r) * ld + c], s2);
+          s3 = fmaf(vr[r + 3], Ar[(j + 4 + r) * ld + c], s3);
+        }
+        for (; r < len; ++r) s0 = fmaf(vr[r], Ar[(j + 1 + r) * ld + c], s0);
+        const float sc = (s0 + s1 + s2 + s3) * beta;
+#pragma unroll 4
+        for (r = 0; r < len; ++r) Ar[(j + 1 + r) * ld + c] -= sc * vr[r];
       }
       __syncthreads();
       // right: A[r, j+1:] -= beta (A[r, j+1:] v) v^T for all rows
       for (int r = tid; r < n; r += nth) {
-        float s = 0.f;
-        for (int c = 0; c < len; ++c) s = fmaf(A[r * ld + j + 1 + c], v[c], s);
-        s *= beta;
-        for (int c = 0; c < len; ++c) A[r * ld + j + 1 + c] -= s * v[c];
+        float* __restrict__ row = Ar + r * ld + j + 1;
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+        int c = 0;
+        for (; c + 3 < len; c += 4) {
+          s0 = fmaf(row[c], vr[c], s0);
+          s1 = fmaf(row[c + 1], vr[c + 1], s1);
+          s2 = fmaf(row[c + 2], vr[c + 2], s2);
+          s3 = fmaf(row[c + 3], vr[c + 3], s3);
+        }
+        for (; c < len; ++c) s0 = fmaf(row[c], vr[c], s0);
+        const float sc = (s0 + s1 + s2 + s3) * beta;
+#pragma unroll 4
+        for (c = 0; c < len; ++c) row[c] -= sc * vr[c];
       }
       __syncthreads();
-      if (tid == 0) {
-        A[(j + 1) * ld + j] = sh[0];
-        for (int r = 2; r <= len; ++r) A[(j + r) * ld + j] = 0.f;
-      }
+      for (int r = 1 + tid; r <= len; r += nth) A[(j + r) * ld + j] = (r == 1) ? sh[0] : 0.f;
     }
     __syncthreads();
   }
 
-  // ---- 3. Francis double-shift QR (real Schur form, full T updated), reflectors logged
-  // shi[0]: nn, shi[1]: l, shi[2]: m, shi[3]: done flag, shi[4]: failed, shi[5]: log count
+  // ---- 3b. Francis double-shift QR to real Schur form (full T), windowed.
+  //  The bulge of each sweep is chased by warp 0 inside a window of WN rows/columns;
+  //  in-window rows and columns are updated at once and the window's transformations
+  //  accumulate in Zb (WN x WN).  After each window all threads apply Zb to the rows
+  //  right of the window (H[b:e, e:n] = Zb^T H[b:e, e:n]) and to the rows above it
+  //  (H[0:b, b:e] = H[0:b, b:e] Zb), and Zb is logged for the back transformation of
+  //  the eigenvectors.  Same arithmetic as the unwindowed sweep.
+  float* Zbuf = smem + p.log_off;     // 2 buffers of WN x (WN + 4) (16-byte aligned rows)
+  __shared__ int s_ctl[8];            // 0 b, 1 e, 2 kend, 3 state (0 run, 1 done, 2 failed), 4 pending buf, 5 pb, 6 pe
+  __shared__ float s_sh[3];           // shift vector of the first step of the sweep
   if (tid == 0) {
-    float anorm = 0.f;
-    for (int r = 0; r < n; ++r)
-      for (int c = max(r - 1, 0); c < n; ++c) anorm += fabsf(A[r * ld + c]);
-    sh[8] = anorm;
-    shi[0] = n - 1;
-    shi[4] = 0;
-    shi[5] = 0;
+    s_ctl[3] = 0;
+    s_ctl[4] = -1;
+    s_ctl[7] = 0;   // windows logged
   }
   __syncthreads();
-  const long long log_cap = qr_log_cap(n);
-  int its = 0, total_its = 0;
-  const int itmax = 30 * max(10, n);
-  while (true) {
-    // thread 0: deflation search and shift selection
-    if (tid == 0) {
-      int nn = shi[0];
-      const float anorm = sh[8];
-      shi[3] = 0;
-      while (nn >= 0) {
-        int ll;
-        for (ll = nn; ll >= 1; --ll) {
-          float s = fabsf(A[(ll - 1) * ld + ll - 1]) + fabsf(A[ll * ld + ll]);
-          if (s == 0.f) s = anorm;
-          if (fabsf(A[ll * ld + ll - 1]) <= FLT_EPSILON * s) {
-            A[ll * ld + ll - 1] = 0.f;
-            break;
-          }
-        }
-        if (ll < 1) ll = 0;
-        if (ll == nn) { nn -= 1; its = 0; continue; }
-        if (ll == nn - 1) { nn -= 2; its = 0; continue; }
-        // a QR sweep is needed on rows ll..nn
-        if (total_its >= itmax) { shi[4] = 1; nn = -1; break; }
-        float x = A[nn * ld + nn], y = A[(nn - 1) * ld + nn - 1];
-        float w = A[nn * ld + nn - 1] * A[(nn - 1) * ld + nn];
-        if (its == 10 || its == 20) {
-          const float s = fabsf(A[nn * ld + nn - 1]) + fabsf(A[(nn - 1) * ld + nn - 2]);
-          x = y = 0.75f * s;
-          w = -0.4375f * s * s;
-        }
-        ++its;
-        ++total_its;
-        int m;
-        float pp = 0.f, qq = 0.f, rr = 0.f;
-        for (m = nn - 2; m >= ll; --m) {
-          const float z = A[m * ld + m];
-          const float r2 = x - z, s2 = y - z;
-          pp = (r2 * s2 - w) / A[(m + 1) * ld + m] + A[m * ld + m + 1];
-          qq = A[(m + 1) * ld + m + 1] - z - r2 - s2;
-          rr = A[(m + 2) * ld + m + 1];
-          const float s = fabsf(pp) + fabsf(qq) + fabsf(rr);
-          pp /= s; qq /= s; rr /= s;
-          if (m == ll) break;
-          const float u = fabsf(A[m * ld + m - 1]) * (fabsf(qq) + fabsf(rr));
-          const float v = fabsf(pp) * (fabsf(A[(m - 1) * ld + m - 1]) + fabsf(z) + fabsf(A[(m + 1) * ld + m + 1]));
-          if (u <= FLT_EPSILON * v) break;
-        }
-        for (int r = m + 2; r <= nn; ++r) {
-          A[r * ld + r - 2] = 0.f;
-          if (r != m + 2) A[r * ld + r - 3] = 0.f;
-        }
-        shi[1] = ll;
-        shi[2] = m;
-        sh[0] = pp; sh[1] = qq; sh[2] = rr;
-        shi[3] = 1;
-        break;
+  {
+    // warp-0 state (identical in every lane)
+    float anorm = 0.f;
+    int nn = n - 1, its = 0, total_its = 0, ll = 0, m = 0, b = 0, fail = 0, blk = 0;
+    bool in_sweep = false;
+    if (warp_id_of(tid) == 0) {
+      for (int e2 = tid; e2 < n * n; e2 += 32) {
+        const int r = e2 / n, c = e2 % n;
+        if (c >= r - 1) anorm += fabsf(A[r * ld + c]);
       }
-      shi[0] = nn;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) anorm += __shfl_xor_sync(0xffffffffu, anorm, o);
     }
-    __syncthreads();
-    if (!shi[3]) break;   // converged (nn < 0) or failed
-    const int ll = shi[1], m = shi[2], nn = shi[0];
-    // bulge chase k = m .. nn-1
-    for (int kk = m; kk <= nn - 1; ++kk) {
-      if (tid == 0) {
-        float pp, qq, rr, x;
-        bool go = true;
-        if (kk == m) {
-          pp = sh[0]; qq = sh[1]; rr = sh[2];
-          x = 1.f;
-        } else {
-          pp = A[kk * ld + kk - 1];
-          qq = A[(kk + 1) * ld + kk - 1];
-          rr = (kk != nn - 1) ? A[(kk + 2) * ld + kk - 1] : 0.f;
-          x = fabsf(pp) + fabsf(qq) + fabsf(rr);
-          if (x != 0.f) { pp /= x; qq /= x; rr /= x; } else go = false;
-        }
-        float s = 0.f;
-        if (go) {
-          s = sgnf(sqrtf(pp * pp + qq * qq + rr * rr), pp);
-          if (s == 0.f) go = false;
-        }
-        if (go) {
-          if (kk == m) {
-            if (ll != m) A[kk * ld + kk - 1] = -A[kk * ld + kk - 1];
-          } else {
-            A[kk * ld + kk - 1] = -s * x;
+    const int itmax = 30 * max(10, n);
+    while (true) {
+      const int cur = blk & 1;
+      float* Zb = Zbuf + cur * WN * (WN + 4);
+      if (tid < 32) {
+        const int lane0 = tid;
+        // start a sweep when none is running: deflation and shift selection
+        while (!in_sweep && nn >= 0 && !fail) {
+          int l2 = 0;
+          for (int base = nn; base >= 1; base -= 32) {
+            const int cand = base - lane0;
+            bool small = false;
+            if (cand >= 1) {
+              float sd = fabsf(A[(cand - 1) * ld + cand - 1]) + fabsf(A[cand * ld + cand]);
+              if (sd == 0.f) sd = anorm;
+              small = fabsf(A[cand * ld + cand - 1]) <= FLT_EPSILON * sd;
+            }
+            const unsigned msk = __ballot_sync(0xffffffffu, small);
+            if (msk) {
+              l2 = base - (__ffs(msk) - 1);
+              break;
+            }
           }
-          pp += s;
-          sh[4] = pp / s;        // w0
-          sh[5] = qq / s;        // w1
-          sh[6] = rr / s;        // w2
-          sh[9] = qq / pp;       // u1
-          sh[10] = rr / pp;      // u2
-          shi[6] = 1;
-          const int cnt = shi[5];
-          if (cnt < log_cap) {
-            float* e = qlog + 8LL * cnt;
-            e[0] = sh[4]; e[1] = sh[5]; e[2] = sh[6]; e[3] = sh[9]; e[4] = sh[10];
-            e[5] = __int_as_float(kk);
-            e[6] = __int_as_float(kk != nn - 1 ? 3 : 2);
-            e[7] = 0.f;
+          __syncwarp();
+          if (l2 >= 1 && lane0 == 0) A[l2 * ld + l2 - 1] = 0.f;
+          __syncwarp();
+          if (l2 == nn) { nn -= 1; its = 0; continue; }
+          if (l2 == nn - 1) { nn -= 2; its = 0; continue; }
+          if (total_its >= itmax) { fail = 1; break; }
+          float x = A[nn * ld + nn], y = A[(nn - 1) * ld + nn - 1];
+          float w = A[nn * ld + nn - 1] * A[(nn - 1) * ld + nn];
+          if (its == 10 || its == 20) {
+            const float s = fabsf(A[nn * ld + nn - 1]) + fabsf(A[(nn - 1) * ld + nn - 2]);
+            x = y = 0.75f * s;
+            w = -0.4375f * s * s;
           }
-          shi[5] = cnt + 1;
-        } else {
-          shi[6] = 0;
+          ++its;
+          ++total_its;
+          // start of the bulge: the largest mm in [l2, nn-2] where two consecutive
+          // subdiagonals are negligible relative to the shift vector (mm = l2 always
+          // qualifies); lanes test 32 candidates at a time
+          int mm = l2;
+          for (int base = nn - 2; base >= l2; base -= 32) {
+            const int cand = base - lane0;
+            bool ok = false;
+            if (cand >= l2) {
+              if (cand == l2) {
+                ok = true;
+              } else {
+                const float z = A[cand * ld + cand];
+                const float r2 = x - z, s2 = y - z;
+                float p0 = (r2 * s2 - w) / A[(cand + 1) * ld + cand] + A[cand * ld + cand + 1];
+                float q0 = A[(cand + 1) * ld + cand + 1] - z - r2 - s2;
+                float r0 = A[(cand + 2) * ld + cand + 1];
+                const float sc = fabsf(p0) + fabsf(q0) + fabsf(r0);
+                p0 /= sc; q0 /= sc; r0 /= sc;
+                const float u = fabsf(A[cand * ld + cand - 1]) * (fabsf(q0) + fabsf(r0));
+                const float v = fabsf(p0) * (fabsf(A[(cand - 1) * ld + cand - 1]) + fabsf(z) +
+                                             fabsf(A[(cand + 1) * ld + cand + 1]));
+                ok = u <= FLT_EPSILON * v;
+              }
+            }
+            const unsigned msk = __ballot_sync(0xffffffffu, ok);
+            if (msk) {
+              mm = base - (__ffs(msk) - 1);
+              break;
+            }
+          }
+          float pp, qq, rr;
+          {
+            const float z = A[mm * ld + mm];
+            const float r2 = x - z, s2 = y - z;
+            pp = (r2 * s2 - w) / A[(mm + 1) * ld + mm] + A[mm * ld + mm + 1];
+            qq = A[(mm + 1) * ld + mm + 1] - z - r2 - s2;
+            rr = A[(mm + 2) * ld + mm + 1];
+            const float sc = fabsf(pp) + fabsf(qq) + fabsf(rr);
+            pp /= sc; qq /= sc; rr /= sc;
+          }
+          __syncwarp();
+          for (int r = mm + 2 + lane0; r <= nn; r += 32) {
+            A[r * ld + r - 2] = 0.f;
+            if (r != mm + 2) A[r * ld + r - 3] = 0.f;
+          }
+          __syncwarp();
+          ll = l2;
+          m = mm;
+          b = mm;
+          if (lane0 == 0) { s_sh[0] = pp; s_sh[1] = qq; s_sh[2] = rr; }
+          in_sweep = true;
         }
+        __syncwarp();
+        if (lane0 == 0) {
+          if (fail) s_ctl[3] = 2;
+          else if (!in_sweep) s_ctl[3] = 1;
+        }
+        if (in_sweep) {
+          // ---- chase one window: steps kk in [b, kend), window [b, e)
+          const int kend = min(b + WB, nn);
+          const int e = min(b + WN, n);
+          const int w = e - b;
+          for (int q = 0; q < WN; ++q) Zb[lane0 * (WN + 4) + q] = (q == lane0) ? 1.f : 0.f;
+          __syncwarp();
+          for (int kk = b; kk < kend; ++kk) {
+            const bool three = kk != nn - 1;
+            float pp, qq, rr, xs = 1.f;
+            bool go = true;
+            if (kk == m) {
+              pp = s_sh[0]; qq = s_sh[1]; rr = s_sh[2];
+            } else {
+              pp = A[kk * ld + kk - 1];
+              qq = A[(kk + 1) * ld + kk - 1];
+              rr = three ? A[(kk + 2) * ld + kk - 1] : 0.f;
+              xs = fabsf(pp) + fabsf(qq) + fabsf(rr);
+              if (xs != 0.f) {
+                const float ix = __fdividef(1.f, xs);
+                pp *= ix; qq *= ix; rr *= ix;
+              } else {
+                go = false;
+              }
+            }
+            float s = 0.f, is = 0.f;
+            if (go) {
+              const float ss = pp * pp + qq * qq + rr * rr;
+              go = ss > 0.f;
+              if (go) {
+                const float rs = rsqrtf(ss);
+                s = sgnf(ss * rs, pp);
+                is = sgnf(rs, pp);
+              }
+            }
+            __syncwarp();
+            if (go) {
+              if (lane0 == 0) {
+                if (kk == m) {
+                  if (ll != m) A[kk * ld + kk - 1] = -A[kk * ld + kk - 1];
+                } else {
+                  A[kk * ld + kk - 1] = -s * xs;
+                }
+              }
+              pp += s;
+              const float ip = __fdividef(1.f, pp);
+              const float w0 = pp * is, w1 = qq * is, w2 = three ? rr * is : 0.f;
+              const float u1 = qq * ip, u2 = three ? rr * ip : 0.f;
+              // row modification inside the window: columns kk .. e-1
+              {
+                const int j = b + lane0;
+                if (j >= kk && j < e) {
+                  const float a0 = A[kk * ld + j], a1 = A[(kk + 1) * ld + j];
+                  const float a2 = three ? A[(kk + 2) * ld + j] : 0.f;
+                  const float t = a0 + u1 * a1 + u2 * a2;
+                  A[kk * ld + j] = a0 - t * w0;
+                  A[(kk + 1) * ld + j] = a1 - t * w1;
+                  if (three) A[(kk + 2) * ld + j] = a2 - t * w2;
+                }
+              }
+              __syncwarp();
+              // column modification inside the window: rows b .. min(nn, kk+3)
+              {
+                const int i2 = b + lane0;
+                if (i2 <= min(nn, kk + 3)) {
+                  const float b0 = A[i2 * ld + kk], b1 = A[i2 * ld + kk + 1];
+                  const float b2 = three ? A[i2 * ld + kk + 2] : 0.f;
+                  const float t = w0 * b0 + w1 * b1 + w2 * b2;
+                  A[i2 * ld + kk] = b0 - t;
+                  A[i2 * ld + kk + 1] = b1 - t * u1;
+                  if (three) A[i2 * ld + kk + 2] = b2 - t * u2;
+                }
+                // the same transformation accumulated in Zb (window coordinates)
+                const int kl = kk - b;
+                float* zr = Zb + lane0 * (WN + 4);
+                const float z0 = zr[kl], z1 = zr[kl + 1];
+                const float z2 = three ? zr[kl + 2] : 0.f;
+                const float t = w0 * z0 + w1 * z1 + w2 * z2;
+                zr[kl] = z0 - t;
+                zr[kl + 1] = z1 - t * u1;
+                if (three) zr[kl + 2] = z2 - t * u2;
+              }
+            }
+            __syncwarp();
+          }
+          if (lane0 == 0) {
+            s_ctl[0] = b;
+            s_ctl[1] = e;
+            s_ctl[2] = kend;
+          }
+          b = kend;
+          if (b > nn - 1) in_sweep = false;
+          (void)w;
+        }
+        __syncwarp();
       }
       __syncthreads();
-      if (shi[6]) {
-        const float w0 = sh[4], w1 = sh[5], w2 = sh[6], u1 = sh[9], u2 = sh[10];
-        const bool three = kk != nn - 1;
-        // row modification over all columns j >= kk (full Schur form)
-        for (int j = kk + tid; j < n; j += nth) {
-          float s = A[kk * ld + j] + u1 * A[(kk + 1) * ld + j];
-          if (three) s += u2 * A[(kk + 2) * ld + j];
-          A[kk * ld + j] -= s * w0;
-          A[(kk + 1) * ld + j] -= s * w1;
-          if (three) A[(kk + 2) * ld + j] -= s * w2;
+      const int state = s_ctl[3];
+      if (state != 0) break;
+      // ---- apply the window's Zb outside the window (all threads)
+      {
+        const int bb = s_ctl[0], ee = s_ctl[1], ww = ee - bb;
+        float* ZT = Zbuf + (cur ^ 1) * WN * (WN + 4);   // the other buffer: Zb transposed, ld WN+4
+        for (int e2 = tid; e2 < WN * WN; e2 += nth) {
+          const int i2 = e2 / WN, j2 = e2 % WN;
+          ZT[i2 * (WN + 4) + j2] = Zb[j2 * (WN + 4) + i2];
         }
         __syncthreads();
-        // column modification over rows 0 .. min(nn, kk+3)
-        const int imax = min(nn, kk + 3);
-        for (int i2 = tid; i2 <= imax; i2 += nth) {
-          float s = w0 * A[i2 * ld + kk] + w1 * A[i2 * ld + kk + 1];
-          if (three) s += w2 * A[i2 * ld + kk + 2];
-          A[i2 * ld + kk] -= s;
-          A[i2 * ld + kk + 1] -= s * u1;
-          if (three) A[i2 * ld + kk + 2] -= s * u2;
+        const int n_right = n - ee;
+        const int t = tid;
+        if (t < n_right || t - n_right < bb) {
+          const bool right = t < n_right;
+          const int c = ee + t, r = t - n_right;
+          float in[WN];
+#pragma unroll
+          for (int j2 = 0; j2 < WN; ++j2)
+            in[j2] = (j2 < ww) ? (right ? A[(bb + j2) * ld + c] : A[r * ld + bb + j2]) : 0.f;
+          // four outputs at a time: four independent accumulation chains
+          for (int i0 = 0; i0 < ww; i0 += 4) {
+            float acc[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              const float4* zt = reinterpret_cast<const float4*>(ZT + (i0 + u) * (WN + 4));
+              float a = 0.f;
+#pragma unroll
+              for (int q4 = 0; q4 < WN / 4; ++q4) {
+                const float4 z = zt[q4];
+                a = fmaf(z.x, in[4 * q4], a);
+                a = fmaf(z.y, in[4 * q4 + 1], a);
+                a = fmaf(z.z, in[4 * q4 + 2], a);
+                a = fmaf(z.w, in[4 * q4 + 3], a);
+              }
+              acc[u] = a;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              if (i0 + u < ww) {
+                if (right) A[(bb + i0 + u) * ld + c] = acc[u];
+                else A[r * ld + bb + i0 + u] = acc[u];
+              }
+            }
+          }
         }
+        // log the window: (b, e) and Zb
+        const int widx = s_ctl[7];
+        if (widx < zlog_cap(n)) {
+          float* rec = zlog + (size_t)widx * ZREC;
+          for (int e2 = tid; e2 < WN * WN; e2 += nth)
+            rec[8 + e2] = Zb[(e2 / WN) * (WN + 4) + (e2 % WN)];
+          if (tid == 0) {
+            rec[0] = __int_as_float(bb);
+            rec[1] = __int_as_float(ee);
+          }
+        }
+        __syncthreads();
+        if (tid == 0) s_ctl[7] = widx + 1;
       }
       __syncthreads();
+      ++blk;
     }
+    if (tid == 0) {
+      shi[4] = (s_ctl[3] == 2 || s_ctl[7] > zlog_cap(n)) ? 1 : 0;
+      shi[5] = min((long long)s_ctl[7], zlog_cap(n));
+    }
+    (void)total_its;
   }
-  const bool failed = shi[4] != 0 || shi[5] > log_cap;
-  const int n_log = min((long long)shi[5], log_cap);
+  __syncthreads();
+  const bool failed = shi[4] != 0;
 
   // ---- 4. complex eigenvalues (2x2 blocks), ranked by frequency
   __shared__ int s_npole;
@@ -553,31 +780,66 @@ __global__ void __launch_bounds__(EIG_THREADS)
   }
   __syncthreads();
 
-  // ---- 6. back transformation: Psi~ = Z x, reflectors applied in reverse order
-  float* Xs = A;   // T is no longer needed: X moves to shared memory (n x ncx)
+  // ---- 6. back transformation Psi~ = Q_hess Zb_1 ... Zb_B x (X in shared memory; T is
+  //         no longer needed): windows in reverse order, then the Hessenberg reflectors
+  float* Xs = A;
   for (int e = tid; e < n * ncx; e += nth) Xs[e] = X[e];
-  __syncthreads();
-  for (int col = tid; col < ncx; col += nth) {
-    for (int q = n_log - 1; q >= 0; --q) {
-      const float* e = qlog + 8LL * q;
-      const float w0 = e[0], w1 = e[1], w2 = e[2], u1 = e[3], u2 = e[4];
-      const int kk = __float_as_int(e[5]);
-      const bool three = __float_as_int(e[6]) == 3;
-      float s = Xs[kk * ncx + col] + u1 * Xs[(kk + 1) * ncx + col];
-      if (three) s += u2 * Xs[(kk + 2) * ncx + col];
-      Xs[kk * ncx + col] -= s * w0;
-      Xs[(kk + 1) * ncx + col] -= s * w1;
-      if (three) Xs[(kk + 2) * ncx + col] -= s * w2;
+  {
+    float* Zs = smem + p.log_off;   // two staged window factors, WN x (WN + 4) each
+    const int n_win = shi[5];
+    auto stage = [&](int wdx, int buf) {
+      const float* rec = zlog + (size_t)wdx * ZREC;
+      float* dst = Zs + buf * WN * (WN + 4);
+      for (int e2 = tid; e2 < WN * WN; e2 += nth) dst[(e2 / WN) * (WN + 4) + (e2 % WN)] = rec[8 + e2];
+    };
+    if (n_win > 0) stage(n_win - 1, 0);
+    for (int wdx = n_win - 1, buf = 0; wdx >= 0; --wdx, buf ^= 1) {
+      __syncthreads();
+      if (wdx > 0) stage(wdx - 1, buf ^ 1);   // next factor, overlapped with this product
+      const float* rec = zlog + (size_t)wdx * ZREC;
+      const int bb = __float_as_int(rec[0]), ee = __float_as_int(rec[1]), ww = ee - bb;
+      const float* Zc = Zs + buf * WN * (WN + 4);
+      for (int col = tid; col < ncx; col += nth) {
+        float in[WN];
+#pragma unroll
+        for (int j2 = 0; j2 < WN; ++j2) in[j2] = (j2 < ww) ? Xs[(bb + j2) * ncx + col] : 0.f;
+        for (int i0 = 0; i0 < ww; i0 += 4) {
+          float acc[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const float4* zr = reinterpret_cast<const float4*>(Zc + (i0 + u) * (WN + 4));
+            float a = 0.f;
+#pragma unroll
+            for (int q4 = 0; q4 < WN / 4; ++q4) {
+              const float4 z = zr[q4];
+              a = fmaf(z.x, in[4 * q4], a);
+              a = fmaf(z.y, in[4 * q4 + 1], a);
+              a = fmaf(z.z, in[4 * q4 + 2], a);
+              a = fmaf(z.w, in[4 * q4 + 3], a);
+            }
+            acc[u] = a;
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (i0 + u < ww) Xs[(bb + i0 + u) * ncx + col] = acc[u];
+        }
+      }
     }
+    __syncthreads();
+    float* sv3 = Zs;   // Hessenberg reflector staging (n floats)
     for (int j = n - 3; j >= 0; --j) {
-      const float* v = hv + (size_t)j * n;
-      const float beta = v[n - 1];
-      if (beta == 0.f) continue;
       const int len = n - j - 1;
-      float s = 0.f;
-      for (int r = 0; r < len; ++r) s = fmaf(v[r], Xs[(j + 1 + r) * ncx + col], s);
-      s *= beta;
-      for (int r = 0; r < len; ++r) Xs[(j + 1 + r) * ncx + col] -= s * v[r];
+      __syncthreads();
+      for (int c = tid; c < len; c += nth) sv3[c] = hv[(size_t)j * n + c];
+      __syncthreads();
+      const float beta = hv[(size_t)j * n + n - 1];
+      if (beta == 0.f) continue;
+      for (int col = tid; col < ncx; col += nth) {
+        float sacc = 0.f;
+        for (int r = 0; r < len; ++r) sacc = fmaf(sv3[r], Xs[(j + 1 + r) * ncx + col], sacc);
+        sacc *= beta;
+        for (int r = 0; r < len; ++r) Xs[(j + 1 + r) * ncx + col] -= sacc * sv3[r];
+      }
     }
   }
   __syncthreads();
@@ -602,21 +864,39 @@ __global__ void __launch_bounds__(EIG_THREADS)
     int src = 0;
     for (int o = 0; o < npole; ++o) if (s_rank[o] == j) src = o;
     const float* xr = Xs + 2 * j;
-    // phi_c = sum_a U[c][a] x_a, complex; track the norm and the largest component
+    // phi_c = sum_a U[c][a] psi_a, complex: lanes split a (coalesced rows of U, psi held in
+    // registers), a warp reduction per channel
+    constexpr int NA = (SMEM_N_MAX + 31) / 32;
+    float xre[NA], xim[NA];
+#pragma unroll
+    for (int q = 0; q < NA; ++q) {
+      const int a = lane + 32 * q;
+      xre[q] = (a < n) ? xr[a * ncx] : 0.f;
+      xim[q] = (a < n) ? xr[a * ncx + 1] : 0.f;
+    }
     float nrm2 = 0.f, best = -1.f, bre = 1.f, bim = 0.f;
-    for (int c = lane; c < l; c += 32) {
+    for (int c = 0; c < l; ++c) {
+      const float* wrow = U + (size_t)c * k;
       float sr = 0.f, si = 0.f;
-      const float* urow = U + (size_t)c * k;
-      for (int a = 0; a < n; ++a) {
-        const float u = urow[a];
-        sr = fmaf(u, xr[a * ncx], sr);
-        si = fmaf(u, xr[a * ncx + 1], si);
+#pragma unroll
+      for (int q = 0; q < NA; ++q) {
+        const int a = lane + 32 * q;
+        const float u = (a < n) ? wrow[a] : 0.f;
+        sr = fmaf(u, xre[q], sr);
+        si = fmaf(u, xim[q], si);
       }
-      ph[2 * c] = sr;
-      ph[2 * c + 1] = si;
-      const float m2 = sr * sr + si * si;
-      nrm2 += m2;
-      if (m2 > best) { best = m2; bre = sr; bim = si; }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        sr += __shfl_xor_sync(0xffffffffu, sr, o);
+        si += __shfl_xor_sync(0xffffffffu, si, o);
+      }
+      if (lane == (c & 31)) {
+        ph[2 * c] = sr;
+        ph[2 * c + 1] = si;
+        const float m2 = sr * sr + si * si;
+        nrm2 += m2;
+        if (m2 > best) { best = m2; bre = sr; bim = si; }
+      }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -699,10 +979,11 @@ RealizePlan realize_plan(int n_lags, const int* lags, int l, int k, const int* o
   for (int m = 0; m < n_orders; ++m) {
     r.max_order = std::max(r.max_order, orders[m]);
     r.slots_per_lag += orders[m] / 2;
-    work += eig_work_floats(orders[m]) + (orders[m] > SMEM_N_MAX ? (long long)orders[m] * (orders[m] + 1) : 0) + 64;
+    work += eig_work_floats(orders[m], l) + 64;
   }
   for (int t = 0; t < n_lags; ++t) max_i = std::max(max_i, lags[t]);
   const int n_chunks = (int)ceil_div((int64_t)l * (max_i - 1), GR_ROWS);
+  (void)SMEM_N_MAX;
   WsPlan w;
   w.add<float>((size_t)n_lags * std::max(n_chunks, 1) * 2 * k * k);  // Gram partials
   w.add<float>((size_t)n_lags * 2 * k * k);                          // G | H
@@ -738,7 +1019,7 @@ ssi_status realize_ws(ssi_ctx* ctx, Workspace& ws, const RealizePlan& r, const i
   for (int m = 0; m < r.n_orders; ++m) {
     ep.orders[m] = orders[m];
     ep.work_off[m] = work;
-    work += eig_work_floats(orders[m]) + (orders[m] > SMEM_N_MAX ? (long long)orders[m] * (orders[m] + 1) : 0) + 64;
+    work += eig_work_floats(orders[m], r.l) + 64;
   }
   float* eigw = ws.take<float>((size_t)r.n_lags * work);
   if (!partial || !GH || !RM || !eigw) {
@@ -779,7 +1060,8 @@ ssi_status realize_ws(ssi_ctx* ctx, Workspace& ws, const RealizePlan& r, const i
   const int nsm_max = std::min(r.max_order, SMEM_N_MAX);
   ep.nmax = nsm_max;
   ep.xbuf_off = (int)round_up((int64_t)nsm_max * (nsm_max + 1), 32);
-  const size_t esmem = ((size_t)ep.xbuf_off + (size_t)(EIG_THREADS / 32) * 2 * nsm_max) * sizeof(float);
+  ep.log_off = (int)round_up((int64_t)ep.xbuf_off + (int64_t)(EIG_THREADS / 32) * 2 * nsm_max, 32);
+  const size_t esmem = ((size_t)ep.log_off + (size_t)std::max(2 * WN * (WN + 4), SMEM_N_MAX)) * sizeof(float);
   SSI_CUDA(cudaFuncSetAttribute(k_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)esmem));
   ProfScope ps_eig(ctx, ST_EIG, stream);
   k_eig<<<r.n_lags * r.n_orders, EIG_THREADS, esmem, stream>>>(ep);
@@ -798,7 +1080,7 @@ extern "C" ssi_status ssi_realize_batch(ssi_ctx* ctx, int n_lags, const int* lag
   SSI_CHECK(n_lags >= 1 && n_lags <= MAX_LAGS, "ssi_realize_batch: 1 <= n_lags <= %d", MAX_LAGS);
   SSI_CHECK(n_orders >= 1 && n_orders <= 512, "ssi_realize_batch: 1 <= n_orders <= 512");
   SSI_CHECK(l >= 1 && k >= 2 && dt > 0, "ssi_realize_batch: bad l/k/dt");
-  SSI_CHECK(k <= 232, "ssi_realize_batch: k=%d > 232 not supported", k);
+  SSI_CHECK(k <= 224, "ssi_realize_batch: k=%d > 224 not supported", k);
   for (int t = 0; t < n_lags; ++t) {
     SSI_CHECK(lags[t] >= 2, "ssi_realize_batch: lag %d < 2", lags[t]);
     SSI_CHECK(U[t], "ssi_realize_batch: null U[%d]", t);

@@ -15,7 +15,7 @@ namespace ssi {
 
 namespace {
 
-constexpr int JT = 1024;
+constexpr int JT = 512;
 
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
@@ -25,6 +25,7 @@ __device__ __forceinline__ float warp_sum(float v) {
 
 // B: column c of B at B + c*ldb (length K).  Output: Ut (K x K row-major, column j =
 // singular vector of rank j), S (K, descending).
+template <int RJ8>   // K <= 8 * RJ8
 __global__ void __launch_bounds__(JT, 1)
     k_jacobi_svd(const float* __restrict__ R2, int K, float* __restrict__ Bglobal, float tol,
                  int max_sweeps, float* __restrict__ Ut, float* __restrict__ Sout, int* status) {
@@ -45,36 +46,57 @@ __global__ void __launch_bounds__(JT, 1)
     if (tid == 0) s_rot = 0;
     __syncthreads();
     for (int rnd = 0; rnd < n_pad - 1; ++rnd) {
-      // circle method: position 0 fixed, others rotate by rnd
-      for (int pi = warp; pi < half; pi += nw) {
-        int a = pi, b = n_pad - 1 - pi;
-        auto pos = [&](int x) { return x == 0 ? 0 : 1 + (x - 1 + rnd) % (n_pad - 1); };
-        int p = pos(a), q = pos(b);
-        if (p >= K || q >= K) continue;
-        if (p > q) { int t = p; p = q; q = t; }
+      // circle method: position 0 fixed, others rotate by rnd.  Eight lanes per pair
+      // (four pairs per warp): short reductions, many pairs in flight per warp.
+      const int g = lane >> 3, gl = lane & 7;
+      const unsigned gmask = 0xFFu << (8 * g);
+      // the loop bound depends on the warp only, so all 32 lanes run the same iterations
+      // (the group reductions below shuffle across the whole warp)
+      for (int base = warp * 4; base < half; base += nw * 4) {
+        const int pi = base + g;
+        const bool live = pi < half;
+        int p = 0, q = 0;
+        if (live) {
+          const int a = pi, b = n_pad - 1 - pi;
+          p = (a == 0) ? 0 : 1 + (a - 1 + rnd) % (n_pad - 1);
+          q = (b == 0) ? 0 : 1 + (b - 1 + rnd) % (n_pad - 1);
+          if (p > q) { const int t = p; p = q; q = t; }
+        }
+        const bool act = live && p < K && q < K;
         float* bp = B + (size_t)p * K;
         float* bq = B + (size_t)q * K;
+        float xv[RJ8], yv[RJ8];
         float al = 0.f, be = 0.f, ga = 0.f;
-        for (int r = lane; r < K; r += 32) {
-          const float x = bp[r], y = bq[r];
-          al = fmaf(x, x, al);
-          be = fmaf(y, y, be);
-          ga = fmaf(x, y, ga);
+#pragma unroll
+        for (int t = 0; t < RJ8; ++t) {
+          const int r = gl + 8 * t;
+          xv[t] = (act && r < K) ? bp[r] : 0.f;
+          yv[t] = (act && r < K) ? bq[r] : 0.f;
+          al = fmaf(xv[t], xv[t], al);
+          be = fmaf(yv[t], yv[t], be);
+          ga = fmaf(xv[t], yv[t], ga);
         }
-        al = warp_sum(al);
-        be = warp_sum(be);
-        ga = warp_sum(ga);
-        if (fabsf(ga) > tol * sqrtf(al * be) && al > 0.f && be > 0.f) {
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) {
+          al += __shfl_xor_sync(0xffffffffu, al, o);
+          be += __shfl_xor_sync(0xffffffffu, be, o);
+          ga += __shfl_xor_sync(0xffffffffu, ga, o);
+        }
+        (void)gmask;
+        if (act && fabsf(ga) > tol * sqrtf(al * be) && al > 0.f && be > 0.f) {
           const float zeta = (be - al) / (2.f * ga);
           const float t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
           const float c = rsqrtf(1.f + t * t);
           const float s = c * t;
-          for (int r = lane; r < K; r += 32) {
-            const float x = bp[r], y = bq[r];
-            bp[r] = c * x - s * y;
-            bq[r] = s * x + c * y;
+#pragma unroll
+          for (int u = 0; u < RJ8; ++u) {
+            const int r = gl + 8 * u;
+            if (r < K) {
+              bp[r] = c * xv[u] - s * yv[u];
+              bq[r] = s * xv[u] + c * yv[u];
+            }
           }
-          if (lane == 0) s_rot = 1;
+          if (gl == 0) s_rot = 1;
         }
       }
       __syncthreads();
@@ -134,10 +156,13 @@ ssi_status jacobi_launch(Workspace& ws, const float* R2, int K, float* Ut, float
     }
   } else {
     smem = bytes;
-    SSI_CUDA(cudaFuncSetAttribute(k_jacobi_svd, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    SSI_CUDA(cudaFuncSetAttribute(k_jacobi_svd<29>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)(200 * 1024)));
   }
-  k_jacobi_svd<<<1, JT, smem, stream>>>(R2, K, Bg, 2e-6f, 30, Ut, S, status);
+  if (K <= 232)
+    k_jacobi_svd<29><<<1, JT, smem, stream>>>(R2, K, Bg, 1e-5f, 30, Ut, S, status);
+  else
+    k_jacobi_svd<64><<<1, JT, smem, stream>>>(R2, K, Bg, 1e-5f, 30, Ut, S, status);
   SSI_CUDA(cudaGetLastError());
   return SSI_OK;
 }
