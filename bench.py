@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="bridge186_i60")
+    ap.add_argument("--n-samples", type=int, default=0,
+                    help="record length override (smaller cases for profiler captures)")
     ap.add_argument("--prec", default="split_bf16", choices=["split_bf16", "fp32"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -62,6 +64,23 @@ def dist_setup():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return world, rank, local
+
+
+def max_over_ranks(x: float, device=None) -> float:
+    """Largest value of x over the ranks of the default process group (x alone at N = 1).
+    device: where the reduction tensor lives (a CUDA device under NCCL, CPU under gloo)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: int, world: int, max_ms: float) -> float:
+    """Units per second of the whole job: every rank's units over the slowest rank's time."""
+    return world * units_per_rank / (max_ms / 1e3)
 
 
 def load_peaks():
@@ -211,7 +230,7 @@ def oracle_sample_estimate(Y, w, log=None):
 def run_reference(args, world, rank):
     if rank != 0:
         return
-    w = S.workload(args.workload)
+    w = S.workload(args.workload, **({"N": args.n_samples} if args.n_samples else {}))
     w["name"] = args.workload
     Y, *_ = S.record(w, np.float32)
     Y = Y.astype(np.float64)
@@ -237,12 +256,19 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def l2_note(w):
+    mb = w.get("l", w.get("n_dof", 0)) * w["N"] * 4 / 1e6
+    if mb > 129:
+        return f"inputs larger than L2 (record {mb:.0f} MB fp32 > 129 MB)"
+    return f"record {mb:.1f} MB fits in L2; no flush between steps"
+
+
 def config_of(w, prec):
     cfg = {"workload": w.get("name", None) or "", "channels": w.get("l", w.get("n_dof")),
            "N": w["N"], "fs": w["fs"], "lags": w["lags"], "k": w["k"],
            "oversample": w["oversample"], "q": w["q"],
            "orders": f"{w['orders'][0]}..{w['orders'][-1]} step 2", "prec": prec,
-           "l2": "inputs larger than L2 (record 268 MB fp32 > 129 MB)"}
+           "l2": l2_note(w)}
     return cfg
 
 
@@ -269,7 +295,7 @@ def main():
     dev = torch.device("cuda", local)
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
-    w = S.workload(args.workload)
+    w = S.workload(args.workload, **({"N": args.n_samples} if args.n_samples else {}))
     w["name"] = args.workload
     Y, f_true, *_ = S.record(w, np.float32)
     l, N = Y.shape
@@ -312,11 +338,8 @@ def main():
     stage_ms, stage_cnt, launches = ctx.profile_read()
     step_ms = [ev[s].elapsed_time(ev[s + 1]) for s in range(args.steps)]
     total_ms = ev[0].elapsed_time(ev[args.steps])
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * args.steps / (total_ms / 1e3)
+    total_ms = max_over_ranks(total_ms, dev)
+    value = whole_job_rate(args.steps, world, total_ms)
 
     # sanity: the record's modes are found
     rec = P.poles_to_numpy(poles)
@@ -380,14 +403,9 @@ def main():
             P._lib.lib.ssi_release(ctx.ptr, jid.value)
             if s >= 2:
                 lat.append(lu.value / 1e3)
-        if world > 1:
-            t = torch.tensor([sum(lat)], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            tot = float(t.item())
-        else:
-            tot = sum(lat)
+        tot = max_over_ranks(sum(lat), dev)
         if rank == 0:
-            out["e2e"] = {"value": world * len(lat) / (tot / 1e3), "unit": "solves/s",
+            out["e2e"] = {"value": whole_job_rate(len(lat), world, tot), "unit": "solves/s",
                           "h2d_bytes_per_step": int(l * N * 4),
                           "d2h_bytes_per_step": int(n_slots * P._lib.POLE_BYTES + phi_floats * 4),
                           "latency_ms": {"p50": pct(lat, 50), "p99": pct(lat, 99)},

@@ -19,7 +19,7 @@ __all__ = [
     "Context", "PREC", "ssi_covariances", "ssi_gaussian_omega", "ssi_toeplitz_rsvd",
     "ssi_realize_batch", "ssi_stabilize", "ssi_solve", "ssi_pole_slots", "poles_to_numpy",
     "stab_params", "job_desc", "ssi_rank_rule", "ssi_lag_rule", "ssi_time_lag", "check_sync",
-    "ssi_job_sizes",
+    "ssi_job_sizes", "ssi_serve_config", "ssi_submit", "ssi_poll", "ssi_release",
 ]
 
 PREC = {"fp32": SSI_PREC_FP32, "split_bf16": SSI_PREC_SPLIT_BF16}
@@ -45,6 +45,7 @@ class Context:
     def __init__(self, device: int = 0, hbm_budget_bytes: int = 0):
         self.device = device
         self.ptr = ctypes.c_void_p()
+        self._jobs = {}   # serving: job id -> descriptor kept alive until ssi_release
         check(lib.ssi_create(ctypes.byref(self.ptr), device, hbm_budget_bytes), "ssi_create")
 
     def close(self):
@@ -193,6 +194,41 @@ def ssi_solve(ctx: Context, desc: SsiJobDesc, device="cuda", with_s: bool = True
                         ctypes.c_void_p(S.data_ptr() if S is not None else 0),
                         _stream(torch.device(device))), "ssi_solve")
     return poles, phi, S
+
+
+def ssi_serve_config(ctx: Context, max_slots: int = 2, max_queue: int = 64) -> None:
+    check(lib.ssi_serve_config(ctx.ptr, max_slots, max_queue), "ssi_serve_config")
+
+
+def ssi_submit(ctx: Context, desc: SsiJobDesc) -> int:
+    """Queue a job; the descriptor (and a device record it points to) is kept alive by
+    the context until ssi_release."""
+    jid = ctypes.c_uint64()
+    check(lib.ssi_submit(ctx.ptr, ctypes.byref(desc), ctypes.byref(jid)), "ssi_submit")
+    ctx._jobs[jid.value] = desc
+    return jid.value
+
+
+def ssi_poll(ctx: Context, job_id: int, timeout_ms: int = -1):
+    """Wait for a job; returns (pole records as a numpy structured array, phi float32
+    array (slots x l x 2), latency in microseconds).  The arrays are copies."""
+    pp, ff = ctypes.c_void_p(), ctypes.c_void_p()
+    ns, lat = ctypes.c_int64(), ctypes.c_double()
+    check(lib.ssi_poll(ctx.ptr, job_id, timeout_ms, ctypes.byref(pp), ctypes.byref(ff),
+                       ctypes.byref(ns), ctypes.byref(lat)), "ssi_poll")
+    desc = ctx._jobs[job_id]
+    n = ns.value
+    raw = ctypes.string_at(pp.value, n * _lib.POLE_BYTES) if n else b""
+    rec = np.frombuffer(raw, dtype=_POLE_DTYPE).copy()
+    nf = n * desc.l * 2
+    phi = np.ctypeslib.as_array(ctypes.cast(ff.value, ctypes.POINTER(ctypes.c_float)),
+                                shape=(nf,)).copy() if nf else np.zeros(0, np.float32)
+    return rec, phi.reshape(n, desc.l, 2), lat.value
+
+
+def ssi_release(ctx: Context, job_id: int) -> None:
+    check(lib.ssi_release(ctx.ptr, job_id), "ssi_release")
+    ctx._jobs.pop(job_id, None)
 
 
 _POLE_DTYPE = np.dtype([("f_hz", "<f4"), ("xi", "<f4"), ("mu_re", "<f4"), ("mu_im", "<f4"),

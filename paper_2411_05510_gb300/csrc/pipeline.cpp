@@ -50,11 +50,11 @@ JobPlan plan_job(const ssi_job_desc* j, int num_sms) {
   ws = std::max(ws, p.rz.ws_bytes);
   p.ws_bytes = ws;
   WsPlan b;
+  b.add<int>(64);                                              // device status words
   b.add<double>((size_t)p.max_lag * j->l * j->l);             // R
   for (int t = 0; t < j->n_lags; ++t) b.add<float>((size_t)j->l * j->lags[t] * j->k);  // U_t
   b.add<float>((size_t)j->n_lags * j->k);                      // S
   if (j->y_on_host) b.add<float>((size_t)j->l * j->N);        // device copy of Y
-  b.add<int>(64);                                              // device status word
   p.buf_bytes = b.bytes;
   p.n_slots = p.rz.slots_per_lag * j->n_lags;
   p.phi_floats = p.n_slots * 2 * j->l;
@@ -67,12 +67,14 @@ ssi_status run_job(ssi_ctx* ctx, const ssi_job_desc* j, const JobPlan& p, JobBuf
   Workspace carve;
   carve.base = static_cast<char*>(B.buf);
   carve.cap = B.buf_cap;
+  // the status words first: their address must not depend on the job's sizes, because
+  // they are cleared only when the buffer is allocated and then reset by each read
+  int* status = carve.take<int>(64);
   double* R = carve.take<double>((size_t)p.max_lag * j->l * j->l);
   std::vector<float*> U(j->n_lags);
   for (int t = 0; t < j->n_lags; ++t) U[t] = carve.take<float>((size_t)j->l * j->lags[t] * j->k);
   float* S = carve.take<float>((size_t)j->n_lags * j->k);
   float* Ydev = j->y_on_host ? carve.take<float>((size_t)j->l * j->N) : nullptr;
-  int* status = carve.take<int>(64);
   if (!R || !S || !status || (j->y_on_host && !Ydev)) {
     set_error("solve: job buffers too small");
     return SSI_E_NOMEM;

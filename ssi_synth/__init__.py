@@ -32,7 +32,7 @@ import scipy.signal
 __all__ = [
     "shear_chain", "rayleigh_damping", "modal_damping", "DiscreteModel",
     "chain_state_space", "simulate", "stationary_state_cov", "model_covariances",
-    "BridgeRecord", "bridge_record", "WORKLOADS", "workload",
+    "BridgeRecord", "bridge_record", "WORKLOADS", "workload", "serving_mix",
 ]
 
 
@@ -323,3 +323,26 @@ def record(w: dict, dtype=np.float64):
     rec = bridge_record(w["l"], w["modes"], w["f_lo"], w["f_hi"], w["fs"], w["N"], w["noise"],
                         w["seed"], dtype)
     return rec.Y, rec.f_true, rec.xi_true, rec.phi_true
+
+
+def serving_mix(n_jobs: int, seed: int = 4, channels=(16, 48, 96, 186), N_range=(30000, 360000),
+                i_range=(20, 80), modes_range=(5, 30)):
+    """Workload dicts of a heterogeneous job stream (bridge records of uneven size).
+
+    Per job: l uniform over ``channels``; N, i and the number of modes uniform
+    integers in their ranges; frequencies and damping as in ``bridge_record``;
+    orders 2..2m+40 step 2 with k = the largest order, oversampling 20, q = 2.
+    Each job has its own record seed.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    jobs = []
+    for j in range(n_jobs):
+        l = int(rng.choice(channels))
+        N = int(rng.integers(N_range[0], N_range[1] + 1))
+        i = int(rng.integers(i_range[0], i_range[1] + 1))
+        m = int(rng.integers(modes_range[0], modes_range[1] + 1))
+        n_max = 2 * m + 40
+        jobs.append(dict(kind="bridge", l=l, modes=m, f_lo=1.0, f_hi=20.0, fs=100.0, N=N,
+                         noise=0.05, seed=1000 * seed + j, lags=[i], k=n_max, oversample=20, q=2,
+                         orders=list(range(2, n_max + 1, 2))))
+    return jobs

@@ -199,3 +199,53 @@ def test_full_solve_chain_matches_oracle(P, ctx, prec):
         for r, f0 in enumerate(f_true):
             j = nearest(cell, f0, phi_true[:, r])
             assert j is not None and abs(cell["f"][j] - f0) / f0 < 1e-2, (n, r)
+
+
+def test_3d_diagram_matches_oracle(P, ctx):
+    """3D stabilization diagram of a reduced bridge record (24 channels, 6 modes in
+    4-20 Hz, N = 60000, lags 14, 18, 22, RSVD k = 32 + 16 with q = 2, orders 2..32, one
+    solve): each lag against the oracle's FP64 RSVD with the same Omega at its separated
+    orders, and the stability flags of the matched true-mode poles."""
+    w = S.workload("bridge186_3d", l=24, modes=6, f_lo=4.0, N=60000, lags=[14, 18, 22], k=32,
+                   oversample=16, orders=list(range(2, 33, 2)))
+    Y, f_true, _, phi_true = S.record(w, np.float32)
+    desc = P.job_desc(torch.from_numpy(Y).cuda(), w["fs"], w["lags"], w["orders"], k=w["k"],
+                      oversample=w["oversample"], q=w["q"], prec="split_bf16", seed=5)
+    poles, phi, Sg = P.ssi_solve(ctx, desc)
+    P.check_sync(ctx)
+    rec = P.poles_to_numpy(poles)
+    gpu = gpu_cells(rec, phi.cpu().numpy(), w["lags"], w["orders"], w["l"])
+    ora, sv = O.ssi_solve(Y.astype(np.float64), w["fs"], w["lags"], w["orders"], k=w["k"],
+                          oversample=w["oversample"], q=w["q"], seed=5)
+    n_cmp_total, n_flag = 0, 0
+    gates = [separated_orders(w["orders"], sv[t]) for t in range(len(w["lags"]))]
+    for t in range(len(w["lags"])):
+        s_gpu = Sg.cpu().numpy()[t].astype(np.float64)
+        assert np.allclose(s_gpu[:12], sv[t][:12], rtol=1e-4), t
+        gate = gates[t]
+        assert 12 in gate, (t, gate)
+        n_cmp, _ = compare_parity_set([gpu[t]], [ora[t]], f_true, w["orders"], 6, min_matches=6,
+                                      phi_true=phi_true, gate_orders=gate)
+        n_cmp_total += n_cmp
+        # stability flags of the matched true-mode poles: HC always; stable-along-orders
+        # when the previous order is separated too, stable-along-lags when the same order
+        # of the previous lag is (then every pole those neighbour cells hold is
+        # reproducible); the first lag has no lag neighbour on either side
+        for m, n in enumerate(w["orders"]):
+            if n not in gate:
+                continue
+            for r, f0 in enumerate(f_true):
+                a = nearest(ora[t][m], f0, phi_true[:, r])
+                b = nearest(gpu[t][m], f0, phi_true[:, r])
+                if a is None or b is None:
+                    continue
+                fa, fb = int(ora[t][m]["flags"][a]), int(gpu[t][m]["flags"][b])
+                bits = O.ST_HC
+                if (n - 2) in gate:
+                    bits |= O.ST_ORDER
+                if t == 0 or n in gates[t - 1]:
+                    bits |= O.ST_LAG
+                assert fa & bits == fb & bits, (t, n, r, fa, fb)
+                n_flag += 1 + (t > 0 and n in gates[t - 1])
+    assert n_cmp_total >= 18
+    assert n_flag >= 24
