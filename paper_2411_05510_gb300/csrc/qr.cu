@@ -8,7 +8,7 @@
 // (block classical Gram-Schmidt with re-orthogonalisation, each panel made
 // orthonormal by Cholesky-QR).  The Gram matrices are accumulated in double-FP32
 // (error-free products with fma, two-sum accumulation) and reduced in FP64, the
-// 32x32 Cholesky runs in FP64 redundantly in every CTA, so a panel with condition
+// first 32x32 Cholesky runs in FP64 redundantly in every CTA, so a panel with condition
 // number up to ~1e7 is orthonormalised to FP32 precision.  Grid-wide reductions
 // use a two-phase barrier (partials -> sliced sums -> broadcast); every barrier
 // wait is bounded and sets the status word when it runs out.
@@ -131,12 +131,15 @@ __device__ void chol_warp_f32(const double* G, int w, double* R, double* rdiag, 
   __syncwarp();
 }
 
-// Cholesky of the w x w Gram matrix G (FP64, upper triangle used) by the whole CTA:
-// R[j][j] = sqrt(d_j), R[j][c] = G'[j][c] / R[j][j], trailing update of the upper triangle.
-// Reciprocal square roots replace divisions (FP64 division and square root are long
-// instruction sequences on this part).  Writes R (upper) and 1 / R[j][j].
+// Cholesky of the w x w Gram matrix G (FP64, upper triangle used) by the whole CTA.  Per
+// step j, thread 0 forms 1/R[j][j] (reciprocal square root: FP32 seed and two Newton
+// steps in FP64, since FP64 division and square root are long instruction sequences on
+// this part); then, between the same two barriers, row j of R is written
+// (R[j][c] = G[j][c] / R[j][j]) and the trailing upper triangle is updated from the
+// unscaled row (G[a][c] -= G[j][a] G[j][c] / R[j][j]^2).  Warps take rows, lanes
+// columns.  Writes R (upper, zero elsewhere) and 1 / R[j][j].
 __device__ void chol_cta(double* G, int w, double* R, double* rdiag) {
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nwarps = QR_THREADS / 32;
   __shared__ double s_floor;
   if (tid == 0) {
     double gmax = 0.0;
@@ -147,8 +150,6 @@ __device__ void chol_cta(double* G, int w, double* R, double* rdiag) {
   __syncthreads();
   for (int j = 0; j < w; ++j) {
     if (tid == 0) {
-      // 1/sqrt(d): FP32 seed and one Newton step in FP64 (relative error ~1e-14); the FP64
-      // library square root and division are long instruction sequences on this part
       const double d = fmax(G[j * PB + j], s_floor);
       double y = (double)rsqrtf((float)d);
       y = y * (1.5 - 0.5 * d * y * y);
@@ -157,19 +158,18 @@ __device__ void chol_cta(double* G, int w, double* R, double* rdiag) {
       R[j * PB + j] = d * y;
     }
     __syncthreads();
-    const double rs = rdiag[j];
-    for (int c = j + 1 + tid; c < w; c += QR_THREADS) R[j * PB + c] = G[j * PB + c] * rs;
-    __syncthreads();
-    const int m = w - j - 1;
-    for (int e = tid; e < m * m; e += QR_THREADS) {
-      const int a = j + 1 + e / m, c = j + 1 + e % m;
-      if (c >= a) G[a * PB + c] -= R[j * PB + a] * R[j * PB + c];
+    const double rs = rdiag[j], rs2 = rs * rs;
+    if (warp == 0 && lane > j && lane < w) R[j * PB + lane] = G[j * PB + lane] * rs;
+    const int c = lane;
+    if (c > j && c < w) {
+      const double gjc = G[j * PB + c] * rs2;
+      for (int a = j + 1 + warp; a <= c; a += nwarps) G[a * PB + c] -= G[j * PB + a] * gjc;
     }
     __syncthreads();
   }
 }
 
-__global__ void __launch_bounds__(QR_THREADS)
+__global__ void __launch_bounds__(QR_THREADS, 1)   // one CTA per SM (cooperative grid)
     k_qr_bcgs2(QrParams p) {
   extern __shared__ float s_rows[];     // this CTA's rows (when they fit), leading dim p.lds
   __shared__ double sG[PB * PB];

@@ -22,6 +22,7 @@
 //                 pole parameters, MPC and MPD.  Largest orders are scheduled first.
 #include <cfloat>
 
+#include "blackwell.cuh"
 #include "common.cuh"
 
 namespace ssi {
@@ -29,7 +30,7 @@ namespace ssi {
 namespace {
 
 constexpr int MAX_LAGS = 64;
-constexpr int EIG_THREADS = 256;
+constexpr int EIG_THREADS = 512;
 constexpr int GR_ROWS = 512;      // rows per Gram chunk
 constexpr int SMEM_N_MAX = 224;   // largest order whose A fits shared memory
 
@@ -111,92 +112,111 @@ __global__ void k_gram_reduce(const float* __restrict__ partial, int n_lags, int
 }
 
 // ------------------------------------------------------------------ per-lag factorisation
-// GH[t] = [G | H] (2 x k x k); out RM[t] = [Rinv | M] (2 x k x k).
+// GH[t] = [G | H] (2 x k x k); out RM[t] = [Rinv | M] (2 x k x k) with G = R^T R and
+// M = R^{-T} H.  One CTA per lag, R in shared memory (row stride k + 1):
+//   1. right-looking Cholesky on the upper triangle (warp 0 scales row j, then all
+//      threads update the trailing triangle);
+//   2. R^{-1} in place, column by column (column j from the inverted leading block and
+//      a copy of R's column j);
+//   3. M = R^{-T} H = (R^{-1})^T H with 4 x 4 outputs per thread.
 __global__ void __launch_bounds__(1024)
     k_lag_factor(const float* __restrict__ GH, int k, float* __restrict__ RM, int* status) {
-  extern __shared__ float sR[];   // k x k, Cholesky factor (upper)
+  extern __shared__ float sR[];   // k x (k+1), then a column buffer of k floats
+  const int ldr = k + 1;
+  float* col = sR + (size_t)k * ldr;
   const int t = blockIdx.x;
   const float* G = GH + (size_t)t * 2 * k * k;
   const float* H = G + (size_t)k * k;
   float* Rinv = RM + (size_t)t * 2 * k * k;
   float* M = Rinv + (size_t)k * k;
-  const int tid = threadIdx.x, nth = blockDim.x;
-  for (int e = tid; e < k * k; e += nth) sR[e] = G[e];
-  __syncthreads();
-  __shared__ float s_d;
+  const int tid = threadIdx.x, nth = blockDim.x, warp = tid >> 5, lane = tid & 31,
+            nwarps = nth >> 5;
+  __shared__ float s_red[32];
   float gmax = 0.f;
-  for (int j = 0; j < k; ++j) gmax = fmaxf(gmax, G[(size_t)j * k + j]);
-  const float floor_v = fmaxf(gmax * 1e-10f, FLT_MIN);
-  // right-looking Cholesky on the upper triangle: row j of R
+  for (int e = tid; e < k * k; e += nth) {
+    const int r = e / k, c = e % k;
+    const float v = G[e];
+    sR[r * ldr + c] = v;
+    if (r == c) gmax = fmaxf(gmax, v);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) gmax = fmaxf(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
+  if (lane == 0) s_red[warp] = gmax;
+  __syncthreads();
+  if (tid == 0) {
+    float g = 0.f;
+    for (int w2 = 0; w2 < nwarps; ++w2) g = fmaxf(g, s_red[w2]);
+    s_red[0] = g;
+  }
+  __syncthreads();
+  const float floor_v = fmaxf(s_red[0] * 1e-10f, FLT_MIN);
+  // 1. Cholesky: row j of R
   for (int j = 0; j < k; ++j) {
-    if (tid == 0) {
-      float d = sR[j * k + j];
+    if (warp == 0) {
+      float d = sR[j * ldr + j];
       if (!(d > floor_v)) {
-        atomicOr(status, DEV_NOTCONVERGED);
+        if (lane == 0) atomicOr(status, DEV_NOTCONVERGED);
         d = floor_v;
       }
-      s_d = sqrtf(d);
-      sR[j * k + j] = s_d;
+      d = sqrtf(d);
+      const float id = 1.f / d;
+      for (int c = j + 1 + lane; c < k; c += 32) sR[j * ldr + c] *= id;
+      if (lane == 0) sR[j * ldr + j] = d;
     }
     __syncthreads();
-    const float d = s_d;
-    for (int c = j + 1 + tid; c < k; c += nth) sR[j * k + c] /= d;
-    __syncthreads();
-    // trailing update of the upper triangle: G[a][c] -= R[j][a] R[j][c], j < a <= c
-    const int m = k - j - 1;
-    for (int e = tid; e < m * m; e += nth) {
-      const int a = j + 1 + e / m, c = j + 1 + e % m;
-      if (c >= a) sR[a * k + c] -= sR[j * k + a] * sR[j * k + c];
+    // G[a][c] -= R[j][a] R[j][c], j < a <= c: warps along rows, lanes along columns
+    for (int a = j + 1 + warp; a < k; a += nwarps) {
+      const float ra = sR[j * ldr + a];
+      for (int c = a + lane; c < k; c += 32) sR[a * ldr + c] -= ra * sR[j * ldr + c];
     }
     __syncthreads();
   }
-  // Rinv by column back substitution and M = R^{-T} H by forward substitution; one warp
-  // per column, the column held in registers across the lanes (entry j on lane j % 32)
-  const int warp = tid >> 5, lane = tid & 31, nwarps = nth >> 5;
-  constexpr int KJ = 8;   // k <= 256
-  for (int c = warp; c < k; c += nwarps) {
-    float x[KJ];
-#pragma unroll
-    for (int q = 0; q < KJ; ++q) x[q] = 0.f;
-    for (int r = c; r >= 0; --r) {
-      float part = 0.f;
-#pragma unroll
-      for (int q = 0; q < KJ; ++q) {
-        const int j = lane + 32 * q;
-        if (j > r && j <= c) part = fmaf(sR[r * k + j], x[q], part);
+  // 2. R^{-1} in place: column j = -(1/R[j][j]) Rinv[0:j, 0:j] R[0:j, j], Rinv[j][j] = 1/R[j][j]
+  for (int j = 0; j < k; ++j) {
+    for (int i = tid; i < j; i += nth) col[i] = sR[i * ldr + j];
+    __syncthreads();
+    const float inv = 1.f / sR[j * ldr + j];
+    for (int i = tid; i < j; i += nth) {
+      float a0 = 0.f, a1 = 0.f;
+      int m = i;
+      for (; m + 1 < j; m += 2) {
+        a0 = fmaf(sR[i * ldr + m], col[m], a0);
+        a1 = fmaf(sR[i * ldr + m + 1], col[m + 1], a1);
       }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-      const float v = ((r == c) ? 1.f - part : -part) / sR[r * k + r];
-      if (lane == (r & 31)) x[r >> 5] = v;
+      if (m < j) a0 = fmaf(sR[i * ldr + m], col[m], a0);
+      sR[i * ldr + j] = -(a0 + a1) * inv;
     }
-#pragma unroll
-    for (int q = 0; q < KJ; ++q) {
-      const int j = lane + 32 * q;
-      if (j < k) Rinv[(size_t)j * k + c] = (j <= c) ? x[q] : 0.f;
-    }
+    __syncthreads();
+    if (tid == 0) sR[j * ldr + j] = inv;
   }
-  for (int c = warp; c < k; c += nwarps) {
-    float x[KJ];
+  __syncthreads();
+  for (int e = tid; e < k * k; e += nth) {
+    const int r = e / k, c = e % k;
+    Rinv[e] = (c >= r) ? sR[r * ldr + c] : 0.f;
+  }
+  // 3. M[j][c] = sum_{r <= j} Rinv[r][j] H[r][c]
+  const int k4 = (k + 3) / 4;
+  for (int task = tid; task < k4 * k4; task += nth) {
+    const int j0 = 4 * (task / k4), c0 = 4 * (task % k4);
+    float acc[4][4] = {};
+    const int rmax = min(j0 + 3, k - 1);
+    for (int r = 0; r <= rmax; ++r) {
+      float ri[4], hv[4];
 #pragma unroll
-    for (int q = 0; q < KJ; ++q) x[q] = 0.f;
-    for (int r = 0; r < k; ++r) {
-      float part = 0.f;
-#pragma unroll
-      for (int q = 0; q < KJ; ++q) {
-        const int j = lane + 32 * q;
-        if (j < r) part = fmaf(sR[j * k + r], x[q], part);
+      for (int u = 0; u < 4; ++u) {
+        ri[u] = (j0 + u < k && r <= j0 + u) ? sR[r * ldr + j0 + u] : 0.f;
+        hv[u] = (c0 + u < k) ? __ldg(H + (size_t)r * k + c0 + u) : 0.f;
       }
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-      const float v = (H[(size_t)r * k + c] - part) / sR[r * k + r];
-      if (lane == (r & 31)) x[r >> 5] = v;
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc[a][u] = fmaf(ri[a], hv[u], acc[a][u]);
     }
 #pragma unroll
-    for (int q = 0; q < KJ; ++q) {
-      const int j = lane + 32 * q;
-      if (j < k) M[(size_t)j * k + c] = x[q];
-    }
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (j0 + a < k && c0 + u < k) M[(size_t)(j0 + a) * k + c0 + u] = acc[a][u];
   }
 }
 
@@ -211,22 +231,51 @@ struct EigParams {
   float* work;               // per-realisation scratch
   long long work_off[512];   // offset of order m's scratch within a lag's scratch
   long long work_per_lag;
-  int xbuf_off;              // floats: start of the per-warp eigenvector buffers in shared memory
+  int xbuf_off;              // floats: start of the vector buffers (8 warps x 2 nmax) in shared memory
   int log_off;               // floats: start of the reflector staging buffer in shared memory
   int nmax;                  // largest order of the launch
   double dt;
   ssi_pole* poles;
   float* phi;
   int* status;
+  int vec_blocks[512];       // eigenvector blocks of order m (k_eig_vectors)
+  int vec_blocks_per_lag;
 };
 
-// scratch of one realisation of order n: Hessenberg v's (n*n), reflector log, X (n*n)
-// scratch of one realisation of order n: Hessenberg reflectors (n*n), the log of window
-// transformations (zlog_cap(n) entries of ZREC floats), eigenvector matrix X (n*n)
-constexpr int ZREC = 32 * 32 + 8;   // one window: b, e, then the 32 x 32 factor row-major
+// scratch of one realisation of order n: a header (poles, windows, failure flag), the
+// Householder vectors of the Hessenberg reduction (n*n), the eigenvectors of T (n*n) and the
+// log of the QR iteration's window factors (zlog_cap(n) records of ZREC floats: b, e, then
+// the WN x WN factor row-major)
+constexpr int EIG_HDR = 64;
+constexpr int ZREC = WN * WN + 8;
 __host__ __device__ inline long long zlog_cap(int n) { return (long long)n * n / 16 + 2LL * n + 64; }
 __host__ __device__ inline long long eig_work_floats(int n, int) {
-  return (long long)n * n + zlog_cap(n) * ZREC + (long long)n * n + 64;
+  return EIG_HDR + 2LL * n * n + zlog_cap(n) * ZREC + 64;
+}
+constexpr int VEC_COLS = 32;   // columns of X per eigenvector block (16 poles)
+
+// Bounded wait (2 s of %globaltimer) of a whole warp until *x >= v; the result is the
+// same in every lane.  On timeout the status word gets DEV_TIMEOUT from the caller.
+__device__ __forceinline__ bool warp_wait_geq(volatile int* x, int v) {
+  bool ok = true;
+  if (*x < v) {
+    const uint64_t t0 = bw::global_ns();
+    while (*x < v) {
+      if (bw::global_ns() - t0 > 2000000000ull) {
+        ok = false;
+        break;
+      }
+      __nanosleep(32);
+    }
+  }
+  ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+  __threadfence_block();
+  return ok;
+}
+
+// barrier of the helper warps only (named barrier 1; barrier 0 is __syncthreads)
+__device__ __forceinline__ void helper_sync(int nthreads) {
+  asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
 }
 
 __device__ __forceinline__ float sgnf(float a, float b) { return b >= 0.f ? fabsf(a) : -fabsf(a); }
@@ -243,9 +292,10 @@ __global__ void __launch_bounds__(EIG_THREADS)
   const int tid = threadIdx.x, nth = blockDim.x;
   const int ld = n + 1;   // padded leading dimension against bank conflicts
   float* work = p.work + (size_t)t * p.work_per_lag + p.work_off[mi];
-  float* hv = work;                           // Hessenberg reflectors: n x n (v, beta in [j*n + n-1])
-  float* zlog = hv + (size_t)n * n;           // window transformations of the QR sweeps
-  float* X = zlog + zlog_cap(n) * ZREC;       // eigenvector matrix, n x (2 m)
+  int* hdr = reinterpret_cast<int*>(work);    // 0 poles, 1 windows, 2 failed
+  float* hv = work + EIG_HDR;                 // Hessenberg reflectors: n x n (v, beta in [j*n + n-1])
+  float* X = hv + (size_t)n * n;              // eigenvectors of T, n x (2 m)
+  float* zlog = X + (size_t)n * n;            // window factors of the QR iteration
   float* A = smem;                            // n x (n+1), orders <= SMEM_N_MAX
   __shared__ float sh[16];
   __shared__ int shi[16];
@@ -253,9 +303,7 @@ __global__ void __launch_bounds__(EIG_THREADS)
   __shared__ float s_mur[256], s_mui[256];
   const float* Rinv = p.RM + (size_t)t * 2 * k * k;
   const float* M = Rinv + (size_t)k * k;
-  const float* U = p.lt.U[t];
   ssi_pole* poles = p.poles + (size_t)t * p.slots_per_lag + p.slot_off[mi];
-  float* phi_out = p.phi + ((size_t)t * p.slots_per_lag + p.slot_off[mi]) * 2 * l;
   const int n_slots = n / 2;
 
   // ---- 1. A~_n = Rinv[:n,:n] M[:n,:n] (Rinv upper triangular); 1 x 4 strips per thread
@@ -283,7 +331,7 @@ __global__ void __launch_bounds__(EIG_THREADS)
 
   // ---- 2. Householder reduction to upper Hessenberg form (v kept in shared memory and
   //         logged to global memory for the back transformation)
-  float* sv = smem + p.xbuf_off;   // n floats (the eigenvector buffers are not in use yet)
+  float* sv = smem + p.xbuf_off;   // n floats (the vector buffers are not in use yet)
   __shared__ float s_part[EIG_THREADS / 32];
   for (int j = 0; j + 2 < n; ++j) {
     const int len = n - j - 1;
@@ -320,37 +368,50 @@ __global__ void __launch_bounds__(EIG_THREADS)
     if (beta != 0.f) {
       float* __restrict__ Ar = A;
       const float* __restrict__ vr = sv;
+      // tpc consecutive lanes share one column (row) and split its dot product, as many
+      // as keep about all threads busy; loop bounds are warp-uniform around the shuffles
+      int tpc = 1;
+      while (tpc < 8 && len * tpc * 2 <= nth) tpc *= 2;
+      const int grp = tid / tpc, sub = tid % tpc, ngrp = nth / tpc;
       // left: A[j+1:, c] -= beta v (v^T A[j+1:, c]) for c > j (column j is set below)
-      for (int c = j + 1 + tid; c < n; c += nth) {
-        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-        int r = 0;
-        for (; r + 3 < len; r += 4) {
-          s0 = fmaf(vr[r], Ar[(j + 1 + r) * ld + c], s0);
-          s1 = fmaf(vr[r + 1], Ar[(j + 2 + r) * ld + c], s1);
-          s2 = fmaf(vr[r + 2], Ar[(j + 3 + r) * ld + c], s2);
-          s3 = fmaf(vr[r + 3], Ar[(j + 4 + r) * ld + c], s3);
+      for (int base = 0; base < len; base += ngrp) {
+        const int c = j + 1 + base + grp;
+        const bool act = base + grp < len;
+        float s0 = 0.f, s1 = 0.f;
+        if (act) {
+          int r = sub;
+          for (; r + tpc < len; r += 2 * tpc) {
+            s0 = fmaf(vr[r], Ar[(j + 1 + r) * ld + c], s0);
+            s1 = fmaf(vr[r + tpc], Ar[(j + 1 + r + tpc) * ld + c], s1);
+          }
+          if (r < len) s0 = fmaf(vr[r], Ar[(j + 1 + r) * ld + c], s0);
         }
-        for (; r < len; ++r) s0 = fmaf(vr[r], Ar[(j + 1 + r) * ld + c], s0);
-        const float sc = (s0 + s1 + s2 + s3) * beta;
-#pragma unroll 4
-        for (r = 0; r < len; ++r) Ar[(j + 1 + r) * ld + c] -= sc * vr[r];
+        float sc = s0 + s1;
+        for (int o = tpc >> 1; o > 0; o >>= 1) sc += __shfl_xor_sync(0xffffffffu, sc, o);
+        sc *= beta;
+        if (act)
+          for (int r = sub; r < len; r += tpc) Ar[(j + 1 + r) * ld + c] -= sc * vr[r];
       }
       __syncthreads();
       // right: A[r, j+1:] -= beta (A[r, j+1:] v) v^T for all rows
-      for (int r = tid; r < n; r += nth) {
-        float* __restrict__ row = Ar + r * ld + j + 1;
-        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-        int c = 0;
-        for (; c + 3 < len; c += 4) {
-          s0 = fmaf(row[c], vr[c], s0);
-          s1 = fmaf(row[c + 1], vr[c + 1], s1);
-          s2 = fmaf(row[c + 2], vr[c + 2], s2);
-          s3 = fmaf(row[c + 3], vr[c + 3], s3);
+      for (int base = 0; base < n; base += ngrp) {
+        const int r = base + grp;
+        const bool act = r < n;
+        float* __restrict__ row = Ar + (act ? r : 0) * ld + j + 1;
+        float s0 = 0.f, s1 = 0.f;
+        if (act) {
+          int c = sub;
+          for (; c + tpc < len; c += 2 * tpc) {
+            s0 = fmaf(row[c], vr[c], s0);
+            s1 = fmaf(row[c + tpc], vr[c + tpc], s1);
+          }
+          if (c < len) s0 = fmaf(row[c], vr[c], s0);
         }
-        for (; c < len; ++c) s0 = fmaf(row[c], vr[c], s0);
-        const float sc = (s0 + s1 + s2 + s3) * beta;
-#pragma unroll 4
-        for (c = 0; c < len; ++c) row[c] -= sc * vr[c];
+        float sc = s0 + s1;
+        for (int o = tpc >> 1; o > 0; o >>= 1) sc += __shfl_xor_sync(0xffffffffu, sc, o);
+        sc *= beta;
+        if (act)
+          for (int c = sub; c < len; c += tpc) row[c] -= sc * vr[c];
       }
       __syncthreads();
       for (int r = 1 + tid; r <= len; r += nth) A[(j + r) * ld + j] = (r == 1) ? sh[0] : 0.f;
@@ -358,295 +419,365 @@ __global__ void __launch_bounds__(EIG_THREADS)
     __syncthreads();
   }
 
-  // ---- 3b. Francis double-shift QR to real Schur form (full T), windowed.
-  //  The bulge of each sweep is chased by warp 0 inside a window of WN rows/columns;
-  //  in-window rows and columns are updated at once and the window's transformations
-  //  accumulate in Zb (WN x WN).  After each window all threads apply Zb to the rows
-  //  right of the window (H[b:e, e:n] = Zb^T H[b:e, e:n]) and to the rows above it
-  //  (H[0:b, b:e] = H[0:b, b:e] Zb), and Zb is logged for the back transformation of
-  //  the eigenvectors.  Same arithmetic as the unwindowed sweep.
-  float* Zbuf = smem + p.log_off;     // 2 buffers of WN x (WN + 4) (16-byte aligned rows)
-  __shared__ int s_ctl[8];            // 0 b, 1 e, 2 kend, 3 state (0 run, 1 done, 2 failed), 4 pending buf, 5 pb, 6 pe
+
+  // ---- 3b. Francis double-shift QR iteration to real Schur form T = Z^T H Z (Martin,
+  //  Peters and Wilkinson's algorithm for real Hessenberg matrices, with their
+  //  exceptional shifts after 10 and 20 iterations), windowed and pipelined.
+  //  Warp 0 (the chaser) chases the bulge of each sweep inside windows of WN rows/columns,
+  //  updating in-window rows and columns at once and accumulating the window's
+  //  transformations in Zb (WN x WN).  The helpers (warps 1-15 except those sharing warp
+  //  0's scheduler: warps 4, 8, 12) apply each posted Zb to the rest of the matrix -- the
+  //  rows of the window right of it (H[b:e, e:n] = Zb^T H[b:e, e:n]) and the columns of
+  //  the window above it (H[0:b, b:e] = H[0:b, b:e] Zb) -- and log it to global memory
+  //  for the back transformation of the eigenvectors, while the chaser is in the next
+  //  window.  The next window overlaps the rows of the previous one in
+  //  three rows, so the chaser first does the previous window's right update in the
+  //  columns of the next window itself (the helpers skip them).  A sweep starts only when
+  //  every window has been applied.  Same arithmetic as the unwindowed sweep.  Hand-offs
+  //  are shared counters with bounded waits.
+  float* Zbuf = smem + p.log_off;     // 2 window factors, WN x (WN + 4) each (16-byte aligned rows)
+  float* ZT = smem + p.xbuf_off;      // the helpers' transposed factor (vector buffers idle here)
+  __shared__ volatile int s_posted, s_taken, s_applied, s_state, s_go, s_nwin;
+  __shared__ int s_desc[2][4];        // per factor buffer: b, e, kend, end of the chaser's columns
   __shared__ float s_sh[3];           // shift vector of the first step of the sweep
   if (tid == 0) {
-    s_ctl[3] = 0;
-    s_ctl[4] = -1;
-    s_ctl[7] = 0;   // windows logged
+    s_posted = 0;
+    s_taken = 0;
+    s_applied = 0;
+    s_state = 0;   // 0 running, 1 done, 2 failed
+    s_go = 0;
+    s_nwin = 0;
   }
   __syncthreads();
-  {
-    // warp-0 state (identical in every lane)
+  if (warp_id_of(tid) == 0) {
+    const int lane0 = tid;
     float anorm = 0.f;
-    int nn = n - 1, its = 0, total_its = 0, ll = 0, m = 0, b = 0, fail = 0, blk = 0;
-    bool in_sweep = false;
-    if (warp_id_of(tid) == 0) {
-      for (int e2 = tid; e2 < n * n; e2 += 32) {
-        const int r = e2 / n, c = e2 % n;
-        if (c >= r - 1) anorm += fabsf(A[r * ld + c]);
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) anorm += __shfl_xor_sync(0xffffffffu, anorm, o);
+    for (int e2 = lane0; e2 < n * n; e2 += 32) {
+      const int r = e2 / n, c = e2 % n;
+      if (c >= r - 1) anorm += fabsf(A[r * ld + c]);
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) anorm += __shfl_xor_sync(0xffffffffu, anorm, o);
+    if (lane0 == 0) sh[8] = anorm;
+    int nn = n - 1, its = 0, total_its = 0, ll = 0, m = 0, b = 0, fail = 0, wdx = 0;
+    bool in_sweep = false, cont = false;
     const int itmax = 30 * max(10, n);
     while (true) {
-      const int cur = blk & 1;
-      float* Zb = Zbuf + cur * WN * (WN + 4);
-      if (tid < 32) {
-        const int lane0 = tid;
-        // start a sweep when none is running: deflation and shift selection
-        while (!in_sweep && nn >= 0 && !fail) {
-          int l2 = 0;
-          for (int base = nn; base >= 1; base -= 32) {
-            const int cand = base - lane0;
-            bool small = false;
-            if (cand >= 1) {
-              float sd = fabsf(A[(cand - 1) * ld + cand - 1]) + fabsf(A[cand * ld + cand]);
-              if (sd == 0.f) sd = anorm;
-              small = fabsf(A[cand * ld + cand - 1]) <= FLT_EPSILON * sd;
-            }
-            const unsigned msk = __ballot_sync(0xffffffffu, small);
-            if (msk) {
-              l2 = base - (__ffs(msk) - 1);
-              break;
-            }
+      if (!in_sweep) {
+        // every posted window must be applied before the matrix is read outside a window
+        if (!warp_wait_geq(&s_applied, wdx)) { fail = 2; break; }
+      while (!in_sweep && nn >= 0 && !fail) {
+        int l2 = 0;
+        for (int base = nn; base >= 1; base -= 32) {
+          const int cand = base - lane0;
+          bool small = false;
+          if (cand >= 1) {
+            float sd = fabsf(A[(cand - 1) * ld + cand - 1]) + fabsf(A[cand * ld + cand]);
+            if (sd == 0.f) sd = anorm;
+            small = fabsf(A[cand * ld + cand - 1]) <= FLT_EPSILON * sd;
           }
-          __syncwarp();
-          if (l2 >= 1 && lane0 == 0) A[l2 * ld + l2 - 1] = 0.f;
-          __syncwarp();
-          if (l2 == nn) { nn -= 1; its = 0; continue; }
-          if (l2 == nn - 1) { nn -= 2; its = 0; continue; }
-          if (total_its >= itmax) { fail = 1; break; }
-          float x = A[nn * ld + nn], y = A[(nn - 1) * ld + nn - 1];
-          float w = A[nn * ld + nn - 1] * A[(nn - 1) * ld + nn];
-          if (its == 10 || its == 20) {
-            const float s = fabsf(A[nn * ld + nn - 1]) + fabsf(A[(nn - 1) * ld + nn - 2]);
-            x = y = 0.75f * s;
-            w = -0.4375f * s * s;
+          const unsigned msk = __ballot_sync(0xffffffffu, small);
+          if (msk) {
+            l2 = base - (__ffs(msk) - 1);
+            break;
           }
-          ++its;
-          ++total_its;
-          // start of the bulge: the largest mm in [l2, nn-2] where two consecutive
-          // subdiagonals are negligible relative to the shift vector (mm = l2 always
-          // qualifies); lanes test 32 candidates at a time
-          int mm = l2;
-          for (int base = nn - 2; base >= l2; base -= 32) {
-            const int cand = base - lane0;
-            bool ok = false;
-            if (cand >= l2) {
-              if (cand == l2) {
-                ok = true;
-              } else {
-                const float z = A[cand * ld + cand];
-                const float r2 = x - z, s2 = y - z;
-                float p0 = (r2 * s2 - w) / A[(cand + 1) * ld + cand] + A[cand * ld + cand + 1];
-                float q0 = A[(cand + 1) * ld + cand + 1] - z - r2 - s2;
-                float r0 = A[(cand + 2) * ld + cand + 1];
-                const float sc = fabsf(p0) + fabsf(q0) + fabsf(r0);
-                p0 /= sc; q0 /= sc; r0 /= sc;
-                const float u = fabsf(A[cand * ld + cand - 1]) * (fabsf(q0) + fabsf(r0));
-                const float v = fabsf(p0) * (fabsf(A[(cand - 1) * ld + cand - 1]) + fabsf(z) +
-                                             fabsf(A[(cand + 1) * ld + cand + 1]));
-                ok = u <= FLT_EPSILON * v;
-              }
-            }
-            const unsigned msk = __ballot_sync(0xffffffffu, ok);
-            if (msk) {
-              mm = base - (__ffs(msk) - 1);
-              break;
-            }
-          }
-          float pp, qq, rr;
-          {
-            const float z = A[mm * ld + mm];
-            const float r2 = x - z, s2 = y - z;
-            pp = (r2 * s2 - w) / A[(mm + 1) * ld + mm] + A[mm * ld + mm + 1];
-            qq = A[(mm + 1) * ld + mm + 1] - z - r2 - s2;
-            rr = A[(mm + 2) * ld + mm + 1];
-            const float sc = fabsf(pp) + fabsf(qq) + fabsf(rr);
-            pp /= sc; qq /= sc; rr /= sc;
-          }
-          __syncwarp();
-          for (int r = mm + 2 + lane0; r <= nn; r += 32) {
-            A[r * ld + r - 2] = 0.f;
-            if (r != mm + 2) A[r * ld + r - 3] = 0.f;
-          }
-          __syncwarp();
-          ll = l2;
-          m = mm;
-          b = mm;
-          if (lane0 == 0) { s_sh[0] = pp; s_sh[1] = qq; s_sh[2] = rr; }
-          in_sweep = true;
         }
         __syncwarp();
-        if (lane0 == 0) {
-          if (fail) s_ctl[3] = 2;
-          else if (!in_sweep) s_ctl[3] = 1;
+        if (l2 >= 1 && lane0 == 0) A[l2 * ld + l2 - 1] = 0.f;
+        __syncwarp();
+        if (l2 == nn) { nn -= 1; its = 0; continue; }
+        if (l2 == nn - 1) { nn -= 2; its = 0; continue; }
+        if (total_its >= itmax) { fail = 1; break; }
+        float x = A[nn * ld + nn], y = A[(nn - 1) * ld + nn - 1];
+        float w = A[nn * ld + nn - 1] * A[(nn - 1) * ld + nn];
+        if (its == 10 || its == 20) {
+          const float s = fabsf(A[nn * ld + nn - 1]) + fabsf(A[(nn - 1) * ld + nn - 2]);
+          x = y = 0.75f * s;
+          w = -0.4375f * s * s;
         }
-        if (in_sweep) {
-          // ---- chase one window: steps kk in [b, kend), window [b, e)
-          const int kend = min(b + WB, nn);
-          const int e = min(b + WN, n);
-          const int w = e - b;
-          for (int q = 0; q < WN; ++q) Zb[lane0 * (WN + 4) + q] = (q == lane0) ? 1.f : 0.f;
-          __syncwarp();
-          for (int kk = b; kk < kend; ++kk) {
-            const bool three = kk != nn - 1;
-            float pp, qq, rr, xs = 1.f;
-            bool go = true;
-            if (kk == m) {
-              pp = s_sh[0]; qq = s_sh[1]; rr = s_sh[2];
+        ++its;
+        ++total_its;
+        // start of the bulge: the largest mm in [l2, nn-2] where two consecutive
+        // subdiagonals are negligible relative to the shift vector (mm = l2 always
+        // qualifies); lanes test 32 candidates at a time
+        int mm = l2;
+        for (int base = nn - 2; base >= l2; base -= 32) {
+          const int cand = base - lane0;
+          bool ok = false;
+          if (cand >= l2) {
+            if (cand == l2) {
+              ok = true;
             } else {
-              pp = A[kk * ld + kk - 1];
-              qq = A[(kk + 1) * ld + kk - 1];
-              rr = three ? A[(kk + 2) * ld + kk - 1] : 0.f;
-              xs = fabsf(pp) + fabsf(qq) + fabsf(rr);
-              if (xs != 0.f) {
-                const float ix = __fdividef(1.f, xs);
-                pp *= ix; qq *= ix; rr *= ix;
-              } else {
-                go = false;
-              }
+              const float z = A[cand * ld + cand];
+              const float r2 = x - z, s2 = y - z;
+              float p0 = (r2 * s2 - w) / A[(cand + 1) * ld + cand] + A[cand * ld + cand + 1];
+              float q0 = A[(cand + 1) * ld + cand + 1] - z - r2 - s2;
+              float r0 = A[(cand + 2) * ld + cand + 1];
+              const float sc = fabsf(p0) + fabsf(q0) + fabsf(r0);
+              p0 /= sc; q0 /= sc; r0 /= sc;
+              const float u = fabsf(A[cand * ld + cand - 1]) * (fabsf(q0) + fabsf(r0));
+              const float v = fabsf(p0) * (fabsf(A[(cand - 1) * ld + cand - 1]) + fabsf(z) +
+                                           fabsf(A[(cand + 1) * ld + cand + 1]));
+              ok = u <= FLT_EPSILON * v;
             }
-            float s = 0.f, is = 0.f;
-            if (go) {
-              const float ss = pp * pp + qq * qq + rr * rr;
-              go = ss > 0.f;
-              if (go) {
-                const float rs = rsqrtf(ss);
-                s = sgnf(ss * rs, pp);
-                is = sgnf(rs, pp);
-              }
-            }
-            __syncwarp();
-            if (go) {
-              if (lane0 == 0) {
-                if (kk == m) {
-                  if (ll != m) A[kk * ld + kk - 1] = -A[kk * ld + kk - 1];
-                } else {
-                  A[kk * ld + kk - 1] = -s * xs;
-                }
-              }
-              pp += s;
-              const float ip = __fdividef(1.f, pp);
-              const float w0 = pp * is, w1 = qq * is, w2 = three ? rr * is : 0.f;
-              const float u1 = qq * ip, u2 = three ? rr * ip : 0.f;
-              // row modification inside the window: columns kk .. e-1
-              {
-                const int j = b + lane0;
-                if (j >= kk && j < e) {
-                  const float a0 = A[kk * ld + j], a1 = A[(kk + 1) * ld + j];
-                  const float a2 = three ? A[(kk + 2) * ld + j] : 0.f;
-                  const float t = a0 + u1 * a1 + u2 * a2;
-                  A[kk * ld + j] = a0 - t * w0;
-                  A[(kk + 1) * ld + j] = a1 - t * w1;
-                  if (three) A[(kk + 2) * ld + j] = a2 - t * w2;
-                }
-              }
-              __syncwarp();
-              // column modification inside the window: rows b .. min(nn, kk+3)
-              {
-                const int i2 = b + lane0;
-                if (i2 <= min(nn, kk + 3)) {
-                  const float b0 = A[i2 * ld + kk], b1 = A[i2 * ld + kk + 1];
-                  const float b2 = three ? A[i2 * ld + kk + 2] : 0.f;
-                  const float t = w0 * b0 + w1 * b1 + w2 * b2;
-                  A[i2 * ld + kk] = b0 - t;
-                  A[i2 * ld + kk + 1] = b1 - t * u1;
-                  if (three) A[i2 * ld + kk + 2] = b2 - t * u2;
-                }
-                // the same transformation accumulated in Zb (window coordinates)
-                const int kl = kk - b;
-                float* zr = Zb + lane0 * (WN + 4);
-                const float z0 = zr[kl], z1 = zr[kl + 1];
-                const float z2 = three ? zr[kl + 2] : 0.f;
-                const float t = w0 * z0 + w1 * z1 + w2 * z2;
-                zr[kl] = z0 - t;
-                zr[kl + 1] = z1 - t * u1;
-                if (three) zr[kl + 2] = z2 - t * u2;
-              }
-            }
-            __syncwarp();
           }
-          if (lane0 == 0) {
-            s_ctl[0] = b;
-            s_ctl[1] = e;
-            s_ctl[2] = kend;
+          const unsigned msk = __ballot_sync(0xffffffffu, ok);
+          if (msk) {
+            mm = base - (__ffs(msk) - 1);
+            break;
           }
-          b = kend;
-          if (b > nn - 1) in_sweep = false;
-          (void)w;
+        }
+        float pp, qq, rr;
+        {
+          const float z = A[mm * ld + mm];
+          const float r2 = x - z, s2 = y - z;
+          pp = (r2 * s2 - w) / A[(mm + 1) * ld + mm] + A[mm * ld + mm + 1];
+          qq = A[(mm + 1) * ld + mm + 1] - z - r2 - s2;
+          rr = A[(mm + 2) * ld + mm + 1];
+          const float sc = fabsf(pp) + fabsf(qq) + fabsf(rr);
+          pp /= sc; qq /= sc; rr /= sc;
+        }
+        __syncwarp();
+        for (int r = mm + 2 + lane0; r <= nn; r += 32) {
+          A[r * ld + r - 2] = 0.f;
+          if (r != mm + 2) A[r * ld + r - 3] = 0.f;
+        }
+        __syncwarp();
+        ll = l2;
+        m = mm;
+        b = mm;
+        if (lane0 == 0) { s_sh[0] = pp; s_sh[1] = qq; s_sh[2] = rr; }
+        in_sweep = true;
+      }
+        __syncwarp();
+        if (!in_sweep) break;
+        cont = false;
+      }
+      const int cur = wdx & 1;
+      float* Zb = Zbuf + cur * WN * (WN + 4);
+      // the factor buffer of window wdx-2 must have been taken over by the helpers
+      if (!warp_wait_geq(&s_taken, wdx - 1)) { fail = 2; break; }
+      if (cont) {
+        // the previous window's right update in the columns of this window (its rows
+        // overlap this window's); needs the window before it applied
+        if (!warp_wait_geq(&s_applied, wdx - 1)) { fail = 2; break; }
+        const int pb = s_desc[cur ^ 1][0], pe = s_desc[cur ^ 1][1], pc = s_desc[cur ^ 1][3];
+        const int pw = pe - pb;
+        const float* Zp = Zbuf + (cur ^ 1) * WN * (WN + 4);
+        const int c = pe + lane0;
+        const bool mine = c < pc;
+        float out[WN];
+#pragma unroll
+        for (int i2 = 0; i2 < WN; ++i2) out[i2] = 0.f;
+        for (int j2 = 0; j2 < pw; ++j2) {
+          const float a = mine ? A[(pb + j2) * ld + c] : 0.f;
+          const float4* zr = reinterpret_cast<const float4*>(Zp + j2 * (WN + 4));
+#pragma unroll
+          for (int q4 = 0; q4 < WN / 4; ++q4) {
+            const float4 z = zr[q4];
+            out[4 * q4] = fmaf(z.x, a, out[4 * q4]);
+            out[4 * q4 + 1] = fmaf(z.y, a, out[4 * q4 + 1]);
+            out[4 * q4 + 2] = fmaf(z.z, a, out[4 * q4 + 2]);
+            out[4 * q4 + 3] = fmaf(z.w, a, out[4 * q4 + 3]);
+          }
+        }
+        if (mine) {
+#pragma unroll
+          for (int i2 = 0; i2 < WN; ++i2)
+            if (i2 < pw) A[(pb + i2) * ld + c] = out[i2];
         }
         __syncwarp();
       }
-      __syncthreads();
-      const int state = s_ctl[3];
-      if (state != 0) break;
-      // ---- apply the window's Zb outside the window (all threads)
-      {
-        const int bb = s_ctl[0], ee = s_ctl[1], ww = ee - bb;
-        float* ZT = Zbuf + (cur ^ 1) * WN * (WN + 4);   // the other buffer: Zb transposed, ld WN+4
-        for (int e2 = tid; e2 < WN * WN; e2 += nth) {
-          const int i2 = e2 / WN, j2 = e2 % WN;
-          ZT[i2 * (WN + 4) + j2] = Zb[j2 * (WN + 4) + i2];
-        }
-        __syncthreads();
-        const int n_right = n - ee;
-        const int t = tid;
-        if (t < n_right || t - n_right < bb) {
-          const bool right = t < n_right;
-          const int c = ee + t, r = t - n_right;
-          float in[WN];
-#pragma unroll
-          for (int j2 = 0; j2 < WN; ++j2)
-            in[j2] = (j2 < ww) ? (right ? A[(bb + j2) * ld + c] : A[r * ld + bb + j2]) : 0.f;
-          // four outputs at a time: four independent accumulation chains
-          for (int i0 = 0; i0 < ww; i0 += 4) {
-            float acc[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              const float4* zt = reinterpret_cast<const float4*>(ZT + (i0 + u) * (WN + 4));
-              float a = 0.f;
-#pragma unroll
-              for (int q4 = 0; q4 < WN / 4; ++q4) {
-                const float4 z = zt[q4];
-                a = fmaf(z.x, in[4 * q4], a);
-                a = fmaf(z.y, in[4 * q4 + 1], a);
-                a = fmaf(z.z, in[4 * q4 + 2], a);
-                a = fmaf(z.w, in[4 * q4 + 3], a);
-              }
-              acc[u] = a;
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              if (i0 + u < ww) {
-                if (right) A[(bb + i0 + u) * ld + c] = acc[u];
-                else A[r * ld + bb + i0 + u] = acc[u];
-              }
+      // ---- chase one window: steps kk in [b, kend), window [b, e)
+      const int kend = min(b + WB, nn);
+      const int e = min(b + WN, n);
+      for (int q = 0; q < WN; ++q) Zb[lane0 * (WN + 4) + q] = (q == lane0) ? 1.f : 0.f;
+      __syncwarp();
+        for (int kk = b; kk < kend; ++kk) {
+          const bool three = kk != nn - 1;
+          float pp, qq, rr, xs = 1.f;
+          bool go = true;
+          if (kk == m) {
+            pp = s_sh[0]; qq = s_sh[1]; rr = s_sh[2];
+          } else {
+            pp = A[kk * ld + kk - 1];
+            qq = A[(kk + 1) * ld + kk - 1];
+            rr = three ? A[(kk + 2) * ld + kk - 1] : 0.f;
+            xs = fabsf(pp) + fabsf(qq) + fabsf(rr);
+            if (xs != 0.f) {
+              const float ix = __fdividef(1.f, xs);
+              pp *= ix; qq *= ix; rr *= ix;
+            } else {
+              go = false;
             }
           }
-        }
-        // log the window: (b, e) and Zb
-        const int widx = s_ctl[7];
-        if (widx < zlog_cap(n)) {
-          float* rec = zlog + (size_t)widx * ZREC;
-          for (int e2 = tid; e2 < WN * WN; e2 += nth)
-            rec[8 + e2] = Zb[(e2 / WN) * (WN + 4) + (e2 % WN)];
-          if (tid == 0) {
-            rec[0] = __int_as_float(bb);
-            rec[1] = __int_as_float(ee);
+          float s = 0.f, is = 0.f;
+          if (go) {
+            const float ss = pp * pp + qq * qq + rr * rr;
+            go = ss > 0.f;
+            if (go) {
+              const float rs = rsqrtf(ss);
+              s = sgnf(ss * rs, pp);
+              is = sgnf(rs, pp);
+            }
           }
+          __syncwarp();
+          if (go) {
+            if (lane0 == 0) {
+              if (kk == m) {
+                if (ll != m) A[kk * ld + kk - 1] = -A[kk * ld + kk - 1];
+              } else {
+                A[kk * ld + kk - 1] = -s * xs;
+              }
+            }
+            pp += s;
+            const float ip = __fdividef(1.f, pp);
+            const float w0 = pp * is, w1 = qq * is, w2 = three ? rr * is : 0.f;
+            const float u1 = qq * ip, u2 = three ? rr * ip : 0.f;
+            // row modification inside the window: columns kk .. e-1
+            {
+              const int j = b + lane0;
+              if (j >= kk && j < e) {
+                const float a0 = A[kk * ld + j], a1 = A[(kk + 1) * ld + j];
+                const float a2 = three ? A[(kk + 2) * ld + j] : 0.f;
+                const float t = a0 + u1 * a1 + u2 * a2;
+                A[kk * ld + j] = a0 - t * w0;
+                A[(kk + 1) * ld + j] = a1 - t * w1;
+                if (three) A[(kk + 2) * ld + j] = a2 - t * w2;
+              }
+            }
+            __syncwarp();
+            // column modification inside the window: rows b .. min(nn, kk+3)
+            {
+              const int i2 = b + lane0;
+              if (i2 <= min(nn, kk + 3)) {
+                const float b0 = A[i2 * ld + kk], b1 = A[i2 * ld + kk + 1];
+                const float b2 = three ? A[i2 * ld + kk + 2] : 0.f;
+                const float t = w0 * b0 + w1 * b1 + w2 * b2;
+                A[i2 * ld + kk] = b0 - t;
+                A[i2 * ld + kk + 1] = b1 - t * u1;
+                if (three) A[i2 * ld + kk + 2] = b2 - t * u2;
+              }
+              // the same transformation accumulated in Zb (window coordinates)
+              const int kl = kk - b;
+              float* zr = Zb + lane0 * (WN + 4);
+              const float z0 = zr[kl], z1 = zr[kl + 1];
+              const float z2 = three ? zr[kl + 2] : 0.f;
+              const float t = w0 * z0 + w1 * z1 + w2 * z2;
+              zr[kl] = z0 - t;
+              zr[kl + 1] = z1 - t * u1;
+              if (three) zr[kl + 2] = z2 - t * u2;
+            }
+          }
+          __syncwarp();
         }
-        __syncthreads();
-        if (tid == 0) s_ctl[7] = widx + 1;
+      // post the window
+      const bool next = kend <= nn - 1;
+      if (lane0 == 0) {
+        s_desc[cur][0] = b;
+        s_desc[cur][1] = e;
+        s_desc[cur][2] = kend;
+        s_desc[cur][3] = next ? min(kend + WN, n) : e;
       }
-      __syncthreads();
-      ++blk;
+      __syncwarp();
+      __threadfence_block();
+      if (lane0 == 0) s_posted = wdx + 1;
+      ++wdx;
+      b = kend;
+      in_sweep = next;
+      cont = next;
     }
-    if (tid == 0) {
-      shi[4] = (s_ctl[3] == 2 || s_ctl[7] > zlog_cap(n)) ? 1 : 0;
-      shi[5] = min((long long)s_ctl[7], zlog_cap(n));
+    __syncwarp();
+    if (lane0 == 0) {
+      s_nwin = wdx;
+      s_state = fail ? 2 : 1;
+      if (fail == 2) atomicOr(p.status, DEV_TIMEOUT);
     }
     (void)total_its;
+  } else if ((warp_id_of(tid) & 3) != 0) {
+    // helpers: the warps that do not share warp 0's scheduler (warps 4, 8, 12 stay idle,
+    // so the chaser's issue slots are its own)
+    const int hw = warp_id_of(tid) - 1 - (warp_id_of(tid) >> 2);
+    const int nh = (nth / 32 - 1 - (nth / 32 - 1) / 4) * 32;
+    const int h = hw * 32 + (tid & 31);
+    for (int v = 0;; ++v) {
+      if (h == 0) {
+        int go = 0;
+        const uint64_t t0 = bw::global_ns();
+        while (true) {
+          if (s_posted > v) { go = 1; break; }
+          if (s_state != 0) break;
+          if (bw::global_ns() - t0 > 2000000000ull) {
+            atomicOr(p.status, DEV_TIMEOUT);
+            break;
+          }
+          __nanosleep(64);
+        }
+        s_go = go;
+      }
+      helper_sync(nh);
+      if (!s_go) break;
+      __threadfence_block();
+      const int cur = v & 1;
+      const int bb = s_desc[cur][0], ee = s_desc[cur][1], cs = s_desc[cur][3];
+      const int ww = ee - bb;
+      const float* Zb = Zbuf + cur * WN * (WN + 4);
+      for (int e2 = h; e2 < WN * WN; e2 += nh) {
+        const int i2 = e2 / WN, j2 = e2 % WN;
+        ZT[i2 * (WN + 4) + j2] = Zb[j2 * (WN + 4) + i2];
+      }
+      helper_sync(nh);
+      if (h == 0) s_taken = v + 1;
+      // log the factor (row-major Zb, from the transposed copy)
+      if (v < zlog_cap(n)) {
+        float* rec = zlog + (size_t)v * ZREC;
+        for (int e2 = h; e2 < WN * WN; e2 += nh) rec[8 + e2] = ZT[(e2 % WN) * (WN + 4) + e2 / WN];
+        if (h == 0) {
+          rec[0] = __int_as_float(bb);
+          rec[1] = __int_as_float(ee);
+        }
+      }
+      const int n_right = n - cs, n_top = bb;
+      for (int task = h; task < n_right + n_top; task += nh) {
+        const bool right = task < n_right;
+        // right: column cs + task of rows [bb, ee); top: row task - n_right, columns [bb, ee)
+        float* base = right ? A + bb * ld + cs + task : A + (task - n_right) * ld + bb;
+        const int stride = right ? ld : 1;
+        float in[WN];
+#pragma unroll
+        for (int j2 = 0; j2 < WN; ++j2) in[j2] = (j2 < ww) ? base[j2 * stride] : 0.f;
+        for (int i0 = 0; i0 < ww; i0 += 4) {
+          float acc[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const float4* zt = reinterpret_cast<const float4*>(ZT + (i0 + u) * (WN + 4));
+            float a = 0.f;
+#pragma unroll
+            for (int q4 = 0; q4 < WN / 4; ++q4) {
+              const float4 z = zt[q4];
+              a = fmaf(z.x, in[4 * q4], a);
+              a = fmaf(z.y, in[4 * q4 + 1], a);
+              a = fmaf(z.z, in[4 * q4 + 2], a);
+              a = fmaf(z.w, in[4 * q4 + 3], a);
+            }
+            acc[u] = a;
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (i0 + u < ww) base[(i0 + u) * stride] = acc[u];
+        }
+      }
+      helper_sync(nh);
+      if (h == 0) {
+        __threadfence_block();
+        s_applied = v + 1;
+      }
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    shi[4] = (s_state == 2 || s_nwin > zlog_cap(n)) ? 1 : 0;
+    shi[5] = s_nwin;
   }
   __syncthreads();
   const bool failed = shi[4] != 0;
@@ -696,11 +827,12 @@ __global__ void __launch_bounds__(EIG_THREADS)
 
   // ---- 5. eigenvectors of the quasi-triangular T: one warp per eigenvalue, column 2*rank
   //         (real part) and 2*rank+1 (imaginary part) of X
-  const int warp = tid >> 5, lane = tid & 31, nwarps = nth >> 5;
+  const int warp = tid >> 5, lane = tid & 31;
   const int ncx = 2 * npole;   // columns of X
-  float* xr = smem + p.xbuf_off + warp * 2 * p.nmax;   // this warp's vector (shared memory)
+  constexpr int VEC_WARPS = 8;  // warps with a vector buffer (shared memory)
+  float* xr = smem + p.xbuf_off + (warp % VEC_WARPS) * 2 * p.nmax;
   float* xi = xr + p.nmax;
-  for (int j = warp; j < npole; j += nwarps) {
+  for (int j = warp; j < npole && warp < VEC_WARPS; j += VEC_WARPS) {
     const int pos = s_pos[j];
     const float mr = s_mur[j], mu_i = s_mui[j];
     for (int r = lane; r < n; r += 32) { xr[r] = 0.f; xi[r] = 0.f; }
@@ -713,7 +845,7 @@ __global__ void __launch_bounds__(EIG_THREADS)
       xi[pos + 1] = mu_i;
     }
     __syncwarp();
-    const float tiny = FLT_EPSILON * sh[8] + FLT_MIN;
+    const float tiny = FLT_EPSILON * sh[8] + FLT_MIN;   // sh[8] = ||H||_1 (entrywise)
     for (int r = pos - 1; r >= 0;) {
       const bool pair = (r >= 1) && A[r * ld + r - 1] != 0.f;
       const int top = pair ? r - 1 : r;
@@ -780,123 +912,219 @@ __global__ void __launch_bounds__(EIG_THREADS)
   }
   __syncthreads();
 
-  // ---- 6. back transformation Psi~ = Q_hess Zb_1 ... Zb_B x (X in shared memory; T is
-  //         no longer needed): windows in reverse order, then the Hessenberg reflectors
-  float* Xs = A;
-  for (int e = tid; e < n * ncx; e += nth) Xs[e] = X[e];
-  {
-    float* Zs = smem + p.log_off;   // two staged window factors, WN x (WN + 4) each
-    const int n_win = shi[5];
-    auto stage = [&](int wdx, int buf) {
-      const float* rec = zlog + (size_t)wdx * ZREC;
-      float* dst = Zs + buf * WN * (WN + 4);
-      for (int e2 = tid; e2 < WN * WN; e2 += nth) dst[(e2 / WN) * (WN + 4) + (e2 % WN)] = rec[8 + e2];
-    };
-    if (n_win > 0) stage(n_win - 1, 0);
-    for (int wdx = n_win - 1, buf = 0; wdx >= 0; --wdx, buf ^= 1) {
-      __syncthreads();
-      if (wdx > 0) stage(wdx - 1, buf ^ 1);   // next factor, overlapped with this product
-      const float* rec = zlog + (size_t)wdx * ZREC;
-      const int bb = __float_as_int(rec[0]), ee = __float_as_int(rec[1]), ww = ee - bb;
-      const float* Zc = Zs + buf * WN * (WN + 4);
-      for (int col = tid; col < ncx; col += nth) {
-        float in[WN];
-#pragma unroll
-        for (int j2 = 0; j2 < WN; ++j2) in[j2] = (j2 < ww) ? Xs[(bb + j2) * ncx + col] : 0.f;
-        for (int i0 = 0; i0 < ww; i0 += 4) {
-          float acc[4];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const float4* zr = reinterpret_cast<const float4*>(Zc + (i0 + u) * (WN + 4));
-            float a = 0.f;
-#pragma unroll
-            for (int q4 = 0; q4 < WN / 4; ++q4) {
-              const float4 z = zr[q4];
-              a = fmaf(z.x, in[4 * q4], a);
-              a = fmaf(z.y, in[4 * q4 + 1], a);
-              a = fmaf(z.z, in[4 * q4 + 2], a);
-              a = fmaf(z.w, in[4 * q4 + 3], a);
-            }
-            acc[u] = a;
-          }
-#pragma unroll
-          for (int u = 0; u < 4; ++u)
-            if (i0 + u < ww) Xs[(bb + i0 + u) * ncx + col] = acc[u];
-        }
-      }
-    }
-    __syncthreads();
-    float* sv3 = Zs;   // Hessenberg reflector staging (n floats)
-    for (int j = n - 3; j >= 0; --j) {
-      const int len = n - j - 1;
-      __syncthreads();
-      for (int c = tid; c < len; c += nth) sv3[c] = hv[(size_t)j * n + c];
-      __syncthreads();
-      const float beta = hv[(size_t)j * n + n - 1];
-      if (beta == 0.f) continue;
-      for (int col = tid; col < ncx; col += nth) {
-        float sacc = 0.f;
-        for (int r = 0; r < len; ++r) sacc = fmaf(sv3[r], Xs[(j + 1 + r) * ncx + col], sacc);
-        sacc *= beta;
-        for (int r = 0; r < len; ++r) Xs[(j + 1 + r) * ncx + col] -= sacc * sv3[r];
-      }
-    }
-  }
+  // ---- 6. pole records, largest frequency last; MPC and MPD follow with the mode shapes
+  //         (k_eig_vectors)
+  __shared__ int s_src[256];
+  for (int j = tid; j < npole; j += nth) s_src[s_rank[j]] = j;
   __syncthreads();
-
-  // ---- 7. Phi = U[:l, :n] Psi~, normalisation, pole parameters
-  for (int j = warp; j < n_slots; j += nwarps) {
+  for (int j = tid; j < n_slots; j += nth) {
     ssi_pole rec;
     rec.lag = p.lt.i[t];
     rec.order = n;
     rec.index = j;
-    float* ph = phi_out + (size_t)j * 2 * l;
+    rec.mpc = 0.f;
+    rec.mpd = 0.f;
     if (failed || j >= npole) {
-      if (lane == 0) {
-        rec.f_hz = 0.f; rec.xi = 0.f; rec.mu_re = 0.f; rec.mu_im = 0.f; rec.mpc = 0.f; rec.mpd = 0.f;
-        rec.flags = failed ? SSI_POLE_NOTCONV : 0u;
-        poles[j] = rec;
+      rec.f_hz = 0.f; rec.xi = 0.f; rec.mu_re = 0.f; rec.mu_im = 0.f;
+      rec.flags = failed ? SSI_POLE_NOTCONV : 0u;
+    } else {
+      const int src = s_src[j];
+      const double mr = s_mur[src], mu_i = s_mui[src];
+      const double lr = 0.5 * log(mr * mr + mu_i * mu_i) / p.dt, li = atan2(mu_i, mr) / p.dt;
+      const double lam = sqrt(lr * lr + li * li);
+      rec.f_hz = (float)(lam / (2.0 * 3.14159265358979323846));
+      rec.xi = lam > 0 ? (float)(-lr / lam) : 0.f;
+      rec.mu_re = (float)mr;
+      rec.mu_im = (float)mu_i;
+      rec.flags = SSI_POLE_VALID;
+    }
+    poles[j] = rec;
+  }
+  if (tid == 0) {
+    hdr[0] = failed ? 0 : npole;
+    hdr[1] = shi[5];
+    hdr[2] = failed ? 1 : 0;
+  }
+  (void)k;
+  (void)l;
+}
+
+// ------------------------------------------------------------------ mode shapes
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(bw::smem_u32(smem_dst)),
+               "l"(gmem_src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem_dst, const void* gmem_src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(bw::smem_u32(smem_dst)),
+               "l"(gmem_src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// One CTA per (lag, order, block of VEC_COLS columns of X = 16 poles), largest orders
+// first.  The block of X (eigenvectors of T) is carried back to eigenvectors of A~:
+// the logged window factors in reverse order (X[b:e] = Zb X[b:e]), then the Hessenberg
+// reflectors in reverse order; then Phi = U[:l, :n] X, its normalisation (unit norm,
+// largest component real), MPC and MPD of every pole of the block.  Window records and
+// reflectors stream through shared-memory rings filled by cp.async, several ahead.
+constexpr int VEC_THREADS = 256;
+constexpr int XLD = VEC_COLS + 1;   // shared-memory row stride of the X block
+constexpr int ZRING = 4;            // window records in flight
+constexpr int VRING = 4;            // Hessenberg reflectors in flight
+
+__global__ void __launch_bounds__(VEC_THREADS)
+    k_eig_vectors(EigParams p) {
+  extern __shared__ float vsm[];
+  // block -> (lag, order, column block), largest orders first
+  const int per_lag = p.vec_blocks_per_lag;
+  const int t = blockIdx.x % p.lt.n_lags;
+  int q = blockIdx.x / p.lt.n_lags;   // block index within the lag, largest orders first
+  int mi = p.n_orders - 1;
+  while (mi > 0 && q >= p.vec_blocks[mi]) {
+    q -= p.vec_blocks[mi];
+    --mi;
+  }
+  (void)per_lag;
+  const int n = p.orders[mi];
+  const int k = p.lt.k, l = p.lt.l;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nwarps = VEC_THREADS / 32;
+  const float* work = p.work + (size_t)t * p.work_per_lag + p.work_off[mi];
+  const int* hdr = reinterpret_cast<const int*>(work);
+  const float* hv = work + EIG_HDR;
+  const float* X = hv + (size_t)n * n;
+  const float* zlog = X + (size_t)n * n;
+  const int npole = hdr[0], n_win = min(hdr[1], (int)zlog_cap(n));
+  const int ncx = 2 * npole;
+  const int c0 = q * VEC_COLS;                   // first column of this block
+  const int nc = max(0, min(VEC_COLS, ncx - c0));
+  const int slot0 = c0 / 2;
+  ssi_pole* poles = p.poles + (size_t)t * p.slots_per_lag + p.slot_off[mi];
+  float* phi_out = p.phi + ((size_t)t * p.slots_per_lag + p.slot_off[mi]) * 2 * l;
+  const float* U = p.lt.U[t];
+  const int n_slots_blk = min(VEC_COLS / 2, n / 2 - slot0);
+  if (nc == 0) {
+    // no pole of this block has a shape: zero their mode shapes
+    for (int e = tid; e < n_slots_blk * 2 * l; e += VEC_THREADS)
+      phi_out[(size_t)slot0 * 2 * l + e] = 0.f;
+    return;
+  }
+  float* Xs = vsm;                                         // n x XLD
+  float* Zs = Xs + (((size_t)n * XLD + 3) & ~size_t(3));   // ZRING window records
+  float* vs = Zs + ZRING * ZREC;                           // VRING reflectors of SMEM_N_MAX
+  for (int e = tid; e < n * VEC_COLS; e += VEC_THREADS) {
+    const int r = e / VEC_COLS, c = e % VEC_COLS;
+    Xs[r * XLD + c] = (c < nc) ? X[(size_t)r * ncx + c0 + c] : 0.f;
+  }
+  // 1. window factors in reverse order; warp w owns rows 4w..4w+3 of the window, lane the
+  //    column.  Record w goes to ring slot w % ZRING, ZRING - 1 records ahead; a slot is
+  //    refilled only after the barrier that follows every thread's last use of it.
+  {
+    auto issue = [&](int w) {
+      if (w >= 0) {
+        const float* src = zlog + (size_t)w * ZREC;
+        float* dst = Zs + (w % ZRING) * ZREC;
+        for (int e = tid; e < ZREC / 4; e += VEC_THREADS) cp_async16(dst + 4 * e, src + 4 * e);
       }
-      for (int c = lane; c < 2 * l; c += 32) ph[c] = 0.f;
-      continue;
-    }
-    // the pole of rank j
-    int src = 0;
-    for (int o = 0; o < npole; ++o) if (s_rank[o] == j) src = o;
-    const float* xr = Xs + 2 * j;
-    // phi_c = sum_a U[c][a] psi_a, complex: lanes split a (coalesced rows of U, psi held in
-    // registers), a warp reduction per channel
-    constexpr int NA = (SMEM_N_MAX + 31) / 32;
-    float xre[NA], xim[NA];
+      cp_async_commit();
+    };
+    for (int a = 1; a < ZRING; ++a) issue(n_win - a);
+    for (int w = n_win - 1; w >= 0; --w) {
+      cp_async_wait<ZRING - 2>();   // record w has landed (the newer ZRING - 2 may not)
+      __syncthreads();
+      issue(w - (ZRING - 1));       // into the slot of record w + 1, done by every thread
+      const float* rec = Zs + (w % ZRING) * ZREC;
+      const float* Zc = rec + 8;
+      const int bb = __float_as_int(rec[0]), ee = __float_as_int(rec[1]), ww = ee - bb;
+      float acc[4] = {0.f, 0.f, 0.f, 0.f};
+      const int i0 = 4 * warp;
+      for (int j4 = 0; j4 < ww; j4 += 4) {
+        float xv[4];
 #pragma unroll
-    for (int q = 0; q < NA; ++q) {
-      const int a = lane + 32 * q;
-      xre[q] = (a < n) ? xr[a * ncx] : 0.f;
-      xim[q] = (a < n) ? xr[a * ncx + 1] : 0.f;
+        for (int u = 0; u < 4; ++u) xv[u] = (j4 + u < ww) ? Xs[(bb + j4 + u) * XLD + lane] : 0.f;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const float4 z = *reinterpret_cast<const float4*>(Zc + (i0 + r) * WN + j4);
+          acc[r] = fmaf(z.x, xv[0], fmaf(z.y, xv[1], fmaf(z.z, xv[2], fmaf(z.w, xv[3], acc[r]))));
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+        if (i0 + r < ww) Xs[(bb + i0 + r) * XLD + lane] = acc[r];
     }
+    cp_async_wait<0>();
+  }
+  __syncthreads();
+  // 2. Hessenberg reflectors in reverse order: 8 threads per column split the rows; row j
+  //    of the reflector log goes to ring slot j % VRING, VRING - 1 reflectors ahead
+  {
+    const int c = tid & 31, g = tid >> 5;   // column, row group
+    __shared__ float s_part[VEC_THREADS];
+    auto issue = [&](int j) {
+      if (j >= 0)
+        for (int r = tid; r < n; r += VEC_THREADS)
+          cp_async4(vs + (j % VRING) * SMEM_N_MAX + r, hv + (size_t)j * n + r);
+      cp_async_commit();
+    };
+    for (int a = 0; a < VRING - 1; ++a) issue(n - 3 - a);
+    for (int j = n - 3; j >= 0; --j) {
+      cp_async_wait<VRING - 2>();   // reflector j has landed
+      __syncthreads();
+      issue(j - (VRING - 1));       // into the slot of reflector j + 1, done by every thread
+      const float* v = vs + (j % VRING) * SMEM_N_MAX;
+      const int len = n - j - 1;
+      const float beta = v[n - 1];
+      float part = 0.f;
+      if (beta != 0.f)
+        for (int r = g; r < len; r += 8) part = fmaf(v[r], Xs[(j + 1 + r) * XLD + c], part);
+      s_part[tid] = part;
+      __syncthreads();
+      if (beta != 0.f) {
+        float dot = 0.f;
+#pragma unroll
+        for (int g2 = 0; g2 < 8; ++g2) dot += s_part[g2 * 32 + c];
+        const float sc = dot * beta;
+        for (int r = g; r < len; r += 8) Xs[(j + 1 + r) * XLD + c] -= sc * v[r];
+      }
+    }
+    cp_async_wait<0>();
+  }
+  __syncthreads();
+  // 3. Phi = U[:l, :n] X for the block: thread per channel, all columns in registers
+  for (int ch = tid; ch < l; ch += VEC_THREADS) {
+    float acc[VEC_COLS];
+#pragma unroll
+    for (int c = 0; c < VEC_COLS; ++c) acc[c] = 0.f;
+    const float* urow = U + (size_t)ch * k;
+    for (int a = 0; a < n; ++a) {
+      const float u = __ldg(urow + a);
+      const float* xr = Xs + a * XLD;
+#pragma unroll
+      for (int c = 0; c < VEC_COLS; ++c) acc[c] = fmaf(u, xr[c], acc[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < VEC_COLS; ++c)
+      if (c < nc) phi_out[(size_t)(slot0 + c / 2) * 2 * l + 2 * ch + (c & 1)] = acc[c];
+  }
+  // slots of the block without a pole
+  for (int e = tid; e < (n_slots_blk - nc / 2) * 2 * l; e += VEC_THREADS)
+    phi_out[(size_t)(slot0 + nc / 2) * 2 * l + e] = 0.f;
+  __syncthreads();
+  // 4. per pole: scale by conj(largest)/|largest| / ||phi||, MPC, MPD
+  for (int jj = warp; jj < nc / 2; jj += nwarps) {
+    const int j = slot0 + jj;
+    float* ph = phi_out + (size_t)j * 2 * l;
     float nrm2 = 0.f, best = -1.f, bre = 1.f, bim = 0.f;
-    for (int c = 0; c < l; ++c) {
-      const float* wrow = U + (size_t)c * k;
-      float sr = 0.f, si = 0.f;
-#pragma unroll
-      for (int q = 0; q < NA; ++q) {
-        const int a = lane + 32 * q;
-        const float u = (a < n) ? wrow[a] : 0.f;
-        sr = fmaf(u, xre[q], sr);
-        si = fmaf(u, xim[q], si);
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        sr += __shfl_xor_sync(0xffffffffu, sr, o);
-        si += __shfl_xor_sync(0xffffffffu, si, o);
-      }
-      if (lane == (c & 31)) {
-        ph[2 * c] = sr;
-        ph[2 * c + 1] = si;
-        const float m2 = sr * sr + si * si;
-        nrm2 += m2;
-        if (m2 > best) { best = m2; bre = sr; bim = si; }
-      }
+    for (int c = lane; c < l; c += 32) {
+      const float sr = ph[2 * c], si = ph[2 * c + 1];
+      const float m2 = sr * sr + si * si;
+      nrm2 += m2;
+      if (m2 > best) { best = m2; bre = sr; bim = si; }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -907,7 +1135,6 @@ __global__ void __launch_bounds__(EIG_THREADS)
       if (ob > best) { best = ob; bre = orr; bim = oi; }
     }
     __syncwarp();
-    // scale by conj(largest)/|largest| / ||phi||
     const float bm = sqrtf(fmaxf(best, 0.f));
     const float inv = (nrm2 > 0.f && bm > 0.f) ? rsqrtf(nrm2) / bm : 0.f;
     const float cr = bre * inv, ci = -bim * inv;
@@ -949,17 +1176,8 @@ __global__ void __launch_bounds__(EIG_THREADS)
       asum += __shfl_xor_sync(0xffffffffu, asum, o);
     }
     if (lane == 0) {
-      const double mr = s_mur[src], mu_i = s_mui[src];
-      const double lr = 0.5 * log(mr * mr + mu_i * mu_i) / p.dt, li = atan2(mu_i, mr) / p.dt;
-      const double lam = sqrt(lr * lr + li * li);
-      rec.f_hz = (float)(lam / (2.0 * 3.14159265358979323846));
-      rec.xi = lam > 0 ? (float)(-lr / lam) : 0.f;
-      rec.mu_re = (float)mr;
-      rec.mu_im = (float)mu_i;
-      rec.mpc = mpc;
-      rec.mpd = wsum > 0.f ? (asum / wsum) / 1.5707963267948966f : 0.f;
-      rec.flags = SSI_POLE_VALID;
-      poles[j] = rec;
+      poles[j].mpc = mpc;
+      poles[j].mpd = wsum > 0.f ? (asum / wsum) / 1.5707963267948966f : 0.f;
     }
   }
 }
@@ -1028,14 +1246,14 @@ ssi_status realize_ws(ssi_ctx* ctx, Workspace& ws, const RealizePlan& r, const i
   }
   const int tiles = (int)ceil_div(k, 64);
   dim3 g1((unsigned)(tiles * tiles), (unsigned)n_chunks, (unsigned)(2 * r.n_lags));
-  count_launches(ctx, 4);
+  count_launches(ctx, 5);
   {
   ProfScope ps(ctx, ST_GRAM, stream);
   k_gram_gh<<<g1, 256, 0, stream>>>(lt, n_chunks, partial);
   SSI_CUDA(cudaGetLastError());
   k_gram_reduce<<<ctx->num_sms * 4, 256, 0, stream>>>(partial, r.n_lags, n_chunks, k, GH);
   SSI_CUDA(cudaGetLastError());
-  const size_t fsmem = (size_t)k * k * sizeof(float);
+  const size_t fsmem = ((size_t)k * (k + 1) + k) * sizeof(float);
   SSI_CHECK(fsmem <= 220 * 1024, "realize: k=%d too large for the per-lag factorisation", k);
   SSI_CUDA(cudaFuncSetAttribute(k_lag_factor, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)(220 * 1024)));
@@ -1060,11 +1278,23 @@ ssi_status realize_ws(ssi_ctx* ctx, Workspace& ws, const RealizePlan& r, const i
   const int nsm_max = std::min(r.max_order, SMEM_N_MAX);
   ep.nmax = nsm_max;
   ep.xbuf_off = (int)round_up((int64_t)nsm_max * (nsm_max + 1), 32);
-  ep.log_off = (int)round_up((int64_t)ep.xbuf_off + (int64_t)(EIG_THREADS / 32) * 2 * nsm_max, 32);
+  ep.log_off = (int)round_up((int64_t)ep.xbuf_off + std::max<int64_t>(8LL * 2 * nsm_max, WN * (WN + 4)),
+                            32);   // 8 vector warps, or the transposed window factor
   const size_t esmem = ((size_t)ep.log_off + (size_t)std::max(2 * WN * (WN + 4), SMEM_N_MAX)) * sizeof(float);
   SSI_CUDA(cudaFuncSetAttribute(k_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)esmem));
+  int vec_total = 0;
+  for (int m = 0; m < r.n_orders; ++m) {
+    ep.vec_blocks[m] = (int)ceil_div(orders[m], VEC_COLS);
+    vec_total += ep.vec_blocks[m];
+  }
+  ep.vec_blocks_per_lag = vec_total;
+  const size_t vsmem =
+      ((((size_t)nsm_max * XLD + 3) & ~size_t(3)) + ZRING * ZREC + VRING * SMEM_N_MAX) * sizeof(float);
+  SSI_CUDA(cudaFuncSetAttribute(k_eig_vectors, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vsmem));
   ProfScope ps_eig(ctx, ST_EIG, stream);
   k_eig<<<r.n_lags * r.n_orders, EIG_THREADS, esmem, stream>>>(ep);
+  SSI_CUDA(cudaGetLastError());
+  k_eig_vectors<<<r.n_lags * vec_total, VEC_THREADS, vsmem, stream>>>(ep);
   SSI_CUDA(cudaGetLastError());
   return SSI_OK;
 }
