@@ -71,7 +71,9 @@ size_t ssi_memory_in_use(const ssi_ctx* ctx);
  * returns, per stage id, the summed device time in ms and the number of scopes since
  * the previous read, plus the number of kernels the context launched (also reset).
  * Stage ids: 0 split/transpose, 1 lag GEMM, 2 lag reduction, 3 Toeplitz sketch GEMMs,
- * 4 QR, 5 small SVD, 6 Gram/factorisation, 7 eig, 8 stability, 9 other; n >= 10. */
+ * 4 QR, 5 small SVD, 6 Gram/factorisation, 7 eig (Hessenberg, QR iteration, Schur
+ * vectors), 8 stability, 9 other, 10 eigenvector back transformation and mode shapes;
+ * stages with ids >= n are not reported. */
 ssi_status ssi_profile(ssi_ctx* ctx, int enable);
 ssi_status ssi_profile_read(ssi_ctx* ctx, double* ms, int64_t* counts, int n, int64_t* launches);
 

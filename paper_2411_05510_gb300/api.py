@@ -63,7 +63,7 @@ class Context:
         return int(lib.ssi_memory_in_use(self.ptr))
 
     STAGES = ["split", "lag_gemm", "lag_reduce", "sketch_gemm", "qr", "small_svd", "gram_factor",
-              "eig", "stability", "other"]
+              "eig", "stability", "other", "eig_vectors"]
 
     def profile(self, enable: bool = True) -> None:
         check(lib.ssi_profile(self.ptr, 1 if enable else 0), "ssi_profile")

@@ -1291,9 +1291,12 @@ ssi_status realize_ws(ssi_ctx* ctx, Workspace& ws, const RealizePlan& r, const i
   const size_t vsmem =
       ((((size_t)nsm_max * XLD + 3) & ~size_t(3)) + ZRING * ZREC + VRING * SMEM_N_MAX) * sizeof(float);
   SSI_CUDA(cudaFuncSetAttribute(k_eig_vectors, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vsmem));
-  ProfScope ps_eig(ctx, ST_EIG, stream);
-  k_eig<<<r.n_lags * r.n_orders, EIG_THREADS, esmem, stream>>>(ep);
-  SSI_CUDA(cudaGetLastError());
+  {
+    ProfScope ps_eig(ctx, ST_EIG, stream);
+    k_eig<<<r.n_lags * r.n_orders, EIG_THREADS, esmem, stream>>>(ep);
+    SSI_CUDA(cudaGetLastError());
+  }
+  ProfScope ps_vec(ctx, ST_EIG_VEC, stream);
   k_eig_vectors<<<r.n_lags * vec_total, VEC_THREADS, vsmem, stream>>>(ep);
   SSI_CUDA(cudaGetLastError());
   return SSI_OK;

@@ -119,11 +119,20 @@ __global__ void k_to_bf16(const float* __restrict__ x, long long n, __nv_bfloat1
 
 __global__ void k_sum_splits(const float* __restrict__ part, int n_split, long long stride,
                              float* __restrict__ out) {
+  // four loads in flight per thread (independent partial sums)
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < stride;
        e += (long long)gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int sp = 0; sp < n_split; ++sp) s += (double)part[sp * stride + e];
-    out[e] = (float)s;
+    double s[4] = {0.0, 0.0, 0.0, 0.0};
+    int sp = 0;
+    for (; sp + 4 <= n_split; sp += 4) {
+      float v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v[u] = __ldcs(part + (sp + u) * stride + e);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) s[u] += (double)v[u];
+    }
+    for (; sp < n_split; ++sp) s[sp & 3] += (double)__ldcs(part + sp * stride + e);
+    out[e] = (float)((s[0] + s[1]) + (s[2] + s[3]));
   }
 }
 
@@ -451,6 +460,26 @@ ssi_status launch_tg_nb(int nb, const CUtensorMap& ah, const CUtensorMap& al, co
   }
 }
 
+// Reduction splits of the Toeplitz products: the count in [2, 16] whose units
+// (n_tiles per split) fill the SMs' waves best, the smallest such count on ties; each
+// split covers a multiple of SBK rows.
+int toeplitz_splits(int L_pad, int n_tiles, int num_sms) {
+  int best = 1;
+  double best_eff = -1.0;
+  for (int S = 2; S <= 16; ++S) {
+    const int krows = (int)round_up(ceil_div(L_pad, S), SBK);
+    const int S_eff = (int)ceil_div(L_pad, krows);
+    const long long units = (long long)n_tiles * S_eff;
+    const double waves = (double)units / num_sms;
+    const double eff = waves / std::ceil(waves);
+    if (eff > best_eff + 1e-3) {
+      best_eff = eff;
+      best = S_eff;
+    }
+  }
+  return best;
+}
+
 int grid_1d(long long n, int threads, int num_sms) {
   return (int)std::max<long long>(1, std::min<long long>(ceil_div(n, threads), (long long)num_sms * 8));
 }
@@ -478,8 +507,8 @@ RsvdPlan rsvd_plan(int l, int i, int k, int oversample, int q, int num_sms) {
   const int n_nt = (int)ceil_div(round_up(r.K, 64), 256);
   r.Kp = (int)round_up(r.K, 64 * n_nt);
   const int n_mt = r.L_pad / 128 + (r.L_pad % 128 ? 1 : 0);
-  int S = (int)std::max<int64_t>(1, ceil_div(4LL * num_sms, (int64_t)n_mt * n_nt));
-  int krows = (int)round_up(ceil_div(r.L_pad, S), SBK);
+  int S = toeplitz_splits(r.L_pad, n_mt * n_nt, num_sms);
+  const int krows = (int)round_up(ceil_div(r.L_pad, S), SBK);
   S = (int)ceil_div(r.L_pad, krows);
   const int n_lag = 2 * i - 1;
   const size_t rblk = (size_t)n_lag * r.l_pad * r.l_pad;
@@ -518,7 +547,7 @@ ssi_status toeplitz_rsvd_ws(ssi_ctx* ctx, Workspace& ws, const RsvdPlan& r, cons
   p.n_mt = (int)ceil_div(r.L_pad, 128);
   p.n_nt = n_nt;
   {
-    int Sg = (int)std::max<int64_t>(1, ceil_div(4LL * ctx->num_sms, (int64_t)p.n_mt * n_nt));
+    const int Sg = toeplitz_splits(r.L_pad, p.n_mt * n_nt, ctx->num_sms);
     p.krows = (int)round_up(ceil_div(r.L_pad, Sg), SBK);
     p.n_split = (int)ceil_div(r.L_pad, p.krows);
   }

@@ -5,9 +5,10 @@
 // on B = R2^T: rotating the columns of B until they are mutually orthogonal gives
 // B V = W Sigma, hence R2 = V Sigma W^T and U~ = W (the normalised columns of B),
 // Sigma = their norms; V itself is never needed.
-// One CTA of 1024 threads; B is held column by column in shared memory when
-// K^2 floats fit, else in global memory.  Pairs follow the circle (round-robin)
-// ordering, one pair per warp at a time.  Sweeps stop when every pair satisfies
+// One CTA of 512 threads; B is held column by column in shared memory when it fits,
+// else in global memory.  Pairs follow the circle (round-robin) ordering, four pairs
+// per warp (eight lanes each).  The column stride is = 8 (mod 32) floats, so the four
+// groups of a warp, which hold consecutive pair indices, read distinct banks.  Sweeps stop when every pair satisfies
 // |b_p^T b_q| <= tol ||b_p|| ||b_q|| or after max_sweeps (status bit set).
 #include "common.cuh"
 
@@ -16,6 +17,8 @@ namespace ssi {
 namespace {
 
 constexpr int JT = 512;
+
+__host__ __device__ inline int col_stride(int K) { return ((K + 23) / 32) * 32 + 8; }
 
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
@@ -37,7 +40,8 @@ __global__ void __launch_bounds__(JT, 1)
   __shared__ int s_rot;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = JT / 32;
   // B = R2^T: column c of B is row c of R2
-  for (int e = tid; e < K * K; e += JT) B[e] = R2[e];
+  const int KS = col_stride(K);
+  for (int e = tid; e < K * K; e += JT) B[(e / K) * KS + e % K] = R2[e];
   __syncthreads();
   const int n_pad = K + (K & 1);
   const int half = n_pad / 2;
@@ -63,8 +67,8 @@ __global__ void __launch_bounds__(JT, 1)
           if (p > q) { const int t = p; p = q; q = t; }
         }
         const bool act = live && p < K && q < K;
-        float* bp = B + (size_t)p * K;
-        float* bq = B + (size_t)q * K;
+        float* bp = B + (size_t)p * KS;
+        float* bq = B + (size_t)q * KS;
         float xv[RJ8], yv[RJ8];
         float al = 0.f, be = 0.f, ga = 0.f;
 #pragma unroll
@@ -108,7 +112,7 @@ __global__ void __launch_bounds__(JT, 1)
   // norms and ranks
   for (int c = warp; c < K; c += nw) {
     float s = 0.f;
-    for (int r = lane; r < K; r += 32) s = fmaf(B[(size_t)c * K + r], B[(size_t)c * K + r], s);
+    for (int r = lane; r < K; r += 32) s = fmaf(B[(size_t)c * KS + r], B[(size_t)c * KS + r], s);
     s = warp_sum(s);
     if (lane == 0) s_norm[c] = sqrtf(s);
   }
@@ -127,15 +131,17 @@ __global__ void __launch_bounds__(JT, 1)
   for (int e = tid; e < K * K; e += JT) {
     const int c = e / K, r = e % K;
     const float nv = s_norm[c];
-    Ut[(size_t)r * K + s_rank[c]] = nv > 0.f ? B[(size_t)c * K + r] / nv : 0.f;
+    Ut[(size_t)r * K + s_rank[c]] = nv > 0.f ? B[(size_t)c * KS + r] / nv : 0.f;
   }
 }
 
 }  // namespace
 
+constexpr size_t JACOBI_SMEM_MAX = 216 * 1024;
+
 size_t jacobi_ws_bytes(int K) {
   WsPlan w;
-  if ((size_t)K * K * sizeof(float) > 200 * 1024) w.add<float>((size_t)K * K);
+  if ((size_t)K * col_stride(K) * sizeof(float) > JACOBI_SMEM_MAX) w.add<float>((size_t)K * col_stride(K));
   return w.bytes;
 }
 
@@ -145,11 +151,11 @@ ssi_status jacobi_launch(Workspace& ws, const float* R2, int K, float* Ut, float
     set_error("jacobi: K=%d > 512", K);
     return SSI_E_INVALID;
   }
-  const size_t bytes = (size_t)K * K * sizeof(float);
+  const size_t bytes = (size_t)K * col_stride(K) * sizeof(float);
   float* Bg = nullptr;
   size_t smem = 0;
-  if (bytes > 200 * 1024) {
-    Bg = ws.take<float>((size_t)K * K);
+  if (bytes > JACOBI_SMEM_MAX) {
+    Bg = ws.take<float>((size_t)K * col_stride(K));
     if (!Bg) {
       set_error("jacobi: workspace too small");
       return SSI_E_NOMEM;
@@ -157,7 +163,7 @@ ssi_status jacobi_launch(Workspace& ws, const float* R2, int K, float* Ut, float
   } else {
     smem = bytes;
     SSI_CUDA(cudaFuncSetAttribute(k_jacobi_svd<29>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)(200 * 1024)));
+                                  (int)JACOBI_SMEM_MAX));
   }
   if (K <= 232)
     k_jacobi_svd<29><<<1, JT, smem, stream>>>(R2, K, Bg, 1e-5f, 30, Ut, S, status);
