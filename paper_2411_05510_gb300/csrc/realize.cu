@@ -595,6 +595,20 @@ __global__ void __launch_bounds__(EIG_THREADS)
       __syncwarp();
         for (int kk = b; kk < kend; ++kk) {
           const bool three = kk != nn - 1;
+          // loads that do not depend on this step's reflector, issued together: the
+          // previous step's column update was published by its closing __syncwarp
+          const int j = b + lane0;
+          const bool row_lane = j >= kk && j < e;
+          float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+          if (row_lane) {
+            a0 = A[kk * ld + j];
+            a1 = A[(kk + 1) * ld + j];
+            a2 = three ? A[(kk + 2) * ld + j] : 0.f;
+          }
+          const int kl = kk - b;
+          float* zr = Zb + lane0 * (WN + 4);
+          const float z0 = zr[kl], z1 = zr[kl + 1];
+          const float z2 = three ? zr[kl + 2] : 0.f;
           float pp, qq, rr, xs = 1.f;
           bool go = true;
           if (kk == m) {
@@ -621,8 +635,31 @@ __global__ void __launch_bounds__(EIG_THREADS)
               is = sgnf(rs, pp);
             }
           }
+          float w0 = 0.f, w1 = 0.f, w2 = 0.f, u1 = 0.f, u2 = 0.f;
+          if (go) {
+            pp += s;
+            const float ip = __fdividef(1.f, pp);
+            w0 = pp * is;
+            w1 = qq * is;
+            w2 = three ? rr * is : 0.f;
+            u1 = qq * ip;
+            u2 = three ? rr * ip : 0.f;
+            // row modification inside the window: columns kk .. e-1
+            if (row_lane) {
+              const float t = a0 + u1 * a1 + u2 * a2;
+              A[kk * ld + j] = a0 - t * w0;
+              A[(kk + 1) * ld + j] = a1 - t * w1;
+              if (three) A[(kk + 2) * ld + j] = a2 - t * w2;
+            }
+            // the same transformation accumulated in Zb (window coordinates)
+            const float t = w0 * z0 + w1 * z1 + w2 * z2;
+            zr[kl] = z0 - t;
+            zr[kl + 1] = z1 - t * u1;
+            if (three) zr[kl + 2] = z2 - t * u2;
+          }
           __syncwarp();
           if (go) {
+            // A[kk][kk-1]: read by every lane above, by no lane from here on in this step
             if (lane0 == 0) {
               if (kk == m) {
                 if (ll != m) A[kk * ld + kk - 1] = -A[kk * ld + kk - 1];
@@ -630,43 +667,15 @@ __global__ void __launch_bounds__(EIG_THREADS)
                 A[kk * ld + kk - 1] = -s * xs;
               }
             }
-            pp += s;
-            const float ip = __fdividef(1.f, pp);
-            const float w0 = pp * is, w1 = qq * is, w2 = three ? rr * is : 0.f;
-            const float u1 = qq * ip, u2 = three ? rr * ip : 0.f;
-            // row modification inside the window: columns kk .. e-1
-            {
-              const int j = b + lane0;
-              if (j >= kk && j < e) {
-                const float a0 = A[kk * ld + j], a1 = A[(kk + 1) * ld + j];
-                const float a2 = three ? A[(kk + 2) * ld + j] : 0.f;
-                const float t = a0 + u1 * a1 + u2 * a2;
-                A[kk * ld + j] = a0 - t * w0;
-                A[(kk + 1) * ld + j] = a1 - t * w1;
-                if (three) A[(kk + 2) * ld + j] = a2 - t * w2;
-              }
-            }
-            __syncwarp();
             // column modification inside the window: rows b .. min(nn, kk+3)
-            {
-              const int i2 = b + lane0;
-              if (i2 <= min(nn, kk + 3)) {
-                const float b0 = A[i2 * ld + kk], b1 = A[i2 * ld + kk + 1];
-                const float b2 = three ? A[i2 * ld + kk + 2] : 0.f;
-                const float t = w0 * b0 + w1 * b1 + w2 * b2;
-                A[i2 * ld + kk] = b0 - t;
-                A[i2 * ld + kk + 1] = b1 - t * u1;
-                if (three) A[i2 * ld + kk + 2] = b2 - t * u2;
-              }
-              // the same transformation accumulated in Zb (window coordinates)
-              const int kl = kk - b;
-              float* zr = Zb + lane0 * (WN + 4);
-              const float z0 = zr[kl], z1 = zr[kl + 1];
-              const float z2 = three ? zr[kl + 2] : 0.f;
-              const float t = w0 * z0 + w1 * z1 + w2 * z2;
-              zr[kl] = z0 - t;
-              zr[kl + 1] = z1 - t * u1;
-              if (three) zr[kl + 2] = z2 - t * u2;
+            const int i2 = b + lane0;
+            if (i2 <= min(nn, kk + 3)) {
+              const float b0 = A[i2 * ld + kk], b1 = A[i2 * ld + kk + 1];
+              const float b2 = three ? A[i2 * ld + kk + 2] : 0.f;
+              const float t = w0 * b0 + w1 * b1 + w2 * b2;
+              A[i2 * ld + kk] = b0 - t;
+              A[i2 * ld + kk + 1] = b1 - t * u1;
+              if (three) A[i2 * ld + kk + 2] = b2 - t * u2;
             }
           }
           __syncwarp();
