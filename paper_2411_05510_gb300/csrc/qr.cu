@@ -205,12 +205,27 @@ __global__ void __launch_bounds__(QR_THREADS, 1)   // one CTA per SM (cooperativ
         // ---- C = Q[:, :j0]^T W, partial over this CTA's rows
         const int nC = j0 * PB;
         float* myC = p.red_c + (size_t)blockIdx.x * p.ncols * PB;
-        for (int e = tid; e < nC; e += QR_THREADS) {
-          const int a = e / PB, b = e % PB;
-          float s = 0.f;
-          if (b < w)
-            for (int rr = 0; rr < nr; ++rr) s = fmaf(Ab[rr * ldb + a], Ab[rr * ldb + j0 + b], s);
-          myC[e] = s;
+        // 4 x 4 outputs per thread: rows a0..a0+3 of Q^T, columns b0..b0+3 of the panel
+        for (int tt = tid; tt < (j0 / 4) * (PB / 4); tt += QR_THREADS) {
+          const int a0 = 4 * (tt / (PB / 4)), b0 = 4 * (tt % (PB / 4));
+          float acc[4][4] = {};
+          for (int rr = 0; rr < nr; ++rr) {
+            const float* row = Ab + rr * ldb;
+            float qa[4], wb[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              qa[u] = row[a0 + u];
+              wb[u] = (b0 + u < w) ? row[j0 + b0 + u] : 0.f;
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+              for (int u = 0; u < 4; ++u) acc[i][u] = fmaf(qa[i], wb[u], acc[i][u]);
+          }
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) myC[(a0 + i) * PB + b0 + u] = acc[i][u];
         }
         if (!grid_sync(p, gb)) return;
         {
@@ -225,13 +240,26 @@ __global__ void __launch_bounds__(QR_THREADS, 1)   // one CTA per SM (cooperativ
           __syncthreads();
           C = sC;
         }
-        // ---- W -= Q[:, :j0] C on local rows (a warp shares its row; lanes take columns)
-        for (int e = tid; e < nr * PB; e += QR_THREADS) {
-          const int rr = e / PB, b = e % PB;
-          if (b >= w) continue;
-          float s = 0.f;
-          for (int a = 0; a < j0; ++a) s = fmaf(Ab[rr * ldb + a], C[a * PB + b], s);
-          Ab[rr * ldb + j0 + b] -= s;
+        // ---- W -= Q[:, :j0] C on local rows: 4 rows x 4 columns per thread
+        for (int tt = tid; tt < ((nr + 3) / 4) * (PB / 4); tt += QR_THREADS) {
+          const int r0 = 4 * (tt / (PB / 4)), b0 = 4 * (tt % (PB / 4));
+          float acc[4][4] = {};
+          for (int a = 0; a < j0; ++a) {
+            float qv[4], cv[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) qv[i] = (r0 + i < nr) ? Ab[(r0 + i) * ldb + a] : 0.f;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) cv[u] = C[a * PB + b0 + u];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+              for (int u = 0; u < 4; ++u) acc[i][u] = fmaf(qv[i], cv[u], acc[i][u]);
+          }
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+              if (r0 + i < nr && b0 + u < w) Ab[(r0 + i) * ldb + j0 + b0 + u] -= acc[i][u];
         }
         if (p.Rout && blockIdx.x == 0) {
           // R[:j0, j0+b] accumulates C1 + C2 R1
