@@ -7,8 +7,9 @@
 //   pass 2:  W' = W   - Q_{<j} (Q_{<j}^T W);     Q_j = W' R2^{-1}, R2 = chol(W'^T W')
 // (block classical Gram-Schmidt with re-orthogonalisation, each panel made
 // orthonormal by Cholesky-QR).  The Gram matrices are accumulated in double-FP32
-// (error-free products with fma, two-sum accumulation) and reduced in FP64, the
-// first 32x32 Cholesky runs in FP64 redundantly in every CTA, so a panel with condition
+// (error-free products with fma, two-sum accumulation) and reduced in FP64.  The 32x32
+// Cholesky factors run redundantly in every CTA: in FP32 by one warp, and for the first
+// pass in FP64 when the FP32 pivots show cond(G) above ~1e5, so a panel with condition
 // number up to ~1e7 is orthonormalised to FP32 precision.  Grid-wide reductions
 // use a two-phase barrier (partials -> sliced sums -> broadcast); every barrier
 // wait is bounded and sets the status word when it runs out.
@@ -108,15 +109,22 @@ __device__ void slice_reduce(const T* part, size_t stride, int P, int e0, int e1
 
 // FP32 Cholesky of a well-conditioned w x w Gram matrix by one warp (lane c holds column c):
 // used by the second Cholesky-QR pass, whose Gram matrix is the identity up to O(eps).
-__device__ void chol_warp_f32(const double* G, int w, double* R, double* rdiag, int lane) {
+// Returns min_j pivot_j / max_j G[j][j] (the same in every lane), an estimate of
+// 1 / cond(G) that decides whether the FP32 factor is accurate enough.
+__device__ float chol_warp_f32(const double* G, int w, double* R, double* rdiag, int lane) {
   float col[PB];
 #pragma unroll
   for (int a = 0; a < PB; ++a) col[a] = (a < w && lane < w && a <= lane) ? (float)G[a * PB + lane] : 0.f;
+  float gmax = (lane < w) ? (float)G[lane * PB + lane] : 0.f;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) gmax = fmaxf(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
+  float dmin = 3.0e38f;
 #pragma unroll
   for (int j = 0; j < PB; ++j) {
     if (j >= w) break;
     // R[j][j] = sqrt(col_j[j]); R[j][c] = col_c[j] / R[j][j]
     const float djj = __shfl_sync(0xffffffffu, col[j], j);
+    dmin = fminf(dmin, djj);
     const float rs = rsqrtf(fmaxf(djj, 1e-30f));
     const float rjc = (lane >= j) ? col[j] * rs : 0.f;   // lane == j: sqrt(d)
     R[j * PB + lane] = (lane < w) ? (double)rjc : 0.0;
@@ -129,6 +137,7 @@ __device__ void chol_warp_f32(const double* G, int w, double* R, double* rdiag, 
     }
   }
   __syncwarp();
+  return (w == 0) ? 1.f : (gmax > 0.f ? dmin / gmax : 0.f);
 }
 
 // Cholesky of the w x w Gram matrix G (FP64, upper triangle used) by the whole CTA.  Per
@@ -311,11 +320,18 @@ __global__ void __launch_bounds__(QR_THREADS, 1)   // one CTA per SM (cooperativ
         sG[e] = (a < w && b < w && a <= b) ? p.fin_g[e] : 0.0;
       }
       __syncthreads();
-      if (pass == 0) {
-        chol_cta(sG, w, sR[pass], sRd);
-      } else {
-        if (tid < 32) chol_warp_f32(sG, w, sR[pass], sRd, tid);
+      // FP32 Cholesky by one warp; the first pass falls back to the FP64 factorisation
+      // when a pivot is below 1e-5 of the largest diagonal (cond(G) above ~1e5, where the
+      // FP32 factor would be too inaccurate for the second pass to repair).  Every CTA
+      // factors the same G, so every CTA takes the same branch.
+      {
+        __shared__ int s_f32ok;
+        if (tid < 32) {
+          const float ratio = chol_warp_f32(sG, w, sR[pass], sRd, tid);
+          if (tid == 0) s_f32ok = (pass == 1) || ratio >= 1e-5f;
+        }
         __syncthreads();
+        if (!s_f32ok) chol_cta(sG, w, sR[pass], sRd);
       }
       for (int e = tid; e < PB * PB; e += QR_THREADS) sRf[e] = (float)sR[pass][e];
       for (int e = tid; e < PB; e += QR_THREADS) sRdf[e] = (float)sRd[e];
