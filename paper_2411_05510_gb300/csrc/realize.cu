@@ -273,6 +273,14 @@ __device__ __forceinline__ bool warp_wait_geq(volatile int* x, int v) {
   return ok;
 }
 
+constexpr int NCH = 4;        // chaser warps: bulges chased at once in a multi-bulge sweep
+constexpr int NMIN_MB = 30;   // active blocks below this size are swept with one bulge
+
+// barrier of the chaser warps only (named barrier 2)
+__device__ __forceinline__ void chaser_sync() {
+  asm volatile("bar.sync 2, %0;" ::"n"(NCH * 32) : "memory");
+}
+
 // barrier of the helper warps only (named barrier 1; barrier 0 is __syncthreads)
 __device__ __forceinline__ void helper_sync(int nthreads) {
   asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
@@ -449,266 +457,438 @@ __global__ void __launch_bounds__(EIG_THREADS)
     s_nwin = 0;
   }
   __syncthreads();
-  if (warp_id_of(tid) == 0) {
-    const int lane0 = tid;
+  if (warp_id_of(tid) < NCH) {
+    // ---------------------------------------------------------------- chasers
+    const int cw = warp_id_of(tid), lane0 = tid & 31;
+    __shared__ int s_sw[8];              // sweep: 0 go, 1 nbs, 2 l, 3 nn, 4 m, 5 fail
+    __shared__ int s_wok[2];             // per window parity: hand-off waits succeeded
+    __shared__ float s_tr[NCH], s_det[NCH];
     float anorm = 0.f;
-    for (int e2 = lane0; e2 < n * n; e2 += 32) {
-      const int r = e2 / n, c = e2 % n;
-      if (c >= r - 1) anorm += fabsf(A[r * ld + c]);
-    }
+    if (cw == 0) {
+      for (int e2 = lane0; e2 < n * n; e2 += 32) {
+        const int r = e2 / n, c = e2 % n;
+        if (c >= r - 1) anorm += fabsf(A[r * ld + c]);
+      }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) anorm += __shfl_xor_sync(0xffffffffu, anorm, o);
-    if (lane0 == 0) sh[8] = anorm;
-    int nn = n - 1, its = 0, total_its = 0, ll = 0, m = 0, b = 0, fail = 0, wdx = 0;
+      for (int o = 16; o > 0; o >>= 1) anorm += __shfl_xor_sync(0xffffffffu, anorm, o);
+      if (lane0 == 0) sh[8] = anorm;
+    }
+    // warp 0's iteration state; the sweep parameters reach the other chasers via s_sw
+    int nn = n - 1, its = 0, total_its = 0, fail = 0, wdx = 0;
+    int ll = 0, m = 0, nbs = 1, k0 = 0, b = 0;
     bool in_sweep = false, cont = false;
     const int itmax = 30 * max(10, n);
     while (true) {
       if (!in_sweep) {
-        // every posted window must be applied before the matrix is read outside a window
-        if (!warp_wait_geq(&s_applied, wdx)) { fail = 2; break; }
-      while (!in_sweep && nn >= 0 && !fail) {
-        int l2 = 0;
-        for (int base = nn; base >= 1; base -= 32) {
-          const int cand = base - lane0;
-          bool small = false;
-          if (cand >= 1) {
-            float sd = fabsf(A[(cand - 1) * ld + cand - 1]) + fabsf(A[cand * ld + cand]);
-            if (sd == 0.f) sd = anorm;
-            small = fabsf(A[cand * ld + cand - 1]) <= FLT_EPSILON * sd;
-          }
-          const unsigned msk = __ballot_sync(0xffffffffu, small);
-          if (msk) {
-            l2 = base - (__ffs(msk) - 1);
-            break;
-          }
-        }
-        __syncwarp();
-        if (l2 >= 1 && lane0 == 0) A[l2 * ld + l2 - 1] = 0.f;
-        __syncwarp();
-        if (l2 == nn) { nn -= 1; its = 0; continue; }
-        if (l2 == nn - 1) { nn -= 2; its = 0; continue; }
-        if (total_its >= itmax) { fail = 1; break; }
-        float x = A[nn * ld + nn], y = A[(nn - 1) * ld + nn - 1];
-        float w = A[nn * ld + nn - 1] * A[(nn - 1) * ld + nn];
-        if (its == 10 || its == 20) {
-          const float s = fabsf(A[nn * ld + nn - 1]) + fabsf(A[(nn - 1) * ld + nn - 2]);
-          x = y = 0.75f * s;
-          w = -0.4375f * s * s;
-        }
-        ++its;
-        ++total_its;
-        // start of the bulge: the largest mm in [l2, nn-2] where two consecutive
-        // subdiagonals are negligible relative to the shift vector (mm = l2 always
-        // qualifies); lanes test 32 candidates at a time
-        int mm = l2;
-        for (int base = nn - 2; base >= l2; base -= 32) {
-          const int cand = base - lane0;
-          bool ok = false;
-          if (cand >= l2) {
-            if (cand == l2) {
-              ok = true;
-            } else {
-              const float z = A[cand * ld + cand];
-              const float r2 = x - z, s2 = y - z;
-              float p0 = (r2 * s2 - w) / A[(cand + 1) * ld + cand] + A[cand * ld + cand + 1];
-              float q0 = A[(cand + 1) * ld + cand + 1] - z - r2 - s2;
-              float r0 = A[(cand + 2) * ld + cand + 1];
-              const float sc = fabsf(p0) + fabsf(q0) + fabsf(r0);
-              p0 /= sc; q0 /= sc; r0 /= sc;
-              const float u = fabsf(A[cand * ld + cand - 1]) * (fabsf(q0) + fabsf(r0));
-              const float v = fabsf(p0) * (fabsf(A[(cand - 1) * ld + cand - 1]) + fabsf(z) +
-                                           fabsf(A[(cand + 1) * ld + cand + 1]));
-              ok = u <= FLT_EPSILON * v;
+        if (cw == 0) {
+          // every posted window must be applied before the matrix is read outside a window
+          if (!warp_wait_geq(&s_applied, wdx)) fail = 2;
+          int l2 = 0, mm = 0, nb_new = 1;
+          while (!in_sweep && nn >= 0 && !fail) {
+            l2 = 0;
+            for (int base = nn; base >= 1; base -= 32) {
+              const int cand = base - lane0;
+              bool small = false;
+              if (cand >= 1) {
+                float sd = fabsf(A[(cand - 1) * ld + cand - 1]) + fabsf(A[cand * ld + cand]);
+                if (sd == 0.f) sd = anorm;
+                small = fabsf(A[cand * ld + cand - 1]) <= FLT_EPSILON * sd;
+              }
+              const unsigned msk = __ballot_sync(0xffffffffu, small);
+              if (msk) {
+                l2 = base - (__ffs(msk) - 1);
+                break;
+              }
             }
+            __syncwarp();
+            if (l2 >= 1 && lane0 == 0) A[l2 * ld + l2 - 1] = 0.f;
+            __syncwarp();
+            if (l2 == nn) { nn -= 1; its = 0; continue; }
+            if (l2 == nn - 1) { nn -= 2; its = 0; continue; }
+            if (total_its >= itmax) { fail = 1; break; }
+            const bool excep = its == 10 || its == 20;
+            ++its;
+            ++total_its;
+            if (NCH > 1 && nn - l2 + 1 >= NMIN_MB) {
+              // several bulges: shift pair q = the trailing 2x2 diagonal block q (trace and
+              // determinant); bulges enter at the top of the active block
+              nb_new = NCH;
+              if (lane0 < NCH) {
+                const int q = lane0, r0 = nn - 2 * q - 1;
+                float tr, de;
+                if (excep) {
+                  const float s0 = fabsf(A[nn * ld + nn - 1]) + fabsf(A[(nn - 1) * ld + nn - 2]);
+                  tr = 1.5f * s0;
+                  de = s0 * s0;
+                } else {
+                  const float a = A[r0 * ld + r0], bq = A[r0 * ld + r0 + 1];
+                  const float c = A[(r0 + 1) * ld + r0], d = A[(r0 + 1) * ld + r0 + 1];
+                  tr = a + d;
+                  de = a * d - bq * c;
+                }
+                s_tr[q] = tr;
+                s_det[q] = de;
+              }
+              mm = l2;
+            } else {
+              nb_new = 1;
+              float x = A[nn * ld + nn], y = A[(nn - 1) * ld + nn - 1];
+              float w = A[nn * ld + nn - 1] * A[(nn - 1) * ld + nn];
+              if (excep) {
+                const float s0 = fabsf(A[nn * ld + nn - 1]) + fabsf(A[(nn - 1) * ld + nn - 2]);
+                x = y = 0.75f * s0;
+                w = -0.4375f * s0 * s0;
+              }
+            // start of the bulge: the largest mm in [l2, nn-2] where two consecutive
+            // subdiagonals are negligible relative to the shift vector (mm = l2 always
+            // qualifies); lanes test 32 candidates at a time
+            mm = l2;
+            for (int base = nn - 2; base >= l2; base -= 32) {
+              const int cand = base - lane0;
+              bool ok = false;
+              if (cand >= l2) {
+                if (cand == l2) {
+                  ok = true;
+                } else {
+                  const float z = A[cand * ld + cand];
+                  const float r2 = x - z, s2 = y - z;
+                  float p0 = (r2 * s2 - w) / A[(cand + 1) * ld + cand] + A[cand * ld + cand + 1];
+                  float q0 = A[(cand + 1) * ld + cand + 1] - z - r2 - s2;
+                  float r0 = A[(cand + 2) * ld + cand + 1];
+                  const float sc = fabsf(p0) + fabsf(q0) + fabsf(r0);
+                  p0 /= sc; q0 /= sc; r0 /= sc;
+                  const float u = fabsf(A[cand * ld + cand - 1]) * (fabsf(q0) + fabsf(r0));
+                  const float v = fabsf(p0) * (fabsf(A[(cand - 1) * ld + cand - 1]) + fabsf(z) +
+                                               fabsf(A[(cand + 1) * ld + cand + 1]));
+                  ok = u <= FLT_EPSILON * v;
+                }
+              }
+              const unsigned msk = __ballot_sync(0xffffffffu, ok);
+              if (msk) {
+                mm = base - (__ffs(msk) - 1);
+                break;
+              }
+            }
+            float pp, qq, rr;
+            {
+              const float z = A[mm * ld + mm];
+              const float r2 = x - z, s2 = y - z;
+              pp = (r2 * s2 - w) / A[(mm + 1) * ld + mm] + A[mm * ld + mm + 1];
+              qq = A[(mm + 1) * ld + mm + 1] - z - r2 - s2;
+              rr = A[(mm + 2) * ld + mm + 1];
+              const float sc = fabsf(pp) + fabsf(qq) + fabsf(rr);
+              pp /= sc; qq /= sc; rr /= sc;
+            }
+              if (lane0 == 0) { s_sh[0] = pp; s_sh[1] = qq; s_sh[2] = rr; }
+            }
+            __syncwarp();
+            for (int r = mm + 2 + lane0; r <= nn; r += 32) {
+              A[r * ld + r - 2] = 0.f;
+              if (r != mm + 2) A[r * ld + r - 3] = 0.f;
+            }
+            __syncwarp();
+            in_sweep = true;
           }
-          const unsigned msk = __ballot_sync(0xffffffffu, ok);
-          if (msk) {
-            mm = base - (__ffs(msk) - 1);
-            break;
+          if (lane0 == 0) {
+            s_sw[0] = (in_sweep && !fail) ? 1 : 0;
+            s_sw[1] = nb_new;
+            s_sw[2] = l2;
+            s_sw[3] = nn;
+            s_sw[4] = mm;
+            s_sw[5] = fail;
           }
         }
-        float pp, qq, rr;
-        {
-          const float z = A[mm * ld + mm];
-          const float r2 = x - z, s2 = y - z;
-          pp = (r2 * s2 - w) / A[(mm + 1) * ld + mm] + A[mm * ld + mm + 1];
-          qq = A[(mm + 1) * ld + mm + 1] - z - r2 - s2;
-          rr = A[(mm + 2) * ld + mm + 1];
-          const float sc = fabsf(pp) + fabsf(qq) + fabsf(rr);
-          pp /= sc; qq /= sc; rr /= sc;
+        chaser_sync();
+        if (!s_sw[0]) {
+          fail = s_sw[5];
+          break;
         }
-        __syncwarp();
-        for (int r = mm + 2 + lane0; r <= nn; r += 32) {
-          A[r * ld + r - 2] = 0.f;
-          if (r != mm + 2) A[r * ld + r - 3] = 0.f;
-        }
-        __syncwarp();
-        ll = l2;
-        m = mm;
-        b = mm;
-        if (lane0 == 0) { s_sh[0] = pp; s_sh[1] = qq; s_sh[2] = rr; }
+        nbs = s_sw[1];
+        ll = s_sw[2];
+        nn = s_sw[3];
+        m = s_sw[4];
+        k0 = m;     // leading bulge position at the first chain step
+        b = m;
         in_sweep = true;
-      }
-        __syncwarp();
-        if (!in_sweep) break;
         cont = false;
+        chaser_sync();   // s_sw is rewritten only after every chaser has read it
       }
       const int cur = wdx & 1;
       float* Zb = Zbuf + cur * WN * (WN + 4);
-      // the factor buffer of window wdx-2 must have been taken over by the helpers
-      if (!warp_wait_geq(&s_taken, wdx - 1)) { fail = 2; break; }
-      if (cont) {
-        // the previous window's right update in the columns of this window (its rows
-        // overlap this window's); needs the window before it applied
-        if (!warp_wait_geq(&s_applied, wdx - 1)) { fail = 2; break; }
-        const int pb = s_desc[cur ^ 1][0], pe = s_desc[cur ^ 1][1], pc = s_desc[cur ^ 1][3];
-        const int pw = pe - pb;
-        const float* Zp = Zbuf + (cur ^ 1) * WN * (WN + 4);
-        const int c = pe + lane0;
-        const bool mine = c < pc;
-        float out[WN];
-#pragma unroll
-        for (int i2 = 0; i2 < WN; ++i2) out[i2] = 0.f;
-        for (int j2 = 0; j2 < pw; ++j2) {
-          const float a = mine ? A[(pb + j2) * ld + c] : 0.f;
-          const float4* zr = reinterpret_cast<const float4*>(Zp + j2 * (WN + 4));
-#pragma unroll
-          for (int q4 = 0; q4 < WN / 4; ++q4) {
-            const float4 z = zr[q4];
-            out[4 * q4] = fmaf(z.x, a, out[4 * q4]);
-            out[4 * q4 + 1] = fmaf(z.y, a, out[4 * q4 + 1]);
-            out[4 * q4 + 2] = fmaf(z.z, a, out[4 * q4 + 2]);
-            out[4 * q4 + 3] = fmaf(z.w, a, out[4 * q4 + 3]);
-          }
-        }
-        if (mine) {
-#pragma unroll
-          for (int i2 = 0; i2 < WN; ++i2)
-            if (i2 < pw) A[(pb + i2) * ld + c] = out[i2];
-        }
-        __syncwarp();
-      }
-      // ---- chase one window: steps kk in [b, kend), window [b, e)
-      const int kend = min(b + WB, nn);
       const int e = min(b + WN, n);
-      for (int q = 0; q < WN; ++q) Zb[lane0 * (WN + 4) + q] = (q == lane0) ? 1.f : 0.f;
-      __syncwarp();
-        for (int kk = b; kk < kend; ++kk) {
-          const bool three = kk != nn - 1;
-          // loads that do not depend on this step's reflector, issued together: the
-          // previous step's column update was published by its closing __syncwarp
-          const int j = b + lane0;
-          const bool row_lane = j >= kk && j < e;
-          float a0 = 0.f, a1 = 0.f, a2 = 0.f;
-          if (row_lane) {
-            a0 = A[kk * ld + j];
-            a1 = A[(kk + 1) * ld + j];
-            a2 = three ? A[(kk + 2) * ld + j] : 0.f;
+      // hand-off checks (warp 0), then the previous window's right update in the columns of
+      // this window (warp 0) and the identity factor
+      if (cw == 0) {
+        bool ok = warp_wait_geq(&s_taken, wdx - 1);
+        if (ok && cont) ok = warp_wait_geq(&s_applied, wdx - 1);
+        if (ok && cont) {
+          const int pb = s_desc[cur ^ 1][0], pe = s_desc[cur ^ 1][1], pc = s_desc[cur ^ 1][3];
+          const int pw = pe - pb;
+          const float* Zp = Zbuf + (cur ^ 1) * WN * (WN + 4);
+          const int c = pe + lane0;
+          const bool mine = c < pc;
+          float out[WN];
+#pragma unroll
+          for (int i2 = 0; i2 < WN; ++i2) out[i2] = 0.f;
+          for (int j2 = 0; j2 < pw; ++j2) {
+            const float a = mine ? A[(pb + j2) * ld + c] : 0.f;
+            const float4* zr = reinterpret_cast<const float4*>(Zp + j2 * (WN + 4));
+#pragma unroll
+            for (int q4 = 0; q4 < WN / 4; ++q4) {
+              const float4 z = zr[q4];
+              out[4 * q4] = fmaf(z.x, a, out[4 * q4]);
+              out[4 * q4 + 1] = fmaf(z.y, a, out[4 * q4 + 1]);
+              out[4 * q4 + 2] = fmaf(z.z, a, out[4 * q4 + 2]);
+              out[4 * q4 + 3] = fmaf(z.w, a, out[4 * q4 + 3]);
+            }
           }
-          const int kl = kk - b;
-          float* zr = Zb + lane0 * (WN + 4);
-          const float z0 = zr[kl], z1 = zr[kl + 1];
-          const float z2 = three ? zr[kl + 2] : 0.f;
-          float pp, qq, rr, xs = 1.f;
-          bool go = true;
-          if (kk == m) {
-            pp = s_sh[0]; qq = s_sh[1]; rr = s_sh[2];
-          } else {
-            pp = A[kk * ld + kk - 1];
-            qq = A[(kk + 1) * ld + kk - 1];
-            rr = three ? A[(kk + 2) * ld + kk - 1] : 0.f;
+          if (mine) {
+#pragma unroll
+            for (int i2 = 0; i2 < WN; ++i2)
+              if (i2 < pw) A[(pb + i2) * ld + c] = out[i2];
+          }
+        }
+        for (int q = 0; q < WN; ++q) Zb[lane0 * (WN + 4) + q] = (q == lane0) ? 1.f : 0.f;
+        if (lane0 == 0) s_wok[cur] = ok ? 1 : 0;   // rewritten two windows later, after
+      }                                              // every chaser passed the next barrier
+      chaser_sync();
+      if (!s_wok[cur]) {
+        fail = 2;
+        break;
+      }
+      int kend;       // positions chased in this window end before kend (single bulge)
+      bool next;      // the sweep continues in another window
+      int nb_next;    // start row of the next window
+      if (nbs == 1) {
+        kend = min(b + WB, nn);
+        if (cw == 0) {
+            for (int kk = b; kk < kend; ++kk) {
+              const bool three = kk != nn - 1;
+              // loads that do not depend on this step's reflector, issued together: the
+              // previous step's column update was published by its closing __syncwarp
+              const int j = b + lane0;
+              const bool row_lane = j >= kk && j < e;
+              float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+              if (row_lane) {
+                a0 = A[kk * ld + j];
+                a1 = A[(kk + 1) * ld + j];
+                a2 = three ? A[(kk + 2) * ld + j] : 0.f;
+              }
+              const int kl = kk - b;
+              float* zr = Zb + lane0 * (WN + 4);
+              const float z0 = zr[kl], z1 = zr[kl + 1];
+              const float z2 = three ? zr[kl + 2] : 0.f;
+              float pp, qq, rr, xs = 1.f;
+              bool go = true;
+              if (kk == m) {
+                pp = s_sh[0]; qq = s_sh[1]; rr = s_sh[2];
+              } else {
+                pp = A[kk * ld + kk - 1];
+                qq = A[(kk + 1) * ld + kk - 1];
+                rr = three ? A[(kk + 2) * ld + kk - 1] : 0.f;
+                xs = fabsf(pp) + fabsf(qq) + fabsf(rr);
+                if (xs != 0.f) {
+                  const float ix = __fdividef(1.f, xs);
+                  pp *= ix; qq *= ix; rr *= ix;
+                } else {
+                  go = false;
+                }
+              }
+              float s = 0.f, is = 0.f;
+              if (go) {
+                const float ss = pp * pp + qq * qq + rr * rr;
+                go = ss > 0.f;
+                if (go) {
+                  const float rs = rsqrtf(ss);
+                  s = sgnf(ss * rs, pp);
+                  is = sgnf(rs, pp);
+                }
+              }
+              float w0 = 0.f, w1 = 0.f, w2 = 0.f, u1 = 0.f, u2 = 0.f;
+              if (go) {
+                pp += s;
+                const float ip = __fdividef(1.f, pp);
+                w0 = pp * is;
+                w1 = qq * is;
+                w2 = three ? rr * is : 0.f;
+                u1 = qq * ip;
+                u2 = three ? rr * ip : 0.f;
+                // row modification inside the window: columns kk .. e-1
+                if (row_lane) {
+                  const float t = a0 + u1 * a1 + u2 * a2;
+                  A[kk * ld + j] = a0 - t * w0;
+                  A[(kk + 1) * ld + j] = a1 - t * w1;
+                  if (three) A[(kk + 2) * ld + j] = a2 - t * w2;
+                }
+                // the same transformation accumulated in Zb (window coordinates)
+                const float t = w0 * z0 + w1 * z1 + w2 * z2;
+                zr[kl] = z0 - t;
+                zr[kl + 1] = z1 - t * u1;
+                if (three) zr[kl + 2] = z2 - t * u2;
+              }
+              __syncwarp();
+              if (go) {
+                // A[kk][kk-1]: read by every lane above, by no lane from here on in this step
+                if (lane0 == 0) {
+                  if (kk == m) {
+                    if (ll != m) A[kk * ld + kk - 1] = -A[kk * ld + kk - 1];
+                  } else {
+                    A[kk * ld + kk - 1] = -s * xs;
+                  }
+                }
+                // column modification inside the window: rows b .. min(nn, kk+3)
+                const int i2 = b + lane0;
+                if (i2 <= min(nn, kk + 3)) {
+                  const float b0 = A[i2 * ld + kk], b1 = A[i2 * ld + kk + 1];
+                  const float b2 = three ? A[i2 * ld + kk + 2] : 0.f;
+                  const float t = w0 * b0 + w1 * b1 + w2 * b2;
+                  A[i2 * ld + kk] = b0 - t;
+                  A[i2 * ld + kk + 1] = b1 - t * u1;
+                  if (three) A[i2 * ld + kk + 2] = b2 - t * u2;
+                }
+              }
+              __syncwarp();
+            }
+        }
+        next = kend <= nn - 1;
+        nb_next = kend;
+      } else {
+        // ---- chain of nbs bulges: bulge j at position k0 - 3 j, active while in [ll, nn-1].
+        //  One chain step: every chaser computes its bulge's reflector and applies it to the
+        //  rows (the rows of different bulges are disjoint), then, after a barrier, to the
+        //  columns (disjoint too); left and right transformations commute, so this equals
+        //  the bulges moving one after another.
+        float w0 = 0.f, w1 = 0.f, w2 = 0.f, u1 = 0.f, u2 = 0.f;
+        while (true) {
+          // the lowest active bulge must stay inside the window
+          const int lead = min(k0, nn - 1);
+          const int jl = (k0 - lead + 2) / 3;               // first bulge at or above nn-1
+          const int klead = k0 - 3 * jl;
+          if (jl >= nbs || klead < ll) break;               // every bulge has left
+          if (min(klead + 3, nn) >= e) break;               // window full
+          const int k = k0 - 3 * cw;
+          const bool act = cw < nbs && k >= ll && k <= nn - 1;
+          const bool three = k != nn - 1;
+          bool go = false;
+          float s = 0.f, xs = 1.f;
+          if (act) {
+            const int j = b + lane0;
+            const bool row_lane = j >= k && j < e;
+            float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+            if (row_lane) {
+              a0 = A[k * ld + j];
+              a1 = A[(k + 1) * ld + j];
+              a2 = three ? A[(k + 2) * ld + j] : 0.f;
+            }
+            const int kl = k - b;
+            float* zr = Zb + lane0 * (WN + 4);
+            const float z0 = zr[kl], z1 = zr[kl + 1];
+            const float z2 = three ? zr[kl + 2] : 0.f;
+            float pp, qq, rr;
+            if (k == ll) {
+              // bulge entry: first column of (H - s1 I)(H - s2 I) from this bulge's shifts
+              const float tr = s_tr[cw], de = s_det[cw];
+              const float h00 = A[ll * ld + ll], h01 = A[ll * ld + ll + 1];
+              const float h10 = A[(ll + 1) * ld + ll], h11 = A[(ll + 1) * ld + ll + 1];
+              const float h21 = A[(ll + 2) * ld + ll + 1];
+              pp = h00 * h00 + h01 * h10 - tr * h00 + de;
+              qq = h10 * (h00 + h11 - tr);
+              rr = three ? h21 * h10 : 0.f;
+            } else {
+              pp = A[k * ld + k - 1];
+              qq = A[(k + 1) * ld + k - 1];
+              rr = three ? A[(k + 2) * ld + k - 1] : 0.f;
+            }
             xs = fabsf(pp) + fabsf(qq) + fabsf(rr);
             if (xs != 0.f) {
               const float ix = __fdividef(1.f, xs);
               pp *= ix; qq *= ix; rr *= ix;
-            } else {
-              go = false;
-            }
-          }
-          float s = 0.f, is = 0.f;
-          if (go) {
-            const float ss = pp * pp + qq * qq + rr * rr;
-            go = ss > 0.f;
-            if (go) {
-              const float rs = rsqrtf(ss);
-              s = sgnf(ss * rs, pp);
-              is = sgnf(rs, pp);
-            }
-          }
-          float w0 = 0.f, w1 = 0.f, w2 = 0.f, u1 = 0.f, u2 = 0.f;
-          if (go) {
-            pp += s;
-            const float ip = __fdividef(1.f, pp);
-            w0 = pp * is;
-            w1 = qq * is;
-            w2 = three ? rr * is : 0.f;
-            u1 = qq * ip;
-            u2 = three ? rr * ip : 0.f;
-            // row modification inside the window: columns kk .. e-1
-            if (row_lane) {
-              const float t = a0 + u1 * a1 + u2 * a2;
-              A[kk * ld + j] = a0 - t * w0;
-              A[(kk + 1) * ld + j] = a1 - t * w1;
-              if (three) A[(kk + 2) * ld + j] = a2 - t * w2;
-            }
-            // the same transformation accumulated in Zb (window coordinates)
-            const float t = w0 * z0 + w1 * z1 + w2 * z2;
-            zr[kl] = z0 - t;
-            zr[kl + 1] = z1 - t * u1;
-            if (three) zr[kl + 2] = z2 - t * u2;
-          }
-          __syncwarp();
-          if (go) {
-            // A[kk][kk-1]: read by every lane above, by no lane from here on in this step
-            if (lane0 == 0) {
-              if (kk == m) {
-                if (ll != m) A[kk * ld + kk - 1] = -A[kk * ld + kk - 1];
-              } else {
-                A[kk * ld + kk - 1] = -s * xs;
+              const float ss = pp * pp + qq * qq + rr * rr;
+              if (ss > 0.f) {
+                go = true;
+                const float rs = rsqrtf(ss);
+                s = sgnf(ss * rs, pp);
+                const float is = sgnf(rs, pp);
+                pp += s;
+                const float ip = __fdividef(1.f, pp);
+                w0 = pp * is;
+                w1 = qq * is;
+                w2 = three ? rr * is : 0.f;
+                u1 = qq * ip;
+                u2 = three ? rr * ip : 0.f;
               }
             }
-            // column modification inside the window: rows b .. min(nn, kk+3)
-            const int i2 = b + lane0;
-            if (i2 <= min(nn, kk + 3)) {
-              const float b0 = A[i2 * ld + kk], b1 = A[i2 * ld + kk + 1];
-              const float b2 = three ? A[i2 * ld + kk + 2] : 0.f;
-              const float t = w0 * b0 + w1 * b1 + w2 * b2;
-              A[i2 * ld + kk] = b0 - t;
-              A[i2 * ld + kk + 1] = b1 - t * u1;
-              if (three) A[i2 * ld + kk + 2] = b2 - t * u2;
+            if (go) {
+              if (row_lane) {
+                const float t = a0 + u1 * a1 + u2 * a2;
+                A[k * ld + j] = a0 - t * w0;
+                A[(k + 1) * ld + j] = a1 - t * w1;
+                if (three) A[(k + 2) * ld + j] = a2 - t * w2;
+              }
+              const float t = w0 * z0 + w1 * z1 + w2 * z2;
+              zr[kl] = z0 - t;
+              zr[kl + 1] = z1 - t * u1;
+              if (three) zr[kl + 2] = z2 - t * u2;
+            }
+            __syncwarp();
+            // column k-1 below the subdiagonal is now annihilated: store it (the next bulge
+            // of the chain reaches position k within this sweep and reads these entries)
+            if (go && k != ll) {
+              if (lane0 == 0) A[k * ld + k - 1] = -s * xs;
+              if (lane0 == 1) A[(k + 1) * ld + k - 1] = 0.f;
+              if (lane0 == 2 && three) A[(k + 2) * ld + k - 1] = 0.f;
             }
           }
-          __syncwarp();
+          chaser_sync();
+          if (act && go) {
+            const int i2 = b + lane0;
+            if (i2 <= min(nn, k + 3)) {
+              const float b0 = A[i2 * ld + k], b1 = A[i2 * ld + k + 1];
+              const float b2 = three ? A[i2 * ld + k + 2] : 0.f;
+              const float t = w0 * b0 + w1 * b1 + w2 * b2;
+              A[i2 * ld + k] = b0 - t;
+              A[i2 * ld + k + 1] = b1 - t * u1;
+              if (three) A[i2 * ld + k + 2] = b2 - t * u2;
+            }
+          }
+          chaser_sync();
+          ++k0;
         }
-      // post the window
-      const bool next = kend <= nn - 1;
-      if (lane0 == 0) {
-        s_desc[cur][0] = b;
-        s_desc[cur][1] = e;
-        s_desc[cur][2] = kend;
-        s_desc[cur][3] = next ? min(kend + WN, n) : e;
+        const int ktr = k0 - 3 * (nbs - 1);
+        next = ktr <= nn - 1;
+        nb_next = max(ll, ktr);
+        kend = nb_next;
       }
-      __syncwarp();
-      __threadfence_block();
-      if (lane0 == 0) s_posted = wdx + 1;
+      // post the window
+      if (cw == 0) {
+        if (lane0 == 0) {
+          s_desc[cur][0] = b;
+          s_desc[cur][1] = e;
+          s_desc[cur][2] = kend;
+          s_desc[cur][3] = next ? min(nb_next + WN, n) : e;
+        }
+        __syncwarp();
+        __threadfence_block();
+        if (lane0 == 0) s_posted = wdx + 1;
+      }
       ++wdx;
-      b = kend;
+      b = nb_next;
       in_sweep = next;
       cont = next;
     }
-    __syncwarp();
-    if (lane0 == 0) {
-      s_nwin = wdx;
-      s_state = fail ? 2 : 1;
-      if (fail == 2) atomicOr(p.status, DEV_TIMEOUT);
+    if (cw == 0) {
+      __syncwarp();
+      if (lane0 == 0) {
+        s_nwin = wdx;
+        s_state = fail ? 2 : 1;
+        if (fail == 2) atomicOr(p.status, DEV_TIMEOUT);
+      }
     }
     (void)total_its;
-  } else if ((warp_id_of(tid) & 3) != 0) {
-    // helpers: the warps that do not share warp 0's scheduler (warps 4, 8, 12 stay idle,
-    // so the chaser's issue slots are its own)
-    const int hw = warp_id_of(tid) - 1 - (warp_id_of(tid) >> 2);
-    const int nh = (nth / 32 - 1 - (nth / 32 - 1) / 4) * 32;
-    const int h = hw * 32 + (tid & 31);
+  } else {
+    // ---------------------------------------------------------------- helpers
+    const int nh = nth - 32 * NCH;
+    const int h = tid - 32 * NCH;
     for (int v = 0;; ++v) {
       if (h == 0) {
         int go = 0;
