@@ -273,7 +273,7 @@ __device__ __forceinline__ bool warp_wait_geq(volatile int* x, int v) {
   return ok;
 }
 
-constexpr int NCH = 4;        // chaser warps: bulges chased at once in a multi-bulge sweep
+constexpr int NCH = 6;        // chaser warps: bulges chased at once in a multi-bulge sweep
 constexpr int NMIN_MB = 30;   // active blocks below this size are swept with one bulge
 
 // barrier of the chaser warps only (named barrier 2)
@@ -344,6 +344,7 @@ __global__ void __launch_bounds__(EIG_THREADS)
   for (int j = 0; j + 2 < n; ++j) {
     const int len = n - j - 1;
     float* v = hv + (size_t)j * n;
+    const float x0 = A[(j + 1) * ld + j];   // read by every thread before the barrier
     float ss = 0.f;
     for (int r = tid; r < len; r += nth) {
       const float x = A[(j + 1 + r) * ld + j];
@@ -353,23 +354,20 @@ __global__ void __launch_bounds__(EIG_THREADS)
     for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
     if ((tid & 31) == 0) s_part[tid >> 5] = ss;
     __syncthreads();
-    if (tid == 0) {
-      float tot = 0.f;
-      for (int w2 = 0; w2 < nth / 32; ++w2) tot += s_part[w2];
-      const float x0 = A[(j + 1) * ld + j];
-      const float nx = sqrtf(tot);
-      const float alpha = x0 >= 0.f ? -nx : nx;
-      const float vv = tot - x0 * x0 + (x0 - alpha) * (x0 - alpha);
-      sh[0] = alpha;
-      sh[1] = (nx > 0.f && vv > 0.f) ? 2.f / vv : 0.f;
-      sh[2] = x0 - alpha;
-    }
-    __syncthreads();
-    const float beta = sh[1];
+    // every thread forms the reflector (the same in every thread: no second barrier)
+    float tot = 0.f;
+    for (int w2 = 0; w2 < nth / 32; ++w2) tot += s_part[w2];
+    const float nx = sqrtf(tot);
+    const float alpha = x0 >= 0.f ? -nx : nx;
+    const float vv = tot - x0 * x0 + (x0 - alpha) * (x0 - alpha);
+    const float beta = (nx > 0.f && vv > 0.f) ? 2.f / vv : 0.f;
+    // v to shared and global memory; column j takes its final value (alpha, then zeros)
+    // from the thread that read the entry
     for (int r = tid; r < len; r += nth) {
-      const float vr = (r == 0) ? sh[2] : A[(j + 1 + r) * ld + j];
+      const float vr = (r == 0) ? x0 - alpha : A[(j + 1 + r) * ld + j];
       sv[r] = vr;
       v[r] = vr;
+      if (beta != 0.f) A[(j + 1 + r) * ld + j] = (r == 0) ? alpha : 0.f;
     }
     if (tid == 0) v[n - 1] = beta;   // v has len <= n-2 entries; beta stored at the end
     __syncthreads();
@@ -421,8 +419,6 @@ __global__ void __launch_bounds__(EIG_THREADS)
         if (act)
           for (int c = sub; c < len; c += tpc) row[c] -= sc * vr[c];
       }
-      __syncthreads();
-      for (int r = 1 + tid; r <= len; r += nth) A[(j + r) * ld + j] = (r == 1) ? sh[0] : 0.f;
     }
     __syncthreads();
   }

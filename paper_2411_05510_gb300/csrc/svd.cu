@@ -61,9 +61,13 @@ __global__ void __launch_bounds__(JT, 1)
         const bool live = pi < half;
         int p = 0, q = 0;
         if (live) {
-          const int a = pi, b = n_pad - 1 - pi;
-          p = (a == 0) ? 0 : 1 + (a - 1 + rnd) % (n_pad - 1);
-          q = (b == 0) ? 0 : 1 + (b - 1 + rnd) % (n_pad - 1);
+          // (x - 1 + rnd) mod (n_pad - 1) with both terms below the modulus: one subtraction
+          const int a = pi, b = n_pad - 1 - pi, m1 = n_pad - 1;
+          int va = a - 1 + rnd, vb = b - 1 + rnd;
+          if (va >= m1) va -= m1;
+          if (vb >= m1) vb -= m1;
+          p = (a == 0) ? 0 : 1 + va;
+          q = (b == 0) ? 0 : 1 + vb;
           if (p > q) { const int t = p; p = q; q = t; }
         }
         const bool act = live && p < K && q < K;
