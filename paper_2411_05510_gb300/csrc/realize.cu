@@ -314,25 +314,29 @@ __global__ void __launch_bounds__(EIG_THREADS)
   ssi_pole* poles = p.poles + (size_t)t * p.slots_per_lag + p.slot_off[mi];
   const int n_slots = n / 2;
 
-  // ---- 1. A~_n = Rinv[:n,:n] M[:n,:n] (Rinv upper triangular); 1 x 4 strips per thread
+  // ---- 1. A~_n = Rinv[:n,:n] M[:n,:n] (Rinv upper triangular); 4 x 4 tiles per thread
   {
     const int n4 = (n + 3) / 4;
-    for (int e = tid; e < n * n4; e += nth) {
-      const int r = e / n4, c0 = (e % n4) * 4;
-      float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-      const float* rrow = Rinv + (size_t)r * k;
-      for (int j = r; j < n; ++j) {
-        const float a = rrow[j];
-        const float* mrow = M + (size_t)j * k + c0;
-        s0 = fmaf(a, mrow[0], s0);
-        if (c0 + 1 < n) s1 = fmaf(a, mrow[1], s1);
-        if (c0 + 2 < n) s2 = fmaf(a, mrow[2], s2);
-        if (c0 + 3 < n) s3 = fmaf(a, mrow[3], s3);
+    for (int tt = tid; tt < n4 * n4; tt += nth) {
+      const int r0 = 4 * (tt / n4), c0 = 4 * (tt % n4);
+      float acc[4][4] = {};
+      for (int j = r0; j < n; ++j) {
+        float ri[4], mv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          ri[u] = (r0 + u < n && j >= r0 + u) ? Rinv[(size_t)(r0 + u) * k + j] : 0.f;
+          mv[u] = (c0 + u < n) ? M[(size_t)j * k + c0 + u] : 0.f;
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int u = 0; u < 4; ++u) acc[a][u] = fmaf(ri[a], mv[u], acc[a][u]);
       }
-      A[r * ld + c0] = s0;
-      if (c0 + 1 < n) A[r * ld + c0 + 1] = s1;
-      if (c0 + 2 < n) A[r * ld + c0 + 2] = s2;
-      if (c0 + 3 < n) A[r * ld + c0 + 3] = s3;
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (r0 + a < n && c0 + u < n) A[(r0 + a) * ld + c0 + u] = acc[a][u];
     }
   }
   __syncthreads();
@@ -372,57 +376,60 @@ __global__ void __launch_bounds__(EIG_THREADS)
     if (tid == 0) v[n - 1] = beta;   // v has len <= n-2 entries; beta stored at the end
     __syncthreads();
     if (beta != 0.f) {
-      float* __restrict__ Ar = A;
-      const float* __restrict__ vr = sv;
-      // tpc consecutive lanes share one column (row) and split its dot product, as many
-      // as keep about all threads busy; loop bounds are warp-uniform around the shuffles
-      int tpc = 1;
-      while (tpc < 8 && len * tpc * 2 <= nth) tpc *= 2;
-      const int grp = tid / tpc, sub = tid % tpc, ngrp = nth / tpc;
-      // left: A[j+1:, c] -= beta v (v^T A[j+1:, c]) for c > j (column j is set below)
-      for (int base = 0; base < len; base += ngrp) {
-        const int c = j + 1 + base + grp;
-        const bool act = base + grp < len;
-        float s0 = 0.f, s1 = 0.f;
-        if (act) {
-          int r = sub;
-          for (; r + tpc < len; r += 2 * tpc) {
-            s0 = fmaf(vr[r], Ar[(j + 1 + r) * ld + c], s0);
-            s1 = fmaf(vr[r + tpc], Ar[(j + 1 + r + tpc) * ld + c], s1);
-          }
-          if (r < len) s0 = fmaf(vr[r], Ar[(j + 1 + r) * ld + c], s0);
+      // v in registers: entry c on lane c % 32, slot c / 32 (the same layout serves the rows
+      // of the left update and the columns of the right update); a warp owns whole
+      // columns (rows), forms the dot product, reduces it, and updates the elements it
+      // still holds in registers
+      constexpr int NV = (SMEM_N_MAX + 31) / 32;
+      const int hw = tid >> 5, hl = tid & 31, hnw = nth >> 5;
+      float vreg[NV];
+#pragma unroll
+      for (int q = 0; q < NV; ++q) {
+        const int c = hl + 32 * q;
+        vreg[q] = (c < len) ? sv[c] : 0.f;
+      }
+      // left: A[j+1:, c] -= beta v (v^T A[j+1:, c]) for c > j (column j is already final)
+      for (int c = j + 1 + hw; c < n; c += hnw) {
+        float a[NV];
+        float dot = 0.f;
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+          const int r = hl + 32 * q;
+          a[q] = (r < len) ? A[(j + 1 + r) * ld + c] : 0.f;
+          dot = fmaf(a[q], vreg[q], dot);
         }
-        float sc = s0 + s1;
-        for (int o = tpc >> 1; o > 0; o >>= 1) sc += __shfl_xor_sync(0xffffffffu, sc, o);
-        sc *= beta;
-        if (act)
-          for (int r = sub; r < len; r += tpc) Ar[(j + 1 + r) * ld + c] -= sc * vr[r];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+        const float sc = dot * beta;
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+          const int r = hl + 32 * q;
+          if (r < len) A[(j + 1 + r) * ld + c] = fmaf(-sc, vreg[q], a[q]);
+        }
       }
       __syncthreads();
       // right: A[r, j+1:] -= beta (A[r, j+1:] v) v^T for all rows
-      for (int base = 0; base < n; base += ngrp) {
-        const int r = base + grp;
-        const bool act = r < n;
-        float* __restrict__ row = Ar + (act ? r : 0) * ld + j + 1;
-        float s0 = 0.f, s1 = 0.f;
-        if (act) {
-          int c = sub;
-          for (; c + tpc < len; c += 2 * tpc) {
-            s0 = fmaf(row[c], vr[c], s0);
-            s1 = fmaf(row[c + tpc], vr[c + tpc], s1);
-          }
-          if (c < len) s0 = fmaf(row[c], vr[c], s0);
+      for (int r = hw; r < n; r += hnw) {
+        float a[NV];
+        float dot = 0.f;
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+          const int c = hl + 32 * q;
+          a[q] = (c < len) ? A[r * ld + j + 1 + c] : 0.f;
+          dot = fmaf(a[q], vreg[q], dot);
         }
-        float sc = s0 + s1;
-        for (int o = tpc >> 1; o > 0; o >>= 1) sc += __shfl_xor_sync(0xffffffffu, sc, o);
-        sc *= beta;
-        if (act)
-          for (int c = sub; c < len; c += tpc) row[c] -= sc * vr[c];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+        const float sc = dot * beta;
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+          const int c = hl + 32 * q;
+          if (c < len) A[r * ld + j + 1 + c] = fmaf(-sc, vreg[q], a[q]);
+        }
       }
     }
     __syncthreads();
   }
-
 
   // ---- 3b. Francis double-shift QR iteration to real Schur form T = Z^T H Z (Martin,
   //  Peters and Wilkinson's algorithm for real Hessenberg matrices, with their
