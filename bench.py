@@ -7,7 +7,11 @@ covariances R_1..R_119, Toeplitz RSVD at i = 60 (T 11160 x 11160, k = 200 + 20, 
 realisations of orders 2..200 step 2, hard and soft stability criteria.
 
 Lines printed (one JSON line on rank 0):
-  value      solves/s with the record resident in HBM (CUDA events around K solves)
+  value      solves/s with the record resident in HBM: CUDA events around K solves dealt
+             round robin to --inflight independent solvers (own context, record copy and
+             stream each), so that one solve's latency-bound stages (the single-CTA Jacobi
+             SVD, the tail of the per-order eigenproblems) overlap another's GEMMs
+  serial     the same with one solve in flight (unloaded latency, per-stage times)
   e2e        the same through ssi_submit / ssi_poll with the record in pinned host memory
              (host->device copy and the read-back of poles and mode shapes inside)
   roofline   dominant kernel (the tcgen05 lag GEMM): algorithmic FP32-equivalent flops
@@ -55,6 +59,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--inflight", type=int, default=3,
+                    help="solves in flight at once, each on its own stream and context")
     return ap.parse_args()
 
 
@@ -309,50 +315,101 @@ def main():
     w["name"] = args.workload
     Y, f_true, *_ = S.record(w, np.float32)
     l, N = Y.shape
-    Yd = torch.from_numpy(Y).to(dev)
-    ctx = P.Context(local)
-    desc = P.job_desc(Yd, w["fs"], w["lags"], w["orders"], k=w["k"], oversample=w["oversample"],
-                      q=w["q"], prec=args.prec, seed=12345)
-    n_slots, phi_floats = P.ssi_job_sizes(desc)
-    poles = torch.zeros((n_slots, P._lib.POLE_BYTES), dtype=torch.uint8, device=dev)
-    phi = torch.zeros((phi_floats,), dtype=torch.float32, device=dev)
-    stream = torch.cuda.current_stream(dev)
+    J = max(1, args.inflight)
 
-    def solve_once(d):
-        P._lib.check(P._lib.lib.ssi_solve(ctx.ptr, P._lib.ctypes.byref(d),
-                                          P._lib.ctypes.c_void_p(poles.data_ptr()),
-                                          P._lib.ctypes.c_void_p(phi.data_ptr()), None,
-                                          P._lib.ctypes.c_void_p(stream.cuda_stream)), "ssi_solve")
+    def make_lanes(prec):
+        """J independent solvers: own context (workspace), own copy of the record, own
+        outputs and own stream."""
+        lanes = []
+        for j in range(J):
+            Yj = torch.from_numpy(Y).to(dev)
+            c = P.Context(local)
+            c.set_concurrency(J)
+            d = P.job_desc(Yj, w["fs"], w["lags"], w["orders"], k=w["k"],
+                           oversample=w["oversample"], q=w["q"], prec=prec, seed=12345)
+            n_slots, phi_floats = P.ssi_job_sizes(d)
+            lanes.append(dict(ctx=c, Y=Yj, desc=d,
+                              poles=torch.zeros((n_slots, P._lib.POLE_BYTES), dtype=torch.uint8,
+                                                device=dev),
+                              phi=torch.zeros((phi_floats,), dtype=torch.float32, device=dev),
+                              stream=torch.cuda.Stream(dev)))
+        return lanes
 
-    for _ in range(args.warmup):
-        solve_once(desc)
-    P.check_sync(ctx, dev)
-    ctx.profile_read()   # drop warm-up records
-    ctx.profile(True)
+    def solve_on(ln):
+        P._lib.check(P._lib.lib.ssi_solve(ln["ctx"].ptr, P._lib.ctypes.byref(ln["desc"]),
+                                          P._lib.ctypes.c_void_p(ln["poles"].data_ptr()),
+                                          P._lib.ctypes.c_void_p(ln["phi"].data_ptr()), None,
+                                          P._lib.ctypes.c_void_p(ln["stream"].cuda_stream)),
+                     "ssi_solve")
 
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize(dev)
-    clocks = ClockSampler(local)
-    with (clocks if not args.no_clocks else _Null()):
-        ev[0].record(stream)
-        for s in range(args.steps):
-            solve_once(desc)
-            ev[s + 1].record(stream)
+    def warm(lanes):
+        for ln in lanes:
+            for _ in range(args.warmup):
+                solve_on(ln)
+        for ln in lanes:
+            P.check_sync(ln["ctx"], dev)
+
+    def run_inflight(lanes, K, sampler=None):
+        """K solves dealt round robin over the lanes, each lane's solves in order on its
+        stream, the lanes' solves overlapping on the device.  Returns the wall time from the
+        first launch to the last completion (CUDA events) and each solve's own duration."""
+        s0 = lanes[0]["stream"]
+        st = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(K)]
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        if world > 1:
+            dist.barrier()
         torch.cuda.synchronize(dev)
-    if world > 1:
-        dist.barrier()
-    P.check_sync(ctx, dev)
-    ctx.profile(False)
-    stage_ms, stage_cnt, launches = ctx.profile_read()
-    step_ms = [ev[s].elapsed_time(ev[s + 1]) for s in range(args.steps)]
-    total_ms = ev[0].elapsed_time(ev[args.steps])
+        with (sampler if sampler is not None else _Null()):
+            e0.record(s0)
+            for ln in lanes[1:]:
+                ln["stream"].wait_event(e0)
+            for s in range(K):
+                ln = lanes[s % len(lanes)]
+                st[s][0].record(ln["stream"])
+                solve_on(ln)
+                st[s][1].record(ln["stream"])
+            for ln in lanes[1:]:
+                ej = torch.cuda.Event()
+                ej.record(ln["stream"])
+                s0.wait_event(ej)
+            e1.record(s0)
+            torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+        for ln in lanes:
+            P.check_sync(ln["ctx"], dev)
+        return e0.elapsed_time(e1), [a.elapsed_time(b2) for a, b2 in st]
+
+    lanes = make_lanes(args.prec)
+    warm(lanes)
+    for ln in lanes:
+        ln["ctx"].profile_read()   # drop warm-up records
+        ln["ctx"].profile(True)     # counts this context's launches (events only, no sync)
+    clocks = ClockSampler(local)
+    total_ms, step_ms = run_inflight(lanes, args.steps, None if args.no_clocks else clocks)
+    launches = 0
+    for ln in lanes:
+        ln["ctx"].profile(False)
+        launches += ln["ctx"].profile_read()[2]
     total_ms = max_over_ranks(total_ms, dev)
     value = whole_job_rate(args.steps, world, total_ms)
 
+    # one solve at a time on lane 0: the latency of an unloaded solve and the per-stage
+    # times (CUDA events around each stage on the solve's stream)
+    ctx = lanes[0]["ctx"]
+    n_ser = max(3, min(args.steps, 10))
+    ctx.set_concurrency(1)
+    solve_on(lanes[0])   # the first solve with the full-device QR grid, untimed
+    ctx.profile(True)
+    ser_total, ser_ms = run_inflight(lanes[:1], n_ser)
+    ctx.profile(False)
+    ctx.set_concurrency(J)
+    stage_ms, stage_cnt, _ = ctx.profile_read()
+    ser_total = max_over_ranks(ser_total, dev)
+
     # sanity: the record's modes are found
-    rec = P.poles_to_numpy(poles)
+    rec = P.poles_to_numpy(lanes[0]["poles"])
     top = rec[-(w["orders"][-1] // 2):]
     hc = top[(top["flags"] & 8) != 0]
     found = int(sum(np.min(np.abs(hc["f_hz"] - f0) / f0) < 1e-2 for f0 in f_true)) if len(hc) else 0
@@ -372,20 +429,29 @@ def main():
             peak = 72.0
             peak_note = "FP32 FMA rate 72 TFLOP/s measured by a probe on this GB300"
         traffic, tnote = stored_traffic(args.workload)
+        cfg = config_of(w, args.prec)
+        cfg["inflight"] = J
         out = {
             "metric": "SSI solves/s", "value": value, "unit": "solves/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "bf16" if args.prec == "split_bf16" else "f32", "data": "synthetic",
-            "config": config_of(w, args.prec),
-            "latency_ms": {"p50": pct(step_ms, 50), "p99": pct(step_ms, 99), "kind": "device"},
+            "config": cfg,
+            "latency_ms": {"p50": pct(step_ms, 50), "p99": pct(step_ms, 99),
+                           "kind": f"device, each solve from its first launch to its last "
+                                   f"completion with {J} solves in flight"},
+            "serial": {"value": whole_job_rate(n_ser, world, ser_total), "unit": "solves/s",
+                       "solves": n_ser,
+                       "latency_ms": {"p50": pct(ser_ms, 50), "p99": pct(ser_ms, 99),
+                                      "kind": "device, one solve in flight"}},
             "roofline": {"bound": "tensor" if args.prec == "split_bf16" else "alu",
                          "kernel": "k_lag_gemm_tc" if args.prec == "split_bf16" else "k_lag_gemm_fp32",
                          "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": traffic, "peak_note": peak_note,
                          "flops_per_launch": flops, "ms_per_launch": gemm_ms,
+                         "timing": "CUDA events around the launch on its stream, serial solves",
                          "traffic_note": tnote},
-            "stages_ms_per_step": {k: v / args.steps for k, v in stage_ms.items()},
+            "stages_ms_per_step": {k: v / n_ser for k, v in stage_ms.items()},
             "gpu_launches": launches,
             "modes_found": f"{found}/{len(f_true)}",
         }
@@ -393,16 +459,17 @@ def main():
             out["clocks"] = clocks.summary()
 
     # e2e through the serving API, record in pinned host memory: latency with one job in
-    # flight, throughput with the jobs submitted back to back (two serving slots, so the
-    # host->device copy of one job overlaps the compute of the other)
+    # flight, throughput with the jobs submitted back to back (J serving slots, so the
+    # host->device copies and the compute of the jobs overlap)
     if not args.no_e2e:
         Yh = torch.from_numpy(Y).pin_memory()
-        P.ssi_serve_config(ctx, 2, 64)
+        P.ssi_serve_config(ctx, J, 64)
         desc_h = P.job_desc(Yh, w["fs"], w["lags"], w["orders"], k=w["k"],
                             oversample=w["oversample"], q=w["q"], prec=args.prec, seed=12345)
-        n_e2e = max(3, min(args.steps, 10))
+        n_slots, phi_floats = P.ssi_job_sizes(desc_h)
+        n_e2e = max(3 * J, min(args.steps, 12))
         lat = []
-        for s in range(2 + n_e2e):
+        for s in range(2 + 3):
             jid = P.ssi_submit(ctx, desc_h)
             _, _, lu = P.ssi_poll(ctx, jid, -1)
             P.ssi_release(ctx, jid)
@@ -426,27 +493,32 @@ def main():
                                          "kind": "submit to completion, one job in flight"},
                           "queued_latency_ms": {"p50": pct(lat_q, 50), "p99": pct(lat_q, 99),
                                                 "jobs": n_e2e},
-                          "api": "ssi_submit/ssi_poll (2 slots), record in pinned host memory, "
-                                 "host clock around all jobs"}
+                          "api": f"ssi_submit/ssi_poll ({J} slots), record in pinned host "
+                                 f"memory, host clock around all jobs"}
 
-    # the plain FP32 path of the same pipeline on the same GPU
+    # the plain FP32 path of the same pipeline on the same GPU, measured the same way
     if not args.no_fp32 and args.prec == "split_bf16":
-        d32 = P.job_desc(Yd, w["fs"], w["lags"], w["orders"], k=w["k"], oversample=w["oversample"],
-                         q=w["q"], prec="fp32", seed=12345)
-        solve_once(d32)
-        torch.cuda.synchronize(dev)
-        ts = []
-        for s in range(3):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            solve_once(d32)
-            e1.record(stream)
-            torch.cuda.synchronize(dev)
-            ts.append(e0.elapsed_time(e1))
+        for ln in lanes[1:]:
+            ln["ctx"].close()
+        lanes = lanes[:1]
+        l32 = make_lanes("fp32")
+        saved_warmup = args.warmup
+        args.warmup = 1
+        warm(l32)
+        args.warmup = saved_warmup
+        K32 = 2 * J
+        t32, ms32 = run_inflight(l32, K32)
+        s32, ms32s = run_inflight(l32[:1], 2)
+        t32 = max_over_ranks(t32, dev)
+        for ln in l32:
+            ln["ctx"].close()
         if rank == 0:
-            out["fp32_path"] = {"value": 1e3 / statistics.mean(ts), "unit": "solves/s",
-                                "latency_ms": {"p50": pct(ts, 50), "p99": pct(ts, 99)},
-                                "split_bf16_speedup": value / world / (1e3 / statistics.mean(ts))}
+            v32 = whole_job_rate(K32, world, t32)
+            out["fp32_path"] = {"value": v32, "unit": "solves/s",
+                                "latency_ms": {"p50": pct(ms32, 50), "p99": pct(ms32, 99),
+                                               "kind": f"{J} solves in flight"},
+                                "serial_latency_ms": pct(ms32s, 50),
+                                "split_bf16_speedup": value / v32}
 
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         tot, parts = oracle_sample_estimate(Y.astype(np.float64), w)
@@ -458,7 +530,8 @@ def main():
                                "stage_s": {k: round(v, 3) for k, v in parts.items()}}
     if rank == 0:
         print(json.dumps(out), flush=True)
-    ctx.close()
+    for ln in lanes:
+        ln["ctx"].close()
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()

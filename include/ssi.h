@@ -65,6 +65,16 @@ int ssi_version(void);
 /* Device memory currently held by the context (bytes). */
 size_t ssi_memory_in_use(const ssi_ctx* ctx);
 
+/* Concurrency hint: how many solves are expected on the device at once (several
+ * contexts, or the slots of this context's serving loop).  With more than one, the
+ * cooperative QR of the range finder (Sec. 2.2) takes half the SMs, two row chunks per
+ * CTA, so that two solves' QR grids execute side by side and other SMs stay free for a
+ * third solve's GEMMs and eigenproblems; with one it takes every SM.  Results are
+ * bit-identical either way (the QR reductions run over fixed row chunks in a fixed
+ * order).  Default 1; ssi_serve_config sets it to max_slots.  Takes effect for launches
+ * made after the call.  SSI_E_INVALID for a null context or solves_in_flight < 1. */
+ssi_status ssi_set_concurrency(ssi_ctx* ctx, int solves_in_flight);
+
 /* Instrumentation.  ssi_profile(ctx, 1) makes the direct (non-serving) calls of the
  * context record a CUDA event pair around each stage on the call's stream; this adds
  * no synchronisation.  ssi_profile_read synchronises on the recorded events and

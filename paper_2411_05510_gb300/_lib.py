@@ -57,6 +57,7 @@ PROTOTYPES = {
     "ssi_last_error": (_c.c_char_p, []),
     "ssi_version": (_c.c_int, []),
     "ssi_memory_in_use": (_c.c_size_t, [_P]),
+    "ssi_set_concurrency": (_c.c_int, [_P, _c.c_int]),
     "ssi_profile": (_c.c_int, [_P, _c.c_int]),
     "ssi_profile_read": (_c.c_int, [_P, _c.POINTER(_c.c_double), _c.POINTER(_c.c_int64), _c.c_int,
                                     _c.POINTER(_c.c_int64)]),

@@ -62,6 +62,10 @@ class Context:
     def memory_in_use(self) -> int:
         return int(lib.ssi_memory_in_use(self.ptr))
 
+    def set_concurrency(self, solves_in_flight: int) -> None:
+        """ssi_set_concurrency: how many solves share the device at once."""
+        check(lib.ssi_set_concurrency(self.ptr, int(solves_in_flight)), "ssi_set_concurrency")
+
     STAGES = ["split", "lag_gemm", "lag_reduce", "sketch_gemm", "qr", "small_svd", "gram_factor",
               "eig", "stability", "other", "eig_vectors"]
 

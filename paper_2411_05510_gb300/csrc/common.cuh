@@ -94,6 +94,7 @@ struct ssi_ctx {
   int* dev_status = nullptr;  // device status word of the direct calls
   ssi::Serving* serving = nullptr;
   ssi::JobBuffers* solve = nullptr;  // buffers of ssi_solve
+  std::atomic<int> inflight{1};        // solves expected to share the device at once
   std::atomic<long long> launches{0};  // kernels launched through this context
   bool prof_on = false;               // per-stage CUDA-event timers
   std::mutex prof_mu;

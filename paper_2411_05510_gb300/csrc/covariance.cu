@@ -25,6 +25,8 @@ constexpr int ATOM_BYTES = BT * 128;  // one 64-channel x BT box, bf16
 constexpr int A_ATOMS = 4;        // two M tiles of 128 rows per CTA
 constexpr int TC_THREADS = 192;   // warp 0 TMA, warp 1 MMA, warps 2..5 epilogue
 constexpr uint64_t WAIT_NS = 2000000000ull;  // bounded waits: 2 s
+constexpr int UR = 4;             // ring of work-unit indices from the producer to the MMA
+                                  // issuer and the epilogue
 
 struct LagGemmParams {
   int n_atoms;          // max_lag * l_pad / 64
@@ -36,6 +38,7 @@ struct LagGemmParams {
   int l_pad;
   int ld_out;           // l_pad
   long long split_stride;  // floats between splits in the partial buffer
+  int* unit_counter;    // zero before the launch: units handed out beyond the first wave
 };
 
 // ------------------------------------------------------------------ split/transpose
@@ -75,9 +78,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   unsigned char* smem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
-  // bars[0..S) full, [S..2S) empty, [2S] tmem_full, [2S+1] tmem_empty
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 2);
+  // bars[0..S) full, [S..2S) empty, [2S] tmem_full, [2S+1] tmem_empty,
+  // [2S+2..2S+2+UR) unit_full, [2S+2+UR..2S+2+2UR) unit_empty
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 2 + 2 * UR);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  volatile int* s_unit = abort_flag + 1;   // UR entries
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t smem_base = bw::smem_u32(smem);
@@ -86,6 +91,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   auto empty_bar = [&](int s) { return bar_base + 8u * (STAGES + s); };
   const uint32_t tfull_bar = bar_base + 8u * (2 * STAGES);
   const uint32_t tempty_bar = bar_base + 8u * (2 * STAGES + 1);
+  auto unit_full = [&](int r) { return bar_base + 8u * (2 * STAGES + 2 + r); };
+  auto unit_empty = [&](int r) { return bar_base + 8u * (2 * STAGES + 2 + UR + r); };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -94,6 +101,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
     bw::mbar_init(tfull_bar, 1);
     bw::mbar_init(tempty_bar, 4);
+    for (int r = 0; r < UR; ++r) {
+      bw::mbar_init(unit_full(r), 1);
+      bw::mbar_init(unit_empty(r), 5);   // the MMA issuer and the four epilogue warps
+    }
     *abort_flag = 0;
     bw::fence_mbar_init();
     bw::tma_prefetch_desc(&tm_hi);
@@ -134,7 +145,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       int armed_phase[STAGES];
       for (int s = 0; s < STAGES; ++s) armed_phase[s] = -1;
       bool ok = true;
-      for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
+      // dynamic schedule: the first unit is blockIdx.x, later ones come from a global
+      // counter, claimed one unit ahead so that the atomic's latency is hidden; a CTA
+      // that starts late (the SMs busy with other work) simply takes fewer units
+      int u = blockIdx.x;
+      int u_next = (u < n_units) ? (int)gridDim.x + atomicAdd(p.unit_counter, 1) : n_units;
+      for (int uc = 0; ok; ++uc) {
+        const int r = uc % UR;
+        if (!wait(unit_empty(r), ((uc / UR) & 1) ^ 1)) { ok = false; break; }
+        s_unit[r] = (u < n_units) ? u : -1;
+        bw::mbar_arrive(unit_full(r));
+        if (u >= n_units) break;
         const int mp = u % p.n_mp;
         const int v = u / p.n_mp;
         const int nt = v % p.n_nt;
@@ -166,6 +187,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             bw::tma_load_2d(sb + 2 * A_BYTES + B_BYTES + b * ATOM_BYTES, &tm_lo, full_bar(s), ch, t);
           }
         }
+        u = u_next;
+        if (u < n_units) u_next = (int)gridDim.x + atomicAdd(p.unit_counter, 1);
       }
       if (*abort_flag) {
         // do not leave the CTA while TMA writes into its shared memory are in flight
@@ -181,9 +204,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
-      int g = 0, uc = 0;
+      int g = 0;
       bool ok = true;
-      for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x, ++uc) {
+      for (int uc = 0; ok; ++uc) {
+        const int r = uc % UR;
+        if (!wait(unit_full(r), (uc / UR) & 1)) { ok = false; break; }
+        const int u = s_unit[r];
+        bw::mbar_arrive(unit_empty(r));
+        if (u < 0) break;
         const int v = u / p.n_mp;
         const int sp = v / p.n_nt;
         const int t0 = sp * p.rows_per_split;
@@ -222,8 +250,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   } else {
     // ------------------------------------------------------------ epilogue (warps 2..5)
     const int quarter = warp & 3;   // TMEM lane quarter this warp may access
-    int uc = 0;
-    for (int u = blockIdx.x; u < n_units; u += gridDim.x, ++uc) {
+    for (int uc = 0;; ++uc) {
+      int u = -1;
+      if (lane == 0) {
+        const int r = uc % UR;
+        if (wait(unit_full(r), (uc / UR) & 1)) {
+          u = s_unit[r];
+          bw::mbar_arrive(unit_empty(r));
+        }
+      }
+      u = __shfl_sync(0xffffffffu, u, 0);
+      if (u < 0) break;
       const int mp = u % p.n_mp;
       const int v = u / p.n_mp;
       const int nt = v % p.n_nt;
@@ -349,7 +386,7 @@ ssi_status launch_tc(const CUtensorMap& thi, const CUtensorMap& tlo, const LagGe
                      float* partial, int* status, int grid, cudaStream_t stream) {
   constexpr int STAGES = tc_stages<NB>();
   constexpr int STAGE_BYTES = (2 * A_ATOMS + 2 * NB) * ATOM_BYTES;
-  const size_t smem = 1024 + (size_t)STAGES * STAGE_BYTES + 8 * (2 * STAGES + 2) + 16;
+  const size_t smem = 1024 + (size_t)STAGES * STAGE_BYTES + 8 * (2 * STAGES + 2 + 2 * UR) + 8 + 4 * UR;
   auto kern = k_lag_gemm_tc<NB, STAGES>;
   SSI_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   kern<<<grid, TC_THREADS, smem, stream>>>(thi, tlo, p, partial, status);
@@ -385,6 +422,7 @@ CovPlan cov_plan(int l, int64_t N, int max_lag, ssi_precision prec, int num_sms)
     w.add<__nv_bfloat16>((size_t)c.n_rows * c.l_pad);
   }
   w.add<float>((size_t)c.n_split * max_lag * c.l_pad * c.l_pad);
+  if (prec == SSI_PREC_SPLIT_BF16) w.add<int>(64);   // the lag GEMM's unit counter
   c.ws_bytes = w.bytes;
   return c;
 }
@@ -397,7 +435,11 @@ ssi_status covariances_ws(ssi_ctx* ctx, Workspace& ws, const CovPlan& c, const f
     __nv_bfloat16* hi = ws.take<__nv_bfloat16>((size_t)c.n_rows * c.l_pad);
     __nv_bfloat16* lo = ws.take<__nv_bfloat16>((size_t)c.n_rows * c.l_pad);
     float* partial = ws.take<float>((size_t)c.n_split * split_stride);
-    if (!hi || !lo || !partial) { set_error("covariances: workspace too small"); return SSI_E_NOMEM; }
+    int* counter = ws.take<int>(64);
+    if (!hi || !lo || !partial || !counter) {
+      set_error("covariances: workspace too small");
+      return SSI_E_NOMEM;
+    }
     {
       ProfScope ps(ctx, ST_SPLIT, stream);
       dim3 blk(32, 8), grd((unsigned)ceil_div(c.n_rows, 32), c.l_pad / 32);
@@ -420,6 +462,8 @@ ssi_status covariances_ws(ssi_ctx* ctx, Workspace& ws, const CovPlan& c, const f
     p.l_pad = c.l_pad;
     p.ld_out = c.l_pad;
     p.split_stride = split_stride;
+    p.unit_counter = counter;
+    SSI_CUDA(cudaMemsetAsync(counter, 0, sizeof(int), stream));
     const int n_units = p.n_mp * p.n_nt * p.n_split;
     const int grid = std::min(n_units, ctx->num_sms);
     {

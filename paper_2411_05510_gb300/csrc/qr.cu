@@ -1,8 +1,12 @@
 // Economy QR of a tall-skinny FP32 matrix (the sketch re-orthonormalisation of Sec. 2.2,
 // "(Q, R) = qr(Y, 0)" of Algorithm 1).
 //
-// One cooperative persistent kernel.  Each CTA owns a contiguous block of rows;
-// columns are processed in panels of 32:
+// One cooperative persistent kernel.  The rows are cut into a fixed number of chunks
+// (one per SM of the device) and each CTA owns one or two consecutive chunks: one when
+// the solve has the device to itself, two when several solves share it (half the
+// SMs, so that two solves' QR grids run side by side).  Every reduction is taken over
+// per-chunk partials in a fixed order, so the result does not depend on the grid.
+// Columns are processed in panels of 32:
 //   pass 1:  W  = Y_j - Q_{<j} (Q_{<j}^T Y_j);   W  = W R1^{-1},  R1 = chol(W^T W)
 //   pass 2:  W' = W   - Q_{<j} (Q_{<j}^T W);     Q_j = W' R2^{-1}, R2 = chol(W'^T W')
 // (block classical Gram-Schmidt with re-orthogonalisation, each panel made
@@ -39,6 +43,8 @@ struct QrParams {
   int* status;
   int* abort_flag;
   int lds;             // leading dimension of the rows staged in shared memory (0: not staged)
+  int n_chunks;        // row chunks (partials per reduction)
+  int chunks_per_cta;
 };
 
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
@@ -82,25 +88,30 @@ __device__ bool grid_sync(const QrParams& p, GridBar& gb) {
   return ok_s != 0;
 }
 
-// Sum over the P per-CTA partials of entries [e0, e1) (stride `stride` between partials):
-// this CTA's threads split the partials of each entry, then combine in shared memory.
+// Sum over the C per-chunk partials of entries [e0, e1) (stride `stride` between
+// partials).  Each entry is summed by RED_PER threads, thread q taking partials
+// q, q + RED_PER, ... in order, and their sums are added in order: the same rounding
+// whatever the grid and however the entries are split between CTAs.
+constexpr int RED_PER = 8;
 template <typename T>
-__device__ void slice_reduce(const T* part, size_t stride, int P, int e0, int e1, T* out) {
+__device__ void slice_reduce(const T* part, size_t stride, int C, int e0, int e1, T* out) {
   __shared__ double red[QR_THREADS];
   const int E = e1 - e0;
   if (E <= 0) return;
-  const int per = max(1, QR_THREADS / E);       // threads per entry
+  constexpr int EPP = QR_THREADS / RED_PER;   // entries per pass
   const int tid = threadIdx.x;
-  for (int base = 0; base < E; base += QR_THREADS / per) {
-    const int le = base + tid / per, sub = tid % per;
+  const int sub = tid % RED_PER;
+  for (int base = 0; base < E; base += EPP) {
+    const int le = base + tid / RED_PER;
     double s = 0.0;
-    if (tid / per < QR_THREADS / per && le < E)
-      for (int c = sub; c < P; c += per) s += (double)part[(size_t)c * stride + e0 + le];
+    if (le < E)
+      for (int c = sub; c < C; c += RED_PER) s += (double)part[(size_t)c * stride + e0 + le];
     red[tid] = s;
     __syncthreads();
-    if (sub == 0 && tid / per < QR_THREADS / per && le < E) {
+    if (sub == 0 && le < E) {
       double t = 0.0;
-      for (int q = 0; q < per; ++q) t += red[tid + q];
+#pragma unroll
+      for (int q = 0; q < RED_PER; ++q) t += red[tid + q];
       out[e0 + le] = (T)t;
     }
     __syncthreads();
@@ -190,15 +201,18 @@ __global__ void __launch_bounds__(QR_THREADS, 1)   // one CTA per SM (cooperativ
   gb.gen = *(volatile unsigned*)&p.bar[1];
 
   const int P = gridDim.x;
-  const int rows_per = (p.rows + P - 1) / P;
-  const int r0 = blockIdx.x * rows_per;
-  const int r1 = min(p.rows, r0 + rows_per);
+  const int C = p.n_chunks;
+  const int rows_per = (p.rows + C - 1) / C;            // rows of a chunk
+  const int c0 = blockIdx.x * p.chunks_per_cta;         // this CTA's chunks [c0, c1)
+  const int c1 = min(C, c0 + p.chunks_per_cta);
+  const int r0 = min(p.rows, c0 * rows_per);
+  const int r1 = min(p.rows, c1 * rows_per);
   const int nr = max(0, r1 - r0);
   const int tid = threadIdx.x;
   // local rows: shared memory when they fit, else the matrix itself
   float* Ab = p.lds ? s_rows : p.A + (size_t)r0 * p.ld;
   const int ldb = p.lds ? p.lds : p.ld;
-  float* sC = p.lds ? s_rows + (size_t)rows_per * p.lds : nullptr;   // projection (j0 x PB)
+  float* sC = p.lds ? s_rows + (size_t)rows_per * p.chunks_per_cta * p.lds : nullptr;   // projection (j0 x PB)
   if (p.lds) {
     for (int e = tid; e < nr * p.ncols; e += QR_THREADS) {
       const int rr = e / p.ncols, c = e % p.ncols;
@@ -213,12 +227,16 @@ __global__ void __launch_bounds__(QR_THREADS, 1)   // one CTA per SM (cooperativ
       if (j0 > 0) {
         // ---- C = Q[:, :j0]^T W, partial over this CTA's rows
         const int nC = j0 * PB;
-        float* myC = p.red_c + (size_t)blockIdx.x * p.ncols * PB;
-        // 4 x 4 outputs per thread: rows a0..a0+3 of Q^T, columns b0..b0+3 of the panel
-        for (int tt = tid; tt < (j0 / 4) * (PB / 4); tt += QR_THREADS) {
+        // 4 x 4 outputs per thread: rows a0..a0+3 of Q^T, columns b0..b0+3 of the panel;
+        // one partial per chunk
+        const int n_tiles = (j0 / 4) * (PB / 4);
+        for (int tc = tid; tc < n_tiles * (c1 - c0); tc += QR_THREADS) {
+          const int ch = tc / n_tiles, tt = tc % n_tiles;
+          float* myC = p.red_c + (size_t)(c0 + ch) * p.ncols * PB;
+          const int lr0 = ch * rows_per, lr1 = min(nr, lr0 + rows_per);
           const int a0 = 4 * (tt / (PB / 4)), b0 = 4 * (tt % (PB / 4));
           float acc[4][4] = {};
-          for (int rr = 0; rr < nr; ++rr) {
+          for (int rr = lr0; rr < lr1; ++rr) {
             const float* row = Ab + rr * ldb;
             float qa[4], wb[4];
 #pragma unroll
@@ -240,7 +258,7 @@ __global__ void __launch_bounds__(QR_THREADS, 1)   // one CTA per SM (cooperativ
         {
           const int per_cta = (nC + P - 1) / P;
           const int e0 = blockIdx.x * per_cta, e1 = min(nC, e0 + per_cta);
-          slice_reduce<float>(p.red_c, (size_t)p.ncols * PB, P, e0, e1, p.fin_c);
+          slice_reduce<float>(p.red_c, (size_t)p.ncols * PB, C, e0, e1, p.fin_c);
         }
         if (!grid_sync(p, gb)) return;
         const float* C = p.fin_c;
@@ -288,12 +306,14 @@ __global__ void __launch_bounds__(QR_THREADS, 1)   // one CTA per SM (cooperativ
       }
       // ---- Gram G = W^T W in double-FP32 over local rows
       {
-        double* myG = p.red_g + (size_t)blockIdx.x * PB * PB;
-        for (int e = tid; e < PB * PB; e += QR_THREADS) {
+        for (int ec = tid; ec < PB * PB * (c1 - c0); ec += QR_THREADS) {
+          const int ch = ec / (PB * PB), e = ec % (PB * PB);
+          double* myG = p.red_g + (size_t)(c0 + ch) * PB * PB;
+          const int lr0 = ch * rows_per, lr1 = min(nr, lr0 + rows_per);
           const int a = e / PB, b = e % PB;
           float sh = 0.f, sl = 0.f;
           if (a < w && b < w && a <= b) {
-            for (int rr = 0; rr < nr; ++rr) {
+            for (int rr = lr0; rr < lr1; ++rr) {
               const float x = Ab[rr * ldb + j0 + a];
               const float y = Ab[rr * ldb + j0 + b];
               const float pr = x * y;
@@ -310,7 +330,7 @@ __global__ void __launch_bounds__(QR_THREADS, 1)   // one CTA per SM (cooperativ
         {
           const int per_cta = (PB * PB + P - 1) / P;
           const int e0 = blockIdx.x * per_cta, e1 = min(PB * PB, e0 + per_cta);
-          slice_reduce<double>(p.red_g, (size_t)PB * PB, P, e0, e1, p.fin_g);
+          slice_reduce<double>(p.red_g, (size_t)PB * PB, C, e0, e1, p.fin_g);
         }
         if (!grid_sync(p, gb)) return;
       }
@@ -399,16 +419,23 @@ ssi_status qr_launch(ssi_ctx* ctx, Workspace& ws, float* A, int rows, int ncols,
   p.ncols = ncols;
   p.ld = ld;
   p.Rout = Rout;
-  int P = std::max(1, std::min<int>(ctx->num_sms, (int)ceil_div(rows, 32)));
-  const int rows_per = (int)ceil_div(rows, P);
+  // chunks: one per SM (fixed for the device and the shape, so the result is too); a CTA
+  // per chunk when the solve has the device to itself, a CTA per two chunks when several
+  // solves share it
+  const int C = std::max(1, std::min<int>(ctx->num_sms, (int)ceil_div(rows, 32)));
+  const int cpc = ctx->inflight > 1 ? 2 : 1;
+  const int P = (int)ceil_div(C, cpc);
+  p.n_chunks = C;
+  p.chunks_per_cta = cpc;
+  const int rows_per = (int)ceil_div(rows, C) * cpc;   // rows of a CTA
   const int lds = ncols | 1;   // odd leading dimension: rows of a warp fall in distinct banks
   size_t smem = ((size_t)rows_per * lds + (size_t)ncols * PB) * sizeof(float);
-  if (smem > 160 * 1024) {
+  if (smem > 192 * 1024) {
     smem = 0;   // rows stay in global memory
   } else {
     p.lds = lds;
   }
-  SSI_CUDA(cudaFuncSetAttribute(k_qr_bcgs2, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
+  SSI_CUDA(cudaFuncSetAttribute(k_qr_bcgs2, cudaFuncAttributeMaxDynamicSharedMemorySize, 192 * 1024));
   p.red_c = ws.take<float>((size_t)ctx->num_sms * ncols * PB);
   p.fin_c = ws.take<float>((size_t)ncols * PB);
   p.red_g = ws.take<double>((size_t)ctx->num_sms * PB * PB);

@@ -192,6 +192,13 @@ void ssi_destroy(ssi_ctx* ctx) {
 
 size_t ssi_memory_in_use(const ssi_ctx* ctx) { return ctx ? ctx->in_use : 0; }
 
+ssi_status ssi_set_concurrency(ssi_ctx* ctx, int solves_in_flight) {
+  SSI_CHECK(ctx, "ssi_set_concurrency: null context");
+  SSI_CHECK(solves_in_flight >= 1, "ssi_set_concurrency: solves_in_flight < 1");
+  ctx->inflight.store(solves_in_flight);
+  return SSI_OK;
+}
+
 ssi_status ssi_profile(ssi_ctx* ctx, int enable) {
   SSI_CHECK(ctx, "ssi_profile: null context");
   std::lock_guard<std::mutex> g(ctx->prof_mu);

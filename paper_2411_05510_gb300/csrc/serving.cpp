@@ -279,6 +279,7 @@ extern "C" ssi_status ssi_serve_config(ssi_ctx* ctx, int max_slots, int max_queu
   SSI_CHECK(max_slots >= 1 && max_slots <= 64 && max_queue >= 1, "ssi_serve_config: bad limits");
   SSI_CUDA(cudaSetDevice(ctx->device));
   serving_destroy(ctx);
+  ctx->inflight.store(max_slots);
   return serving_start(ctx, max_slots, max_queue);
 }
 

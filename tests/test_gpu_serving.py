@@ -124,3 +124,33 @@ def test_job_larger_than_budget_fails_cleanly(P, jobs):
         P.ssi_release(ctx, jid)
     finally:
         ctx.close()
+
+
+def test_concurrency_hint_leaves_results_bit_identical(P, jobs):
+    """ssi_set_concurrency changes the QR grid (every SM, or half of them with two row
+    chunks per CTA); the reductions run over the same chunks in the same order, so the
+    poles and mode shapes must be the same bit for bit."""
+    w, Y, _ = max(jobs, key=lambda j: j[0]["l"] * j[0]["N"])
+    out = []
+    for n in (1, 3):
+        ctx = P.Context(0)
+        try:
+            ctx.set_concurrency(n)
+            poles, phi, S = P.ssi_solve(ctx, _desc(P, w, torch.from_numpy(Y).cuda()))
+            P.check_sync(ctx)
+            out.append((poles.cpu().numpy().tobytes(), phi.cpu().numpy().tobytes(),
+                        S.cpu().numpy().tobytes()))
+        finally:
+            ctx.close()
+    assert out[0][2] == out[1][2]
+    assert out[0][0] == out[1][0]
+    assert out[0][1] == out[1][1]
+
+
+def test_concurrency_hint_rejects_bad_values(P):
+    ctx = P.Context(0)
+    try:
+        with pytest.raises(P.SsiError):
+            ctx.set_concurrency(0)
+    finally:
+        ctx.close()
