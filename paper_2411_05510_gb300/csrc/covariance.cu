@@ -140,64 +140,89 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 
   if (warp == 0) {
     // ------------------------------------------------------------ TMA producer
-    if (lane == 0) {
-      int g = 0;
-      int armed_phase[STAGES];
-      for (int s = 0; s < STAGES; ++s) armed_phase[s] = -1;
-      bool ok = true;
-      // dynamic schedule: the first unit is blockIdx.x, later ones come from a global
-      // counter, claimed one unit ahead so that the atomic's latency is hidden; a CTA
-      // that starts late (the SMs busy with other work) simply takes fewer units
-      int u = blockIdx.x;
-      int u_next = (u < n_units) ? (int)gridDim.x + atomicAdd(p.unit_counter, 1) : n_units;
-      for (int uc = 0; ok; ++uc) {
-        const int r = uc % UR;
-        if (!wait(unit_empty(r), ((uc / UR) & 1) ^ 1)) { ok = false; break; }
-        s_unit[r] = (u < n_units) ? u : -1;
-        bw::mbar_arrive(unit_full(r));
-        if (u >= n_units) break;
-        const int mp = u % p.n_mp;
-        const int v = u / p.n_mp;
-        const int nt = v % p.n_nt;
-        const int sp = v / p.n_nt;
-        const int t0 = sp * p.rows_per_split;
-        const int t1 = min(p.N, t0 + p.rows_per_split);
-        const int n_st = (t1 - t0 + BT - 1) / BT;
-        const int cpl = p.l_pad / 64;
-        int n_valid = min(A_ATOMS, p.n_atoms - mp * A_ATOMS);
-        for (int st = 0; st < n_st; ++st, ++g) {
-          const int s = g % STAGES;
-          const uint32_t ph = (g / STAGES) & 1;
-          if (!wait(empty_bar(s), ph ^ 1)) { ok = false; break; }
-          const uint32_t bytes = (uint32_t)(2 * n_valid + 2 * NB) * ATOM_BYTES;
-          bw::mbar_arrive_expect_tx(full_bar(s), bytes);
-          armed_phase[s] = (int)ph;
-          const uint32_t sb = smem_base + s * STAGE_BYTES;
-          const int t = t0 + st * BT;
-          for (int a = 0; a < n_valid; ++a) {
-            const int atom = mp * A_ATOMS + a;
-            const int lag = atom / cpl + 1;
-            const int ch = (atom % cpl) * 64;
-            bw::tma_load_2d(sb + a * ATOM_BYTES, &tm_hi, full_bar(s), ch, t + lag);
-            bw::tma_load_2d(sb + A_BYTES + a * ATOM_BYTES, &tm_lo, full_bar(s), ch, t + lag);
-          }
-          for (int b = 0; b < NB; ++b) {
-            const int ch = nt * NT + b * 64;
-            bw::tma_load_2d(sb + 2 * A_BYTES + b * ATOM_BYTES, &tm_hi, full_bar(s), ch, t);
-            bw::tma_load_2d(sb + 2 * A_BYTES + B_BYTES + b * ATOM_BYTES, &tm_lo, full_bar(s), ch, t);
+    // Lane 0 takes the barrier waits and the transaction count; the boxes of a stage
+    // (2 per A atom, 2 per B atom) are issued by one lane each, so that their issue
+    // does not serialise on one thread.
+    int g = 0;
+    int armed_phase[STAGES];
+    for (int s = 0; s < STAGES; ++s) armed_phase[s] = -1;
+    bool ok = true;
+    // dynamic schedule: the first unit is blockIdx.x, later ones come from a global
+    // counter, claimed one unit ahead so that the atomic's latency is hidden; a CTA
+    // that starts late (the SMs busy with other work) simply takes fewer units
+    int u = blockIdx.x;
+    int u_next = n_units;
+    if (lane == 0 && u < n_units) u_next = (int)gridDim.x + atomicAdd(p.unit_counter, 1);
+    for (int uc = 0; ok; ++uc) {
+      const int r = uc % UR;
+      int okl = 1;
+      if (lane == 0) {
+        okl = wait(unit_empty(r), ((uc / UR) & 1) ^ 1) ? 1 : 0;
+        if (okl) {
+          s_unit[r] = (u < n_units) ? u : -1;
+          bw::mbar_arrive(unit_full(r));
+        }
+      }
+      okl = __shfl_sync(0xffffffffu, okl, 0);
+      if (!okl) { ok = false; break; }
+      if (u >= n_units) break;
+      const int mp = u % p.n_mp;
+      const int v = u / p.n_mp;
+      const int nt = v % p.n_nt;
+      const int sp = v / p.n_nt;
+      const int t0 = sp * p.rows_per_split;
+      const int t1 = min(p.N, t0 + p.rows_per_split);
+      const int n_st = (t1 - t0 + BT - 1) / BT;
+      const int cpl = p.l_pad / 64;
+      const int n_valid = min(A_ATOMS, p.n_atoms - mp * A_ATOMS);
+      // this lane's box: A atom (lane / 2) for lanes < 2 A_ATOMS, B atom for the next 2 NB
+      const bool lo_half = (lane & 1) != 0;
+      const bool a_box = lane < 2 * n_valid;
+      const bool b_box = lane >= 2 * A_ATOMS && lane < 2 * A_ATOMS + 2 * NB;
+      int box_ch = 0, box_lag = 0;
+      uint32_t box_off = 0;
+      if (a_box) {
+        const int atom = mp * A_ATOMS + (lane >> 1);
+        box_lag = atom / cpl + 1;
+        box_ch = (atom % cpl) * 64;
+        box_off = (lo_half ? A_BYTES : 0) + (lane >> 1) * ATOM_BYTES;
+      } else if (b_box) {
+        const int bb = (lane - 2 * A_ATOMS) >> 1;
+        box_ch = nt * NT + bb * 64;
+        box_off = 2 * A_BYTES + (lo_half ? B_BYTES : 0) + bb * ATOM_BYTES;
+      }
+      const CUtensorMap* box_map = lo_half ? &tm_lo : &tm_hi;
+      for (int st = 0; st < n_st; ++st, ++g) {
+        const int s = g % STAGES;
+        const uint32_t ph = (g / STAGES) & 1;
+        int okw = 1;
+        if (lane == 0) {
+          okw = wait(empty_bar(s), ph ^ 1) ? 1 : 0;
+          if (okw) {
+            const uint32_t bytes = (uint32_t)(2 * n_valid + 2 * NB) * ATOM_BYTES;
+            bw::mbar_arrive_expect_tx(full_bar(s), bytes);
+            armed_phase[s] = (int)ph;
           }
         }
+        okw = __shfl_sync(0xffffffffu, okw, 0);
+        if (!okw) { ok = false; break; }
+        if (a_box || b_box)
+          bw::tma_load_2d(smem_base + s * STAGE_BYTES + box_off, box_map, full_bar(s), box_ch,
+                          t0 + st * BT + box_lag);
+      }
+      if (lane == 0) {
         u = u_next;
         if (u < n_units) u_next = (int)gridDim.x + atomicAdd(p.unit_counter, 1);
       }
-      if (*abort_flag) {
-        // do not leave the CTA while TMA writes into its shared memory are in flight
-        for (int s = 0; s < STAGES; ++s) {
-          if (armed_phase[s] < 0) continue;
-          const uint64_t t0 = bw::global_ns();
-          while (!bw::mbar_try_wait(full_bar(s), (uint32_t)armed_phase[s]) &&
-                 bw::global_ns() - t0 < 50000000ull) {
-          }
+      u = __shfl_sync(0xffffffffu, u, 0);
+    }
+    if (lane == 0 && *abort_flag) {
+      // do not leave the CTA while TMA writes into its shared memory are in flight
+      for (int s = 0; s < STAGES; ++s) {
+        if (armed_phase[s] < 0) continue;
+        const uint64_t t0 = bw::global_ns();
+        while (!bw::mbar_try_wait(full_bar(s), (uint32_t)armed_phase[s]) &&
+               bw::global_ns() - t0 < 50000000ull) {
         }
       }
     }

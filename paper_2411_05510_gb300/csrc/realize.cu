@@ -388,64 +388,43 @@ __global__ void __launch_bounds__(EIG_THREADS)
         const int c = hl + 32 * q;
         vreg[q] = (c < len) ? sv[c] : 0.f;
       }
-      // left: A[j+1:, c] -= beta v (v^T A[j+1:, c]) for c > j (column j is already
-      // final); two columns per pass of a warp, for two independent reductions in flight
-      for (int c = j + 1 + hw; c < n; c += 2 * hnw) {
-        const int c2 = c + hnw;
-        const bool two = c2 < n;   // warp-uniform
-        float a[NV], b[NV];
-        float d1 = 0.f, d2 = 0.f;
+      // left: A[j+1:, c] -= beta v (v^T A[j+1:, c]) for c > j (column j is already final)
+      for (int c = j + 1 + hw; c < n; c += hnw) {
+        float a[NV];
+        float dot = 0.f;
 #pragma unroll
         for (int q = 0; q < NV; ++q) {
           const int r = hl + 32 * q;
           a[q] = (r < len) ? A[(j + 1 + r) * ld + c] : 0.f;
-          b[q] = (two && r < len) ? A[(j + 1 + r) * ld + c2] : 0.f;
-          d1 = fmaf(a[q], vreg[q], d1);
-          d2 = fmaf(b[q], vreg[q], d2);
+          dot = fmaf(a[q], vreg[q], dot);
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          d1 += __shfl_xor_sync(0xffffffffu, d1, o);
-          d2 += __shfl_xor_sync(0xffffffffu, d2, o);
-        }
-        const float s1 = d1 * beta, s2 = d2 * beta;
+        for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+        const float sc = dot * beta;
 #pragma unroll
         for (int q = 0; q < NV; ++q) {
           const int r = hl + 32 * q;
-          if (r < len) {
-            A[(j + 1 + r) * ld + c] = fmaf(-s1, vreg[q], a[q]);
-            if (two) A[(j + 1 + r) * ld + c2] = fmaf(-s2, vreg[q], b[q]);
-          }
+          if (r < len) A[(j + 1 + r) * ld + c] = fmaf(-sc, vreg[q], a[q]);
         }
       }
       __syncthreads();
-      // right: A[r, j+1:] -= beta (A[r, j+1:] v) v^T for all rows, two rows per pass
-      for (int r = hw; r < n; r += 2 * hnw) {
-        const int r2 = r + hnw;
-        const bool two = r2 < n;   // warp-uniform
-        float a[NV], b[NV];
-        float d1 = 0.f, d2 = 0.f;
+      // right: A[r, j+1:] -= beta (A[r, j+1:] v) v^T for all rows
+      for (int r = hw; r < n; r += hnw) {
+        float a[NV];
+        float dot = 0.f;
 #pragma unroll
         for (int q = 0; q < NV; ++q) {
           const int c = hl + 32 * q;
           a[q] = (c < len) ? A[r * ld + j + 1 + c] : 0.f;
-          b[q] = (two && c < len) ? A[r2 * ld + j + 1 + c] : 0.f;
-          d1 = fmaf(a[q], vreg[q], d1);
-          d2 = fmaf(b[q], vreg[q], d2);
+          dot = fmaf(a[q], vreg[q], dot);
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          d1 += __shfl_xor_sync(0xffffffffu, d1, o);
-          d2 += __shfl_xor_sync(0xffffffffu, d2, o);
-        }
-        const float s1 = d1 * beta, s2 = d2 * beta;
+        for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+        const float sc = dot * beta;
 #pragma unroll
         for (int q = 0; q < NV; ++q) {
           const int c = hl + 32 * q;
-          if (c < len) {
-            A[r * ld + j + 1 + c] = fmaf(-s1, vreg[q], a[q]);
-            if (two) A[r2 * ld + j + 1 + c] = fmaf(-s2, vreg[q], b[q]);
-          }
+          if (c < len) A[r * ld + j + 1 + c] = fmaf(-sc, vreg[q], a[q]);
         }
       }
     }
