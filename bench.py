@@ -100,17 +100,20 @@ def load_peaks():
 
 def kernel_source_hash():
     """Hash of the lag-GEMM kernel's own source (its template definition, the constants and
-    parameter block above it) and of the tcgen05/TMA helpers it uses: the stored DRAM
-    traffic stays valid while these are unchanged."""
+    parameter block above it, the time-split plan) and of the tcgen05/TMA helpers it uses:
+    the stored DRAM traffic stays valid while these are unchanged."""
     csrc = os.path.join(ROOT, "paper_2411_05510_gb300", "csrc")
     with open(os.path.join(csrc, "covariance.cu")) as fh:
         src = fh.read()
     a = src.index("constexpr int BT = ")
     b = src.index("template <int NB, int STAGES>\n__global__ void __launch_bounds__(TC_THREADS, 1)")
     c = src.index("\n}\n", b) + 3
+    d = src.index("CovPlan cov_plan(")
+    e = src.index("\n}\n", d) + 3
     h = hashlib.sha256()
     h.update(src[a:src.index("// ------------------------------------------------------------------ split/transpose")].encode())
     h.update(src[b:c].encode())
+    h.update(src[d:e].encode())   # the split plan sets the partial writes
     with open(os.path.join(csrc, "blackwell.cuh"), "rb") as fh:
         h.update(fh.read())
     return h.hexdigest()[:16]

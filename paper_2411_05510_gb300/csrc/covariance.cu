@@ -382,7 +382,18 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-// ------------------------------------------------------------------ FP64 reduction
+// ------------------------------------------------------------------ split reduction
+// Sum of the per-split FP32 partials with Knuth's two-sum: hi + lo carries the running
+// sum to about twice FP32 precision using FP32 adds only (FP64 runs at a small fraction
+// of the FP32 rate on this part); the order over splits is fixed, so the result is
+// deterministic.  Four partials are loaded ahead of their adds.
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
+  const float s = hi + x;
+  const float bb = s - hi;
+  lo += (hi - (s - bb)) + (x - bb);
+  hi = s;
+}
+
 __global__ void k_reduce_partials(const float* __restrict__ partial, int n_split,
                                   long long split_stride, int l, int l_pad, int max_lag, int N,
                                   double* __restrict__ R) {
@@ -392,10 +403,21 @@ __global__ void k_reduce_partials(const float* __restrict__ partial, int n_split
     const int b = (int)(e % l);
     const int a = (int)((e / l) % l);
     const int k = (int)(e / ((long long)l * l)) + 1;
-    const long long off = ((long long)(k - 1) * l_pad + a) * l_pad + b;
-    double s = 0.0;
-    for (int sp = 0; sp < n_split; ++sp) s += (double)partial[sp * split_stride + off];
-    R[e] = s / (double)(N - k);
+    const float* src = partial + ((long long)(k - 1) * l_pad + a) * l_pad + b;
+    float hi = 0.f, lo = 0.f;
+    int sp = 0;
+    for (; sp + 4 <= n_split; sp += 4) {
+      const float x0 = __ldcs(src + (long long)sp * split_stride);
+      const float x1 = __ldcs(src + (long long)(sp + 1) * split_stride);
+      const float x2 = __ldcs(src + (long long)(sp + 2) * split_stride);
+      const float x3 = __ldcs(src + (long long)(sp + 3) * split_stride);
+      two_sum_acc(hi, lo, x0);
+      two_sum_acc(hi, lo, x1);
+      two_sum_acc(hi, lo, x2);
+      two_sum_acc(hi, lo, x3);
+    }
+    for (; sp < n_split; ++sp) two_sum_acc(hi, lo, __ldcs(src + (long long)sp * split_stride));
+    R[e] = ((double)hi + (double)lo) / (double)(N - k);
   }
 }
 
@@ -430,16 +452,29 @@ CovPlan cov_plan(int l, int64_t N, int max_lag, ssi_precision prec, int num_sms)
   c.n_nt = (int)ceil_div(l64, 256);
   c.l_pad = (int)round_up(l, 64 * c.n_nt);
   c.nb = c.l_pad / 64 / c.n_nt;
-  // time split: FP32 partial sums over at most ~8K samples, at least ~6 waves of units
+  // time split: the persistent grid takes units dynamically, so its critical path is
+  // (waves of units) x (samples per unit + the unit's epilogue, which costs about as much
+  // as 512 samples of MMAs whatever the tile).  Choose the split length (a multiple of
+  // BT, 512..16384 samples per FP32 partial sum) that minimises it; on ties the longer
+  // split wins (fewer partials to write and reduce).
   const int n_atoms = max_lag * c.l_pad / 64;
   const int n_mp = (int)ceil_div(n_atoms, A_ATOMS);
-  int64_t units_per_split = (int64_t)n_mp * c.n_nt;
-  int64_t want_splits = ceil_div(6LL * num_sms, units_per_split);
-  int64_t rows = round_up(ceil_div(N, std::max<int64_t>(1, want_splits)), BT);
-  rows = std::min<int64_t>(rows, 8192);
-  rows = std::max<int64_t>(rows, 512);
-  c.rows_per_split = (int)rows;
-  c.n_split = (int)ceil_div(N, rows);
+  const int64_t units_per_split = (int64_t)n_mp * c.n_nt;
+  int64_t best_rows = 0, best_cost = 0;
+  const int64_t s_lo = std::max<int64_t>(1, ceil_div(N, 16384));
+  const int64_t s_hi = std::max<int64_t>(s_lo, ceil_div(N, 512));
+  for (int64_t sp = s_lo; sp <= s_hi; ++sp) {
+    const int64_t rows = std::max<int64_t>(512, round_up(ceil_div(N, sp), BT));
+    const int64_t n_sp = ceil_div(N, rows);
+    const int64_t waves = ceil_div(units_per_split * n_sp, (int64_t)std::max(1, num_sms));
+    const int64_t cost = waves * (rows + 512);
+    if (best_rows == 0 || cost < best_cost || (cost == best_cost && rows > best_rows)) {
+      best_rows = rows;
+      best_cost = cost;
+    }
+  }
+  c.rows_per_split = (int)best_rows;
+  c.n_split = (int)ceil_div(N, best_rows);
   WsPlan w;
   c.n_rows = std::max<int64_t>(N, 64);
   if (prec == SSI_PREC_SPLIT_BF16) {

@@ -220,59 +220,70 @@ __global__ void __launch_bounds__(TG_THREADS, 1)
   };
 
   if (warp == 0) {
-    if (lane == 0) {
-      int g = 0;
-      int armed_phase[STAGES];
-      for (int s = 0; s < STAGES; ++s) armed_phase[s] = -1;
-      bool ok = true;
-      for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
-        const int mt = u % p.n_mt;
-        const int nt = (u / p.n_mt) % p.n_nt;
-        int j_begin, n_st;
-        unit_krange(u, j_begin, n_st);
-        const int m0 = mt * 128;
-        for (int st = 0; st < n_st; ++st, ++g) {
-          const int s = g % STAGES;
-          const uint32_t ph = (g / STAGES) & 1;
-          if (!wait(empty_bar(s), ph ^ 1)) { ok = false; break; }
-          bw::mbar_arrive_expect_tx(full_bar(s), (uint32_t)STAGE_BYTES);
-          armed_phase[s] = (int)ph;
-          const uint32_t sb = smem_base + s * STAGE_BYTES;
-          const int j0 = j_begin + st * SBK;
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const int mrow = m0 + 64 * h;
-            int lag, x, y;
-            if (MODE == 0) {
-              const int a = mrow / p.l_pad, c0 = mrow % p.l_pad;
-              const int b = j0 / p.l_pad, d0 = j0 % p.l_pad;
-              lag = p.i + a - b;
-              x = d0;
-              y = (lag - 1) * p.l_pad + c0;
-            } else {
-              const int a = j0 / p.l_pad, c0 = j0 % p.l_pad;
-              const int b = mrow / p.l_pad, d0 = mrow % p.l_pad;
-              lag = p.i + a - b;
-              x = d0;
-              y = (lag - 1) * p.l_pad + c0;
-            }
-            bw::tma_load_2d(sb + h * BOX_BYTES, &tA_hi, full_bar(s), x, y);
-            bw::tma_load_2d(sb + A_BYTES + h * BOX_BYTES, &tA_lo, full_bar(s), x, y);
-          }
-          for (int b = 0; b < NB; ++b) {
-            const int x = nt * NT + b * 64;
-            bw::tma_load_2d(sb + 2 * A_BYTES + b * BOX_BYTES, &tB_hi, full_bar(s), x, j0);
-            bw::tma_load_2d(sb + 2 * A_BYTES + B_BYTES + b * BOX_BYTES, &tB_lo, full_bar(s), x, j0);
+    // Lane 0 takes the barrier waits and the transaction count; each box of a stage
+    // (A: 2 halves x hi/lo, B: NB atoms x hi/lo) is issued by its own lane.
+    int g = 0;
+    int armed_phase[STAGES];
+    for (int s = 0; s < STAGES; ++s) armed_phase[s] = -1;
+    bool ok = true;
+    const bool lo_half = (lane & 1) != 0;
+    const bool a_box = lane < 4;
+    const bool b_box = lane >= 4 && lane < 4 + 2 * NB;
+    const CUtensorMap* a_map = lo_half ? &tA_lo : &tA_hi;
+    const CUtensorMap* b_map = lo_half ? &tB_lo : &tB_hi;
+    for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
+      const int mt = u % p.n_mt;
+      const int nt = (u / p.n_mt) % p.n_nt;
+      int j_begin, n_st;
+      unit_krange(u, j_begin, n_st);
+      const int m0 = mt * 128;
+      for (int st = 0; st < n_st; ++st, ++g) {
+        const int s = g % STAGES;
+        const uint32_t ph = (g / STAGES) & 1;
+        int okw = 1;
+        if (lane == 0) {
+          okw = wait(empty_bar(s), ph ^ 1) ? 1 : 0;
+          if (okw) {
+            bw::mbar_arrive_expect_tx(full_bar(s), (uint32_t)STAGE_BYTES);
+            armed_phase[s] = (int)ph;
           }
         }
-      }
-      if (*abort_flag) {
-        for (int s = 0; s < STAGES; ++s) {
-          if (armed_phase[s] < 0) continue;
-          const uint64_t t0 = bw::global_ns();
-          while (!bw::mbar_try_wait(full_bar(s), (uint32_t)armed_phase[s]) &&
-                 bw::global_ns() - t0 < 50000000ull) {
+        okw = __shfl_sync(0xffffffffu, okw, 0);
+        if (!okw) { ok = false; break; }
+        const uint32_t sb = smem_base + s * STAGE_BYTES;
+        const int j0 = j_begin + st * SBK;
+        if (a_box) {
+          const int h = lane >> 1;
+          const int mrow = m0 + 64 * h;
+          int lag, x, y;
+          if (MODE == 0) {
+            const int a = mrow / p.l_pad, c0 = mrow % p.l_pad;
+            const int b = j0 / p.l_pad, d0 = j0 % p.l_pad;
+            lag = p.i + a - b;
+            x = d0;
+            y = (lag - 1) * p.l_pad + c0;
+          } else {
+            const int a = j0 / p.l_pad, c0 = j0 % p.l_pad;
+            const int b = mrow / p.l_pad, d0 = mrow % p.l_pad;
+            lag = p.i + a - b;
+            x = d0;
+            y = (lag - 1) * p.l_pad + c0;
           }
+          bw::tma_load_2d(sb + (lo_half ? A_BYTES : 0) + h * BOX_BYTES, a_map, full_bar(s), x, y);
+        } else if (b_box) {
+          const int bb = (lane - 4) >> 1;
+          const int x = nt * NT + bb * 64;
+          bw::tma_load_2d(sb + 2 * A_BYTES + (lo_half ? B_BYTES : 0) + bb * BOX_BYTES, b_map,
+                          full_bar(s), x, j0);
+        }
+      }
+    }
+    if (lane == 0 && *abort_flag) {
+      for (int s = 0; s < STAGES; ++s) {
+        if (armed_phase[s] < 0) continue;
+        const uint64_t t0 = bw::global_ns();
+        while (!bw::mbar_try_wait(full_bar(s), (uint32_t)armed_phase[s]) &&
+               bw::global_ns() - t0 < 50000000ull) {
         }
       }
     }
