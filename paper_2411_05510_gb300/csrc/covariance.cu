@@ -386,7 +386,7 @@ __global__ void __launch_bounds__(256)
 // Sum of the per-split FP32 partials with Knuth's two-sum: hi + lo carries the running
 // sum to about twice FP32 precision using FP32 adds only (FP64 runs at a small fraction
 // of the FP32 rate on this part); the order over splits is fixed, so the result is
-// deterministic.  Four partials are loaded ahead of their adds.
+// deterministic.  Eight partials are loaded ahead of their adds.
 __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float x) {
   const float s = hi + x;
   const float bb = s - hi;
@@ -406,15 +406,12 @@ __global__ void k_reduce_partials(const float* __restrict__ partial, int n_split
     const float* src = partial + ((long long)(k - 1) * l_pad + a) * l_pad + b;
     float hi = 0.f, lo = 0.f;
     int sp = 0;
-    for (; sp + 4 <= n_split; sp += 4) {
-      const float x0 = __ldcs(src + (long long)sp * split_stride);
-      const float x1 = __ldcs(src + (long long)(sp + 1) * split_stride);
-      const float x2 = __ldcs(src + (long long)(sp + 2) * split_stride);
-      const float x3 = __ldcs(src + (long long)(sp + 3) * split_stride);
-      two_sum_acc(hi, lo, x0);
-      two_sum_acc(hi, lo, x1);
-      two_sum_acc(hi, lo, x2);
-      two_sum_acc(hi, lo, x3);
+    for (; sp + 8 <= n_split; sp += 8) {
+      float x[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) x[u] = __ldcs(src + (long long)(sp + u) * split_stride);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) two_sum_acc(hi, lo, x[u]);
     }
     for (; sp < n_split; ++sp) two_sum_acc(hi, lo, __ldcs(src + (long long)sp * split_stride));
     R[e] = ((double)hi + (double)lo) / (double)(N - k);
@@ -540,7 +537,7 @@ ssi_status covariances_ws(ssi_ctx* ctx, Workspace& ws, const CovPlan& c, const f
     }
     {
       ProfScope ps(ctx, ST_LAG_REDUCE, stream);
-      k_reduce_partials<<<ctx->num_sms * 4, 256, 0, stream>>>(partial, c.n_split, split_stride, c.l,
+      k_reduce_partials<<<ctx->num_sms * 8, 256, 0, stream>>>(partial, c.n_split, split_stride, c.l,
                                                               c.l_pad, c.max_lag, (int)c.N, R);
       SSI_CUDA(cudaGetLastError());
     }
@@ -558,7 +555,7 @@ ssi_status covariances_ws(ssi_ctx* ctx, Workspace& ws, const CovPlan& c, const f
     }
     {
       ProfScope ps(ctx, ST_LAG_REDUCE, stream);
-      k_reduce_partials<<<ctx->num_sms * 4, 256, 0, stream>>>(partial, c.n_split, split_stride, c.l,
+      k_reduce_partials<<<ctx->num_sms * 8, 256, 0, stream>>>(partial, c.n_split, split_stride, c.l,
                                                               c.l_pad, c.max_lag, (int)c.N, R);
       SSI_CUDA(cudaGetLastError());
     }

@@ -104,8 +104,19 @@ __device__ void slice_reduce(const T* part, size_t stride, int C, int e0, int e1
   for (int base = 0; base < E; base += EPP) {
     const int le = base + tid / RED_PER;
     double s = 0.0;
-    if (le < E)
-      for (int c = sub; c < C; c += RED_PER) s += (double)part[(size_t)c * stride + e0 + le];
+    if (le < E) {
+      // eight partials loaded ahead of their adds (same order of addition)
+      for (int cb = sub; cb < C; cb += 8 * RED_PER) {
+        T v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int c = cb + u * RED_PER;
+          v[u] = (c < C) ? part[(size_t)c * stride + e0 + le] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) s += (double)v[u];
+      }
+    }
     red[tid] = s;
     __syncthreads();
     if (sub == 0 && le < E) {
@@ -304,27 +315,77 @@ __global__ void __launch_bounds__(QR_THREADS, 1)   // one CTA per SM (cooperativ
         }
         __syncthreads();
       }
-      // ---- Gram G = W^T W in double-FP32 over local rows
+      // ---- Gram G = W^T W over each chunk's rows: the 36 upper 4 x 4 tiles of the 32 x 32
+      // panel Gram (the lower triangle is never read).  Four adjacent lanes per (chunk,
+      // tile) take every fourth row and are merged by shuffles in a fixed order, so a
+      // chunk's sum is the same whatever the number of chunks per CTA.  First pass
+      // (the panel may be ill-conditioned): double-FP32, exact products by fma and sums by
+      // two-sum.  Second pass (the panel is orthonormal to ~1e-4, G close to I): FP32.
       {
-        for (int ec = tid; ec < PB * PB * (c1 - c0); ec += QR_THREADS) {
-          const int ch = ec / (PB * PB), e = ec % (PB * PB);
+        const int nch = c1 - c0;
+        constexpr int RG = 4;
+        const int rg = tid % RG;
+        // every lane runs the same number of iterations (the merge below shuffles across
+        // the whole warp); slots past the last (chunk, tile) accumulate nothing
+        const int n_combo = 36 * nch;
+        const int n_iter = (n_combo + QR_THREADS / RG - 1) / (QR_THREADS / RG);
+        for (int it = 0; it < n_iter; ++it) {
+          const int combo = tid / RG + it * (QR_THREADS / RG);
+          const bool valid = combo < n_combo;
+          const int ch = valid ? combo / 36 : 0;
+          int t = valid ? combo % 36 : 0, ta = 0;
+          while (t >= 8 - ta) { t -= 8 - ta; ++ta; }
+          const int a0 = 4 * ta, b0 = 4 * (ta + t);
+          const int lr0 = ch * rows_per, lr1 = valid ? min(nr, lr0 + rows_per) : lr0;
           double* myG = p.red_g + (size_t)(c0 + ch) * PB * PB;
-          const int lr0 = ch * rows_per, lr1 = min(nr, lr0 + rows_per);
-          const int a = e / PB, b = e % PB;
-          float sh = 0.f, sl = 0.f;
-          if (a < w && b < w && a <= b) {
-            for (int rr = lr0; rr < lr1; ++rr) {
-              const float x = Ab[rr * ldb + j0 + a];
-              const float y = Ab[rr * ldb + j0 + b];
-              const float pr = x * y;
-              const float pe = fmaf(x, y, -pr);
-              float s, e2;
-              two_sum(sh, pr, s, e2);
-              sh = s;
-              sl += e2 + pe;
+          float sh[4][4] = {}, sl[4][4] = {};
+          for (int rr = lr0 + rg; rr < lr1; rr += RG) {
+            float xa[4], yb[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              xa[u] = (a0 + u < w) ? Ab[rr * ldb + j0 + a0 + u] : 0.f;
+              yb[u] = (b0 + u < w) ? Ab[rr * ldb + j0 + b0 + u] : 0.f;
+            }
+            if (pass == 0) {
+#pragma unroll
+              for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                  const float pr = xa[i] * yb[u];
+                  const float pe = fmaf(xa[i], yb[u], -pr);
+                  float s2, e2;
+                  two_sum(sh[i][u], pr, s2, e2);
+                  sh[i][u] = s2;
+                  sl[i][u] += e2 + pe;
+                }
+            } else {
+#pragma unroll
+              for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int u = 0; u < 4; ++u) sh[i][u] = fmaf(xa[i], yb[u], sh[i][u]);
             }
           }
-          myG[e] = (double)sh + (double)sl;
+#pragma unroll
+          for (int o = 1; o < RG; o <<= 1)
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                const float h2 = __shfl_xor_sync(0xffffffffu, sh[i][u], o);
+                const float l2 = __shfl_xor_sync(0xffffffffu, sl[i][u], o);
+                float s2, e2;
+                two_sum(sh[i][u], h2, s2, e2);
+                sh[i][u] = s2;
+                sl[i][u] += l2 + e2;
+              }
+          if (valid && rg == 0) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+              for (int u = 0; u < 4; ++u)
+                myG[(a0 + i) * PB + b0 + u] =
+                    (a0 + i <= b0 + u) ? (double)sh[i][u] + (double)sl[i][u] : 0.0;
+          }
         }
         if (!grid_sync(p, gb)) return;
         {
