@@ -288,7 +288,7 @@ __device__ __forceinline__ void helper_sync(int nthreads) {
 
 __device__ __forceinline__ float sgnf(float a, float b) { return b >= 0.f ? fabsf(a) : -fabsf(a); }
 
-__global__ void __launch_bounds__(EIG_THREADS)
+__global__ void __launch_bounds__(EIG_THREADS, 1)
     k_eig(EigParams p) {
   extern __shared__ float smem[];
   // work item: largest orders first
@@ -619,38 +619,11 @@ __global__ void __launch_bounds__(EIG_THREADS)
       const int cur = wdx & 1;
       float* Zb = Zbuf + cur * WN * (WN + 4);
       const int e = min(b + WN, n);
-      // hand-off checks (warp 0), then the previous window's right update in the columns of
-      // this window (warp 0) and the identity factor
+      // hand-off checks and the identity factor (warp 0), then the previous window's left
+      // transformation on its rows in the columns of this window (every chaser)
       if (cw == 0) {
         bool ok = warp_wait_geq(&s_taken, wdx - 1);
         if (ok && cont) ok = warp_wait_geq(&s_applied, wdx - 1);
-        if (ok && cont) {
-          const int pb = s_desc[cur ^ 1][0], pe = s_desc[cur ^ 1][1], pc = s_desc[cur ^ 1][3];
-          const int pw = pe - pb;
-          const float* Zp = Zbuf + (cur ^ 1) * WN * (WN + 4);
-          const int c = pe + lane0;
-          const bool mine = c < pc;
-          float out[WN];
-#pragma unroll
-          for (int i2 = 0; i2 < WN; ++i2) out[i2] = 0.f;
-          for (int j2 = 0; j2 < pw; ++j2) {
-            const float a = mine ? A[(pb + j2) * ld + c] : 0.f;
-            const float4* zr = reinterpret_cast<const float4*>(Zp + j2 * (WN + 4));
-#pragma unroll
-            for (int q4 = 0; q4 < WN / 4; ++q4) {
-              const float4 z = zr[q4];
-              out[4 * q4] = fmaf(z.x, a, out[4 * q4]);
-              out[4 * q4 + 1] = fmaf(z.y, a, out[4 * q4 + 1]);
-              out[4 * q4 + 2] = fmaf(z.z, a, out[4 * q4 + 2]);
-              out[4 * q4 + 3] = fmaf(z.w, a, out[4 * q4 + 3]);
-            }
-          }
-          if (mine) {
-#pragma unroll
-            for (int i2 = 0; i2 < WN; ++i2)
-              if (i2 < pw) A[(pb + i2) * ld + c] = out[i2];
-          }
-        }
         for (int q = 0; q < WN; ++q) Zb[lane0 * (WN + 4) + q] = (q == lane0) ? 1.f : 0.f;
         if (lane0 == 0) s_wok[cur] = ok ? 1 : 0;   // rewritten two windows later, after
       }                                              // every chaser passed the next barrier
@@ -658,6 +631,35 @@ __global__ void __launch_bounds__(EIG_THREADS)
       if (!s_wok[cur]) {
         fail = 2;
         break;
+      }
+      if (cont) {
+        // H[pb:pe, pe:pc] = Zp^T H[pb:pe, pe:pc]: lane = column, chaser cw = output rows
+        // [RPW cw, RPW cw + RPW); every chaser reads the block before any writes it
+        constexpr int RPW = (WN + NCH - 1) / NCH;
+        const int pb = s_desc[cur ^ 1][0], pe = s_desc[cur ^ 1][1], pc = s_desc[cur ^ 1][3];
+        const int pw = pe - pb;
+        const float* Zp = Zbuf + (cur ^ 1) * WN * (WN + 4);
+        const int c = pe + lane0;
+        const bool mine = c < pc;
+        const int i0 = cw * RPW;
+        float out[RPW];
+#pragma unroll
+        for (int r = 0; r < RPW; ++r) out[r] = 0.f;
+#pragma unroll 4
+        for (int j2 = 0; j2 < pw; ++j2) {
+          const float a = mine ? A[(pb + j2) * ld + c] : 0.f;
+          const float* zr = Zp + j2 * (WN + 4) + i0;
+#pragma unroll
+          for (int r = 0; r < RPW; ++r)
+            if (i0 + r < WN) out[r] = fmaf(zr[r], a, out[r]);
+        }
+        chaser_sync();
+        if (mine) {
+#pragma unroll
+          for (int r = 0; r < RPW; ++r)
+            if (i0 + r < pw) A[(pb + i0 + r) * ld + c] = out[r];
+        }
+        chaser_sync();
       }
       int kend;       // positions chased in this window end before kend (single bulge)
       bool next;      // the sweep continues in another window
