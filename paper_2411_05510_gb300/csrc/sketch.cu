@@ -117,22 +117,27 @@ __global__ void k_to_bf16(const float* __restrict__ x, long long n, __nv_bfloat1
   }
 }
 
+// Sum of the per-split FP32 partials of a sketch product: Knuth's two-sum in FP32 (hi +
+// lo, about twice FP32 precision) in a fixed split order, eight partials loaded ahead of
+// their adds; FP64 arithmetic on this part runs at a small fraction of the FP32 rate.
 __global__ void k_sum_splits(const float* __restrict__ part, int n_split, long long stride,
                              float* __restrict__ out) {
-  // four loads in flight per thread (independent partial sums)
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < stride;
        e += (long long)gridDim.x * blockDim.x) {
-    double s[4] = {0.0, 0.0, 0.0, 0.0};
-    int sp = 0;
-    for (; sp + 4 <= n_split; sp += 4) {
-      float v[4];
+    float hi = 0.f, lo = 0.f;
+    for (int sp = 0; sp < n_split; sp += 8) {
+      float v[8];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) v[u] = __ldcs(part + (sp + u) * stride + e);
+      for (int u = 0; u < 8; ++u) v[u] = (sp + u < n_split) ? __ldcs(part + (sp + u) * stride + e) : 0.f;
 #pragma unroll
-      for (int u = 0; u < 4; ++u) s[u] += (double)v[u];
+      for (int u = 0; u < 8; ++u) {
+        const float s2 = hi + v[u];
+        const float bb = s2 - hi;
+        lo += (hi - (s2 - bb)) + (v[u] - bb);
+        hi = s2;
+      }
     }
-    for (; sp < n_split; ++sp) s[sp & 3] += (double)__ldcs(part + sp * stride + e);
-    out[e] = (float)((s[0] + s[1]) + (s[2] + s[3]));
+    out[e] = hi + lo;
   }
 }
 
