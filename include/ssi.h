@@ -224,8 +224,11 @@ ssi_status ssi_stabilize(ssi_ctx* ctx, int n_lags, int n_orders, const int* orde
 /* ------------------------------------------------------------------------------
  * One complete solve (stages a-d) of one record: covariances up to 2*max(lags)-1,
  * then per lag the Toeplitz RSVD, then the realisations of every (lag, order)
- * and the stability checks.  All work is enqueued on `stream`; nothing is
- * synchronised.  Y may be device memory (y_on_host = 0) or host memory
+ * and the stability checks.  All work is ordered after earlier work on `stream`, and
+ * later work on `stream` is ordered after all of it; nothing is synchronised.  With
+ * several lags the per-lag RSVDs (independent once R exists, Sec. 2.3) run on up to
+ * four internal streams of the context, forked from and joined back to `stream`
+ * through events.  Y may be device memory (y_on_host = 0) or host memory
  * (y_on_host = 1, pinned for overlap), in which case it is copied in on `stream`.
  * ---------------------------------------------------------------------------- */
 typedef struct {

@@ -130,9 +130,11 @@ struct RsvdPlan {
   size_t ws_bytes;
 };
 RsvdPlan rsvd_plan(int l, int i, int k, int oversample, int q, int num_sms);
+// shared_device: other work (another lag of the same solve) runs beside this one, so the
+// QR takes the half-device grid
 ssi_status toeplitz_rsvd_ws(ssi_ctx* ctx, Workspace& ws, const RsvdPlan& plan, const double* R,
                             uint64_t seed, ssi_precision prec, float* U, float* S,
-                            int* dev_status, cudaStream_t stream);
+                            int* dev_status, cudaStream_t stream, bool shared_device);
 
 struct RealizePlan {
   int n_lags, l, k, n_orders, max_order;

@@ -41,10 +41,14 @@ JobPlan plan_job(const ssi_job_desc* j, int num_sms) {
   p.max_lag = 2 * j->lags[j->n_lags - 1] - 1;
   p.cov = cov_plan(j->l, j->N, p.max_lag, (ssi_precision)j->prec, num_sms);
   size_t ws = p.cov.ws_bytes;
+  // the RSVDs of several lags run at once, each in its own region of the scratch
+  size_t rs_total = 0;
   for (int t = 0; t < j->n_lags; ++t) {
     p.rs.push_back(rsvd_plan(j->l, j->lags[t], j->k, j->oversample, j->q, num_sms));
-    ws = std::max(ws, p.rs.back().ws_bytes);
+    p.rs_off.push_back(rs_total);
+    rs_total += (p.rs.back().ws_bytes + 255) & ~size_t(255);
   }
+  ws = std::max(ws, rs_total);
   std::vector<int> lags(j->lags, j->lags + j->n_lags), orders(j->orders, j->orders + j->n_orders);
   p.rz = realize_plan(j->n_lags, lags.data(), j->l, j->k, orders.data(), j->n_orders);
   ws = std::max(ws, p.rz.ws_bytes);
@@ -91,9 +95,34 @@ ssi_status run_job(ssi_ctx* ctx, const ssi_job_desc* j, const JobPlan& p, JobBuf
     B.status_cleared = true;
   }
   SSI_TRY(covariances_ws(ctx, B.ws, p.cov, Y, (ssi_precision)j->prec, R, status, stream));
-  for (int t = 0; t < j->n_lags; ++t)
-    SSI_TRY(toeplitz_rsvd_ws(ctx, B.ws, p.rs[t], R, j->seed, (ssi_precision)j->prec, U[t],
-                             S + (size_t)t * j->k, status, stream));
+  if (j->n_lags == 1) {
+    SSI_TRY(toeplitz_rsvd_ws(ctx, B.ws, p.rs[0], R, j->seed, (ssi_precision)j->prec, U[0], S,
+                             status, stream, false));
+  } else {
+    // the lags' RSVDs are independent (Sec. 2.3): fork them over LAG_STREAMS streams, each
+    // lag in its own scratch region, and join before the realisations
+    const int n_str = std::min(j->n_lags, LAG_STREAMS);
+    if (!B.fork) {
+      SSI_CUDA(cudaEventCreateWithFlags(&B.fork, cudaEventDisableTiming));
+      for (int a = 0; a < LAG_STREAMS; ++a) {
+        SSI_CUDA(cudaStreamCreateWithFlags(&B.lag_stream[a], cudaStreamNonBlocking));
+        SSI_CUDA(cudaEventCreateWithFlags(&B.join[a], cudaEventDisableTiming));
+      }
+    }
+    SSI_CUDA(cudaEventRecord(B.fork, stream));
+    for (int a = 0; a < n_str; ++a) SSI_CUDA(cudaStreamWaitEvent(B.lag_stream[a], B.fork, 0));
+    for (int t = 0; t < j->n_lags; ++t) {
+      Workspace sub;
+      sub.base = B.ws.base + p.rs_off[t];
+      sub.cap = p.rs[t].ws_bytes;
+      SSI_TRY(toeplitz_rsvd_ws(ctx, sub, p.rs[t], R, j->seed, (ssi_precision)j->prec, U[t],
+                               S + (size_t)t * j->k, status, B.lag_stream[t % n_str], true));
+    }
+    for (int a = 0; a < n_str; ++a) {
+      SSI_CUDA(cudaEventRecord(B.join[a], B.lag_stream[a]));
+      SSI_CUDA(cudaStreamWaitEvent(stream, B.join[a], 0));
+    }
+  }
   std::vector<int> lags(j->lags, j->lags + j->n_lags), orders(j->orders, j->orders + j->n_orders);
   std::vector<const float*> Uc(U.begin(), U.end());
   SSI_TRY(realize_ws(ctx, B.ws, p.rz, lags.data(), Uc.data(), orders.data(), 1.0 / j->fs, poles, phi,
@@ -123,6 +152,14 @@ ssi_status buffers_reserve(ssi_ctx* ctx, JobBuffers& B, const JobPlan& p, cudaSt
 }
 
 void buffers_free(ssi_ctx* ctx, JobBuffers& B) {
+  for (int a = 0; a < LAG_STREAMS; ++a) {
+    if (B.lag_stream[a]) {
+      cudaStreamSynchronize(B.lag_stream[a]);
+      cudaStreamDestroy(B.lag_stream[a]);
+    }
+    if (B.join[a]) cudaEventDestroy(B.join[a]);
+  }
+  if (B.fork) cudaEventDestroy(B.fork);
   if (B.buf) ctx_free(ctx, B.buf, B.buf_cap);
   if (B.ws.base) ctx_free(ctx, B.ws.base, B.ws.cap);
   B = JobBuffers{};

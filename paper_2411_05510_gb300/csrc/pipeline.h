@@ -13,9 +13,12 @@ struct JobPlan {
   std::vector<RsvdPlan> rs;
   RealizePlan rz;
   size_t ws_bytes;     // scratch (shared by the stages, which run in sequence)
+  std::vector<size_t> rs_off;   // per-lag RSVD scratch offsets (several lags run at once)
   size_t buf_bytes;    // R, U per lag, S, device Y copy, status word
   int64_t n_slots, phi_floats;
 };
+
+constexpr int LAG_STREAMS = 4;   // the per-lag RSVDs of a multi-lag solve run on this many streams
 
 struct JobBuffers {
   void* buf = nullptr;
@@ -23,6 +26,10 @@ struct JobBuffers {
   Workspace ws;
   int* status = nullptr;
   bool status_cleared = false;
+  // streams and fork/join events of the per-lag fan-out (created on first use)
+  cudaStream_t lag_stream[LAG_STREAMS] = {};
+  cudaEvent_t fork = nullptr;
+  cudaEvent_t join[LAG_STREAMS] = {};
 };
 
 ssi_status validate_job(const ssi_job_desc* j);

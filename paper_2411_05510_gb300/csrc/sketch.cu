@@ -23,7 +23,7 @@ namespace ssi {
 // qr.cu / svd.cu
 size_t qr_ws_bytes(int ncols, int num_sms);
 ssi_status qr_launch(ssi_ctx* ctx, Workspace& ws, float* A, int rows, int ncols, int ld,
-                     float* Rout, int* status, cudaStream_t stream);
+                     float* Rout, int* status, cudaStream_t stream, bool shared_device);
 size_t jacobi_ws_bytes(int K);
 ssi_status jacobi_launch(Workspace& ws, const float* R2, int K, float* Ut, float* S, int* status,
                          cudaStream_t stream);
@@ -548,7 +548,7 @@ RsvdPlan rsvd_plan(int l, int i, int k, int oversample, int q, int num_sms) {
 
 ssi_status toeplitz_rsvd_ws(ssi_ctx* ctx, Workspace& ws, const RsvdPlan& r, const double* R,
                             uint64_t seed, ssi_precision prec, float* U, float* S,
-                            int* dev_status, cudaStream_t stream) {
+                            int* dev_status, cudaStream_t stream, bool shared_device) {
   ws.reset();
   const bool tc = prec == SSI_PREC_SPLIT_BF16;
   const int n_lag = 2 * r.i - 1;
@@ -647,7 +647,7 @@ ssi_status toeplitz_rsvd_ws(ssi_ctx* ctx, Workspace& ws, const RsvdPlan& r, cons
     ws.off = ws_mark;
     ProfScope ps(ctx, ST_QR, stream);
     count_launches(ctx, 1);
-    return qr_launch(ctx, ws, Yb, r.L_pad, r.K, r.Kp, Rout, dev_status, stream);
+    return qr_launch(ctx, ws, Yb, r.L_pad, r.K, r.Kp, Rout, dev_status, stream, shared_device);
   };
 
   // Y = T Omega; Q = qr(Y)
@@ -702,6 +702,6 @@ extern "C" ssi_status ssi_toeplitz_rsvd(ssi_ctx* ctx, const double* R, int l, in
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   RsvdPlan plan = rsvd_plan(l, i, k, oversample, q, ctx->num_sms);
   SSI_TRY(ws_reserve(ctx, ctx->ws, plan.ws_bytes, s));
-  SSI_TRY(toeplitz_rsvd_ws(ctx, ctx->ws, plan, R, seed, prec, U, S, ctx->dev_status, s));
+  SSI_TRY(toeplitz_rsvd_ws(ctx, ctx->ws, plan, R, seed, prec, U, S, ctx->dev_status, s, false));
   return check_dev_status(ctx->dev_status, s);
 }
