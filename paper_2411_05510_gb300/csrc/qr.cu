@@ -10,12 +10,12 @@
 //   pass 1:  W  = Y_j - Q_{<j} (Q_{<j}^T Y_j);   W  = W R1^{-1},  R1 = chol(W^T W)
 //   pass 2:  W' = W   - Q_{<j} (Q_{<j}^T W);     Q_j = W' R2^{-1}, R2 = chol(W'^T W')
 // (block classical Gram-Schmidt with re-orthogonalisation, each panel made
-// orthonormal by Cholesky-QR).  The Gram matrices are accumulated in double-FP32
-// (error-free products with fma, two-sum accumulation) and reduced in FP64.  The 32x32
-// Cholesky factors run redundantly in every CTA: in FP32 by one warp, and for the first
-// pass in FP64 when the FP32 pivots show cond(G) above ~1e5, so a panel with condition
-// number up to ~1e7 is orthonormalised to FP32 precision.  Grid-wide reductions
-// use a two-phase barrier (partials -> sliced sums -> broadcast); every barrier
+// orthonormal by Cholesky-QR).  The first-pass Gram matrices are accumulated in
+// double-FP32 (error-free products with fma, two-sum accumulation) and reduced in FP64.
+// The 32x32 Cholesky factors run redundantly in every CTA: in FP32 by the whole CTA, and
+// for the first pass in FP64 when the FP32 pivots show cond(G) above ~1e5, so a panel
+// with condition number up to ~1e7 is orthonormalised to FP32 precision.  Grid-wide
+// reductions use a two-phase barrier (partials -> sliced sums -> broadcast); every barrier
 // wait is bounded and sets the status word when it runs out.
 // R = [C1 + C2 R1 | R2 R1] per panel is written when requested.
 #include <cooperative_groups.h>
@@ -129,36 +129,52 @@ __device__ void slice_reduce(const T* part, size_t stride, int C, int e0, int e1
   }
 }
 
-// FP32 Cholesky of a well-conditioned w x w Gram matrix by one warp (lane c holds column c):
-// used by the second Cholesky-QR pass, whose Gram matrix is the identity up to O(eps).
-// Returns min_j pivot_j / max_j G[j][j] (the same in every lane), an estimate of
-// 1 / cond(G) that decides whether the FP32 factor is accurate enough.
-__device__ float chol_warp_f32(const double* G, int w, double* R, double* rdiag, int lane) {
-  float col[PB];
-#pragma unroll
-  for (int a = 0; a < PB; ++a) col[a] = (a < w && lane < w && a <= lane) ? (float)G[a * PB + lane] : 0.f;
-  float gmax = (lane < w) ? (float)G[lane * PB + lane] : 0.f;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) gmax = fmaxf(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
-  float dmin = 3.0e38f;
-#pragma unroll
-  for (int j = 0; j < PB; ++j) {
-    if (j >= w) break;
-    // R[j][j] = sqrt(col_j[j]); R[j][c] = col_c[j] / R[j][j]
-    const float djj = __shfl_sync(0xffffffffu, col[j], j);
-    dmin = fminf(dmin, djj);
-    const float rs = rsqrtf(fmaxf(djj, 1e-30f));
-    const float rjc = (lane >= j) ? col[j] * rs : 0.f;   // lane == j: sqrt(d)
-    R[j * PB + lane] = (lane < w) ? (double)rjc : 0.0;
-    if (lane == j) rdiag[j] = (double)rs;
-    // trailing update: col_c[a] -= R[j][a] R[j][c] for j < a <= c
-#pragma unroll
-    for (int a = 0; a < PB; ++a) {
-      const float rja = __shfl_sync(0xffffffffu, rjc, a);
-      if (a > j && a <= lane) col[a] = fmaf(-rja, rjc, col[a]);
-    }
+// FP32 Cholesky of a w x w Gram matrix by the whole CTA, on an FP32 copy of its upper
+// triangle in buf (PB x PB, shared memory).  Step j: every thread forms 1 / R[j][j] from
+// the pivot itself, warp 0 writes row j of R, and the warps update the trailing triangle
+// (rows by warp, columns by lane) from the unscaled row j; one barrier per step.
+// Writes R (FP64, upper, zero elsewhere) and 1 / R[j][j].  Returns min_j pivot_j /
+// max_j G[j][j], an estimate of 1 / cond(G) that decides whether the FP32 factor is
+// accurate enough (the same in every thread).
+__device__ float chol_cta_f32(const double* G, int w, double* R, double* rdiag, float* buf) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nwarps = QR_THREADS / 32;
+  for (int e = tid; e < PB * PB; e += QR_THREADS) {
+    const int a = e / PB, c = e % PB;
+    buf[e] = (a < w && c < w && a <= c) ? (float)G[e] : 0.f;
+    R[e] = 0.0;
   }
-  __syncwarp();
+  __syncthreads();
+  float gmax = 0.f, dmin = 3.0e38f;
+  for (int j = 0; j < w; ++j) gmax = fmaxf(gmax, buf[j * PB + j]);
+  for (int j = 0; j < w; ++j) {
+    const float d = buf[j * PB + j];
+    dmin = fminf(dmin, d);
+    const float rs = rsqrtf(fmaxf(d, 1e-30f)), rs2 = rs * rs;
+    if (warp == 0 && lane >= j && lane < w) {
+      R[j * PB + lane] = (double)(buf[j * PB + lane] * rs);   // lane == j: sqrt(d)
+      if (lane == j) rdiag[j] = (double)rs;
+    }
+    // G[a][c] -= G[j][a] G[j][c] / d for j < a <= c: a lane's (at most PB / nwarps) rows
+    // are loaded first, then updated, so their shared-memory round trips overlap
+    const int c = lane;
+    if (c > j && c < w) {
+      const float gjc = buf[j * PB + c] * rs2;
+      constexpr int RPWARP = PB / (QR_THREADS / 32);
+      float gja[RPWARP], gac[RPWARP];
+#pragma unroll
+      for (int k = 0; k < RPWARP; ++k) {
+        const int a = j + 1 + warp + k * nwarps;
+        gja[k] = (a <= c) ? buf[j * PB + a] : 0.f;
+        gac[k] = (a <= c) ? buf[a * PB + c] : 0.f;
+      }
+#pragma unroll
+      for (int k = 0; k < RPWARP; ++k) {
+        const int a = j + 1 + warp + k * nwarps;
+        if (a <= c) buf[a * PB + c] = fmaf(-gja[k], gjc, gac[k]);
+      }
+    }
+    __syncthreads();
+  }
   return (w == 0) ? 1.f : (gmax > 0.f ? dmin / gmax : 0.f);
 }
 
@@ -223,7 +239,9 @@ __global__ void __launch_bounds__(QR_THREADS, 1)   // one CTA per SM (cooperativ
   // local rows: shared memory when they fit, else the matrix itself
   float* Ab = p.lds ? s_rows : p.A + (size_t)r0 * p.ld;
   const int ldb = p.lds ? p.lds : p.ld;
-  float* sC = p.lds ? s_rows + (size_t)rows_per * p.chunks_per_cta * p.lds : nullptr;   // projection (j0 x PB)
+  // the reduced projection C (j0 x PB), 16-byte aligned for float4 rows
+  float* sC = p.lds ? s_rows + (((size_t)rows_per * p.chunks_per_cta * p.lds + 3) & ~size_t(3))
+                    : nullptr;
   if (p.lds) {
     for (int e = tid; e < nr * p.ncols; e += QR_THREADS) {
       const int rr = e / p.ncols, c = e % p.ncols;
@@ -286,8 +304,13 @@ __global__ void __launch_bounds__(QR_THREADS, 1)   // one CTA per SM (cooperativ
             float qv[4], cv[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) qv[i] = (r0 + i < nr) ? Ab[(r0 + i) * ldb + a] : 0.f;
-#pragma unroll
-            for (int u = 0; u < 4; ++u) cv[u] = C[a * PB + b0 + u];
+            {
+              const float4 c4 = *reinterpret_cast<const float4*>(C + a * PB + b0);
+              cv[0] = c4.x;
+              cv[1] = c4.y;
+              cv[2] = c4.z;
+              cv[3] = c4.w;
+            }
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -401,18 +424,14 @@ __global__ void __launch_bounds__(QR_THREADS, 1)   // one CTA per SM (cooperativ
         sG[e] = (a < w && b < w && a <= b) ? p.fin_g[e] : 0.0;
       }
       __syncthreads();
-      // FP32 Cholesky by one warp; the first pass falls back to the FP64 factorisation
+      // FP32 Cholesky by the CTA; the first pass falls back to the FP64 factorisation
       // when a pivot is below 1e-5 of the largest diagonal (cond(G) above ~1e5, where the
       // FP32 factor would be too inaccurate for the second pass to repair).  Every CTA
       // factors the same G, so every CTA takes the same branch.
       {
-        __shared__ int s_f32ok;
-        if (tid < 32) {
-          const float ratio = chol_warp_f32(sG, w, sR[pass], sRd, tid);
-          if (tid == 0) s_f32ok = (pass == 1) || ratio >= 1e-5f;
-        }
-        __syncthreads();
-        if (!s_f32ok) chol_cta(sG, w, sR[pass], sRd);
+        const float ratio = chol_cta_f32(sG, w, sR[pass], sRd, sRf);
+        const bool f32ok = (pass == 1) || ratio >= 1e-5f;
+        if (!f32ok) chol_cta(sG, w, sR[pass], sRd);
       }
       for (int e = tid; e < PB * PB; e += QR_THREADS) sRf[e] = (float)sR[pass][e];
       for (int e = tid; e < PB; e += QR_THREADS) sRdf[e] = (float)sRd[e];
@@ -490,7 +509,7 @@ ssi_status qr_launch(ssi_ctx* ctx, Workspace& ws, float* A, int rows, int ncols,
   p.chunks_per_cta = cpc;
   const int rows_per = (int)ceil_div(rows, C) * cpc;   // rows of a CTA
   const int lds = ncols | 1;   // odd leading dimension: rows of a warp fall in distinct banks
-  size_t smem = ((size_t)rows_per * lds + (size_t)ncols * PB) * sizeof(float);
+  size_t smem = ((size_t)rows_per * lds + 4 + (size_t)ncols * PB) * sizeof(float);
   if (smem > 192 * 1024) {
     smem = 0;   // rows stay in global memory
   } else {
