@@ -39,7 +39,7 @@ struct QrParams {
   float* fin_c;        // [ncols*PB] reduced projection
   double* red_g;       // [P][PB*PB] Gram partials (hi), [P][PB*PB] (lo) after
   double* fin_g;       // [PB*PB]
-  unsigned* bar;       // [2] arrival counter, generation
+  unsigned* bar;       // [0] monotonic arrival counter of the grid barrier (zeroed per launch)
   int* status;
   int* abort_flag;
   int lds;             // leading dimension of the rows staged in shared memory (0: not staged)
@@ -53,8 +53,12 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   e = (a - (s - bb)) + (b - bb);
 }
 
+// Grid barrier on a monotonic arrival counter (zeroed before the launch): barrier k of the
+// launch is passed once the counter reaches k x gridDim.x.  One atomic per CTA, nothing
+// to reset; a CTA that passes early cannot disturb the count of the barrier others still
+// wait at.  The wait is bounded.
 struct GridBar {
-  unsigned gen;
+  unsigned n;   // barriers this CTA has entered in this launch
 };
 
 __device__ bool grid_sync(const QrParams& p, GridBar& gb) {
@@ -62,15 +66,13 @@ __device__ bool grid_sync(const QrParams& p, GridBar& gb) {
   __shared__ int ok_s;
   if (threadIdx.x == 0) {
     int ok = 1;
+    gb.n += 1;
+    const unsigned target = gb.n * gridDim.x;
     __threadfence();
-    const unsigned arrived = atomicAdd(&p.bar[0], 1u);
-    if (arrived == gridDim.x - 1) {
-      atomicExch(&p.bar[0], 0u);
-      __threadfence();
-      atomicAdd(&p.bar[1], 1u);
-    } else {
+    const unsigned arrived = atomicAdd(&p.bar[0], 1u) + 1u;
+    if (arrived < target) {
       const uint64_t t0 = bw::global_ns();
-      while (*(volatile unsigned*)&p.bar[1] == gb.gen) {
+      while (*(volatile unsigned*)&p.bar[0] < target) {
         if (*(volatile int*)p.abort_flag) { ok = 0; break; }
         if (bw::global_ns() - t0 > BAR_NS) {
           atomicOr(p.status, DEV_TIMEOUT);
@@ -80,7 +82,6 @@ __device__ bool grid_sync(const QrParams& p, GridBar& gb) {
         }
       }
     }
-    gb.gen += 1;
     __threadfence();
     ok_s = ok;
   }
@@ -225,7 +226,7 @@ __global__ void __launch_bounds__(QR_THREADS, 1)   // one CTA per SM (cooperativ
   __shared__ float sRf[PB * PB];        // current factor in FP32
   __shared__ float sRdf[PB];
   GridBar gb;
-  gb.gen = *(volatile unsigned*)&p.bar[1];
+  gb.n = 0;
 
   const int P = gridDim.x;
   const int C = p.n_chunks;
