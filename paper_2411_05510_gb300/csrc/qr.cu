@@ -94,6 +94,7 @@ __device__ bool grid_sync(const QrParams& p, GridBar& gb) {
 // q, q + RED_PER, ... in order, and their sums are added in order: the same rounding
 // whatever the grid and however the entries are split between CTAs.
 constexpr int RED_PER = 8;
+constexpr int RED_AHEAD = 20;   // >= 152 / RED_PER
 template <typename T>
 __device__ void slice_reduce(const T* part, size_t stride, int C, int e0, int e1, T* out) {
   __shared__ double red[QR_THREADS];
@@ -106,16 +107,17 @@ __device__ void slice_reduce(const T* part, size_t stride, int C, int e0, int e1
     const int le = base + tid / RED_PER;
     double s = 0.0;
     if (le < E) {
-      // eight partials loaded ahead of their adds (same order of addition)
-      for (int cb = sub; cb < C; cb += 8 * RED_PER) {
-        T v[8];
+      // up to RED_AHEAD partials loaded ahead of their adds (one L2 round trip for one
+      // chunk per SM; same order of addition)
+      for (int cb = sub; cb < C; cb += RED_AHEAD * RED_PER) {
+        T v[RED_AHEAD];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
+        for (int u = 0; u < RED_AHEAD; ++u) {
           const int c = cb + u * RED_PER;
           v[u] = (c < C) ? part[(size_t)c * stride + e0 + le] : T(0);
         }
 #pragma unroll
-        for (int u = 0; u < 8; ++u) s += (double)v[u];
+        for (int u = 0; u < RED_AHEAD; ++u) s += (double)v[u];
       }
     }
     red[tid] = s;
@@ -297,14 +299,16 @@ __global__ void __launch_bounds__(QR_THREADS, 1)   // one CTA per SM (cooperativ
           __syncthreads();
           C = sC;
         }
-        // ---- W -= Q[:, :j0] C on local rows: 4 rows x 4 columns per thread
-        for (int tt = tid; tt < ((nr + 3) / 4) * (PB / 4); tt += QR_THREADS) {
-          const int r0 = 4 * (tt / (PB / 4)), b0 = 4 * (tt % (PB / 4));
-          float acc[4][4] = {};
+        // ---- W -= Q[:, :j0] C on local rows: UR_ROWS rows x 4 columns per thread (three
+        //      rows keep 200 of the 256 threads busy on a 74-row chunk)
+        constexpr int UR_ROWS = 3;
+        for (int tt = tid; tt < ((nr + UR_ROWS - 1) / UR_ROWS) * (PB / 4); tt += QR_THREADS) {
+          const int r0 = UR_ROWS * (tt / (PB / 4)), b0 = 4 * (tt % (PB / 4));
+          float acc[UR_ROWS][4] = {};
           for (int a = 0; a < j0; ++a) {
-            float qv[4], cv[4];
+            float qv[UR_ROWS], cv[4];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) qv[i] = (r0 + i < nr) ? Ab[(r0 + i) * ldb + a] : 0.f;
+            for (int i = 0; i < UR_ROWS; ++i) qv[i] = (r0 + i < nr) ? Ab[(r0 + i) * ldb + a] : 0.f;
             {
               const float4 c4 = *reinterpret_cast<const float4*>(C + a * PB + b0);
               cv[0] = c4.x;
@@ -313,12 +317,12 @@ __global__ void __launch_bounds__(QR_THREADS, 1)   // one CTA per SM (cooperativ
               cv[3] = c4.w;
             }
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < UR_ROWS; ++i)
 #pragma unroll
               for (int u = 0; u < 4; ++u) acc[i][u] = fmaf(qv[i], cv[u], acc[i][u]);
           }
 #pragma unroll
-          for (int i = 0; i < 4; ++i)
+          for (int i = 0; i < UR_ROWS; ++i)
 #pragma unroll
             for (int u = 0; u < 4; ++u)
               if (r0 + i < nr && b0 + u < w) Ab[(r0 + i) * ldb + j0 + b0 + u] -= acc[i][u];
