@@ -133,9 +133,9 @@ __device__ void slice_reduce(const T* part, size_t stride, int C, int e0, int e1
 }
 
 // FP32 Cholesky of a w x w Gram matrix by the whole CTA, on an FP32 copy of its upper
-// triangle in buf (PB x PB, shared memory).  Step j: every thread forms 1 / R[j][j] from
-// the pivot itself, warp 0 writes row j of R, and the warps update the trailing triangle
-// (rows by warp, columns by lane) from the unscaled row j; one barrier per step.
+// triangle in buf (PB x PB, shared memory).  Two columns per step: every thread forms
+// both pivots itself, warp 0 writes rows j and j+1 of R, and the warps apply the rank-2
+// update to the trailing triangle (rows by warp, columns by lane); one barrier per step.
 // Writes R (FP64, upper, zero elsewhere) and 1 / R[j][j].  Returns min_j pivot_j /
 // max_j G[j][j], an estimate of 1 / cond(G) that decides whether the FP32 factor is
 // accurate enough (the same in every thread).
@@ -149,31 +149,50 @@ __device__ float chol_cta_f32(const double* G, int w, double* R, double* rdiag, 
   __syncthreads();
   float gmax = 0.f, dmin = 3.0e38f;
   for (int j = 0; j < w; ++j) gmax = fmaxf(gmax, buf[j * PB + j]);
-  for (int j = 0; j < w; ++j) {
-    const float d = buf[j * PB + j];
-    dmin = fminf(dmin, d);
-    const float rs = rsqrtf(fmaxf(d, 1e-30f)), rs2 = rs * rs;
-    if (warp == 0 && lane >= j && lane < w) {
-      R[j * PB + lane] = (double)(buf[j * PB + lane] * rs);   // lane == j: sqrt(d)
-      if (lane == j) rdiag[j] = (double)rs;
+  // two columns per barrier: rows j and j+1 of R and the rank-2 update of the trailing
+  // triangle; row j+1 after the rank-1 step of column j is formed where it is needed,
+  // u[c] = G[j+1][c] - G[j][j+1] G[j][c] / d_j
+  for (int j = 0; j < w; j += 2) {
+    const bool two = j + 1 < w;
+    const float d0 = buf[j * PB + j];
+    const float rs0 = rsqrtf(fmaxf(d0, 1e-30f)), q0 = rs0 * rs0;
+    const float g01 = two ? buf[j * PB + j + 1] : 0.f;
+    const float d1 = two ? fmaf(-g01 * q0, g01, buf[(j + 1) * PB + j + 1]) : 1.f;
+    const float rs1 = rsqrtf(fmaxf(d1, 1e-30f)), q1 = rs1 * rs1;
+    dmin = fminf(dmin, two ? fminf(d0, d1) : d0);
+    if (warp == 0 && lane < w) {
+      const float g0l = buf[j * PB + lane];
+      if (lane >= j) R[j * PB + lane] = (double)(g0l * rs0);   // lane == j: sqrt(d0)
+      if (lane == j) rdiag[j] = (double)rs0;
+      if (two && lane >= j + 1) {
+        const float ul = (lane == j + 1) ? d1 : fmaf(-g01 * q0, g0l, buf[(j + 1) * PB + lane]);
+        R[(j + 1) * PB + lane] = (double)(ul * rs1);   // lane == j+1: sqrt(d1)
+        if (lane == j + 1) rdiag[j + 1] = (double)rs1;
+      }
     }
-    // G[a][c] -= G[j][a] G[j][c] / d for j < a <= c: a lane's (at most PB / nwarps) rows
-    // are loaded first, then updated, so their shared-memory round trips overlap
+    // G[a][c] -= G[j][a] G[j][c] / d0 + u[a] u[c] / d1 for j+2 <= a <= c: a lane's rows are
+    // loaded first, then updated, so their shared-memory round trips overlap
     const int c = lane;
-    if (c > j && c < w) {
-      const float gjc = buf[j * PB + c] * rs2;
+    if (two && c >= j + 2 && c < w) {
+      const float g0c = buf[j * PB + c];
+      const float uc = fmaf(-g01 * q0, g0c, buf[(j + 1) * PB + c]);
+      const float g0cq = g0c * q0, ucq = uc * q1;
       constexpr int RPWARP = PB / (QR_THREADS / 32);
-      float gja[RPWARP], gac[RPWARP];
+      float g0a[RPWARP], g1a[RPWARP], gac[RPWARP];
 #pragma unroll
       for (int k = 0; k < RPWARP; ++k) {
-        const int a = j + 1 + warp + k * nwarps;
-        gja[k] = (a <= c) ? buf[j * PB + a] : 0.f;
+        const int a = j + 2 + warp + k * nwarps;
+        g0a[k] = (a <= c) ? buf[j * PB + a] : 0.f;
+        g1a[k] = (a <= c) ? buf[(j + 1) * PB + a] : 0.f;
         gac[k] = (a <= c) ? buf[a * PB + c] : 0.f;
       }
 #pragma unroll
       for (int k = 0; k < RPWARP; ++k) {
-        const int a = j + 1 + warp + k * nwarps;
-        if (a <= c) buf[a * PB + c] = fmaf(-gja[k], gjc, gac[k]);
+        const int a = j + 2 + warp + k * nwarps;
+        if (a <= c) {
+          const float ua = fmaf(-g01 * q0, g0a[k], g1a[k]);
+          buf[a * PB + c] = fmaf(-ua, ucq, fmaf(-g0a[k], g0cq, gac[k]));
+        }
       }
     }
     __syncthreads();
