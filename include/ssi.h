@@ -163,8 +163,10 @@ ssi_status ssi_toeplitz_rsvd(ssi_ctx* ctx, const double* R, int l, int i, int k,
  *
  * lags     host, n_lags block counts i_t (each >= 2), n_lags <= 64.
  * U        host array of n_lags device pointers; U[t] is (l*lags[t]) x k float32.
- * orders   host, n_orders even model orders, ascending, 2 <= order <= min(k, 224),
- *          n_orders <= 512; k <= 224.
+ * orders   host, n_orders even model orders, ascending, 2 <= order <= min(k, 512),
+ *          n_orders <= 512; k <= 512.  Orders up to 224 keep A in shared memory;
+ *          larger ones run the same kernel with A in the realisation's global
+ *          scratch (slower: every access goes to L2).
  * poles    device, ssi_pole_slots(n_orders, orders) * n_lags records.  Slot
  *          (t, m, j) = t*slots_per_lag + sum_{m'<m} orders[m']/2 + j; the poles of
  *          one realisation come first, ascending in frequency; unused slots have

@@ -17,7 +17,7 @@ ssi_status validate_job(const ssi_job_desc* j) {
   SSI_CHECK(j->n_lags >= 1 && j->n_lags <= 64 && j->lags, "job: 1 <= n_lags <= 64");
   SSI_CHECK(j->n_orders >= 1 && j->n_orders <= 512 && j->orders, "job: 1 <= n_orders <= 512");
   SSI_CHECK(j->k >= 2 && j->oversample >= 0 && j->q >= 0, "job: bad k / oversample / q");
-  SSI_CHECK(j->k <= 224 && j->k + j->oversample <= 512, "job: need k <= 224, k + oversample <= 512");
+  SSI_CHECK(j->k + j->oversample <= 512, "job: need k + oversample <= 512");
   SSI_CHECK(j->prec == SSI_PREC_FP32 || j->prec == SSI_PREC_SPLIT_BF16, "job: bad precision");
   for (int t = 0; t < j->n_lags; ++t) {
     SSI_CHECK(j->lags[t] >= 2, "job: lag %d < 2", j->lags[t]);
@@ -30,7 +30,7 @@ ssi_status validate_job(const ssi_job_desc* j) {
   for (int m = 0; m < j->n_orders; ++m) {
     SSI_CHECK(j->orders[m] >= 2 && j->orders[m] % 2 == 0 && j->orders[m] <= j->k,
               "job: order %d must be even and in [2, k]", j->orders[m]);
-    SSI_CHECK(j->orders[m] <= 224, "job: order %d > 224 not supported", j->orders[m]);
+    SSI_CHECK(j->orders[m] <= 512, "job: order %d > 512 not supported", j->orders[m]);
     SSI_CHECK(m == 0 || j->orders[m] > j->orders[m - 1], "job: orders must ascend");
   }
   return SSI_OK;

@@ -33,6 +33,7 @@ constexpr int MAX_LAGS = 64;
 constexpr int EIG_THREADS = 512;
 constexpr int GR_ROWS = 512;      // rows per Gram chunk
 constexpr int SMEM_N_MAX = 224;   // largest order whose A fits shared memory
+constexpr int N_MAX = 512;        // largest order (larger ones keep A in global scratch)
 
 constexpr int WN = 32;                       // window of the bulge chase
 constexpr int WB = WN - 3;                   // bulge steps per window
@@ -112,6 +113,7 @@ __global__ void k_gram_reduce(const float* __restrict__ partial, int n_lags, int
 }
 
 // ------------------------------------------------------------------ per-lag factorisation
+constexpr int FACTOR_SMEM_K = 224;   // largest k whose factor fits shared memory
 // GH[t] = [G | H] (2 x k x k); out RM[t] = [Rinv | M] (2 x k x k) with G = R^T R and
 // M = R^{-T} H.  One CTA per lag, R in shared memory (row stride k + 1):
 //   1. right-looking Cholesky on the upper triangle (warp 0 scales row j, then all
@@ -119,9 +121,14 @@ __global__ void k_gram_reduce(const float* __restrict__ partial, int n_lags, int
 //   2. R^{-1} in place, column by column (column j from the inverted leading block and
 //      a copy of R's column j);
 //   3. M = R^{-T} H = (R^{-1})^T H with 4 x 4 outputs per thread.
+// GLOBAL: k > FACTOR_SMEM_K, the same layout in the lag's global scratch (L2-resident);
+// a separate instantiation keeps shared-memory instructions for the common case.
+template <bool GLOBAL>
 __global__ void __launch_bounds__(1024)
-    k_lag_factor(const float* __restrict__ GH, int k, float* __restrict__ RM, int* status) {
-  extern __shared__ float sR[];   // k x (k+1), then a column buffer of k floats
+    k_lag_factor(const float* __restrict__ GH, int k, float* __restrict__ RM, float* Rglobal,
+                 int* status) {
+  extern __shared__ float s_R[];  // k x (k+1), then a column buffer of k floats
+  float* sR = GLOBAL ? Rglobal + (size_t)blockIdx.x * ((size_t)k * (k + 1) + k) : s_R;
   const int ldr = k + 1;
   float* col = sR + (size_t)k * ldr;
   const int t = blockIdx.x;
@@ -231,9 +238,6 @@ struct EigParams {
   float* work;               // per-realisation scratch
   long long work_off[512];   // offset of order m's scratch within a lag's scratch
   long long work_per_lag;
-  int xbuf_off;              // floats: start of the vector buffers (8 warps x 2 nmax) in shared memory
-  int log_off;               // floats: start of the reflector staging buffer in shared memory
-  int nmax;                  // largest order of the launch
   double dt;
   ssi_pole* poles;
   float* phi;
@@ -249,9 +253,24 @@ struct EigParams {
 constexpr int EIG_HDR = 64;
 constexpr int ZREC = WN * WN + 8;
 __host__ __device__ inline long long zlog_cap(int n) { return (long long)n * n / 16 + 2LL * n + 64; }
+// (a multiple of 8 floats, so that every realisation's window records stay 16-byte aligned
+// for the cp.async copies of the eigenvector kernel)
 __host__ __device__ inline long long eig_work_floats(int n, int) {
-  return EIG_HDR + 2LL * n * n + zlog_cap(n) * ZREC + 64;
+  return EIG_HDR + 2LL * n * n + zlog_cap(n) * ZREC + 64 +
+         (n > SMEM_N_MAX ? (((long long)n * (n + 1) + 7) & ~7LL) : 0LL);   // A of the larger orders
 }
+// shared-memory layout of one k_eig CTA of order n (in floats): A when n <= SMEM_N_MAX,
+// then the vector buffers (8 warps x 2n floats; before the eigenvectors they hold the
+// Hessenberg vector and the helpers' transposed window factor), then the two window
+// factors of the QR iteration
+__host__ __device__ inline int eig_xbuf_off(int n) {
+  return n <= SMEM_N_MAX ? ((n * (n + 1) + 31) / 32) * 32 : 0;
+}
+__host__ __device__ inline int eig_log_off(int n) {
+  const int vb = 16 * n > WN * (WN + 4) ? 16 * n : WN * (WN + 4);
+  return ((eig_xbuf_off(n) + vb + 31) / 32) * 32;
+}
+__host__ __device__ inline int eig_smem_floats(int n) { return eig_log_off(n) + 2 * WN * (WN + 4); }
 constexpr int VEC_COLS = 32;   // columns of X per eigenvector block (16 poles)
 
 // Bounded wait (2 s of %globaltimer) of a whole warp until *x >= v; the result is the
@@ -288,11 +307,71 @@ __device__ __forceinline__ void helper_sync(int nthreads) {
 
 __device__ __forceinline__ float sgnf(float a, float b) { return b >= 0.f ? fabsf(a) : -fabsf(a); }
 
+// One Householder reflector of the Hessenberg reduction applied from both sides,
+// H = (I - beta v v^T) H (I - beta v v^T) on rows/columns j+1.., with v in registers: entry c
+// on lane c % 32, slot c / 32 (the same layout serves the rows of the left update and the
+// columns of the right update); a warp owns whole columns (rows), forms the dot product,
+// reduces it, and updates the elements it still holds in registers.  NV slots cover
+// orders up to 32 NV.
+template <int NV>
+__device__ __forceinline__ void hess_update(float* A, int ld, int n, int j, int len, float beta,
+                                            const float* sv, int hw, int hl, int hnw) {
+  float vreg[NV];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    const int c = hl + 32 * q;
+    vreg[q] = (c < len) ? sv[c] : 0.f;
+  }
+  // left: A[j+1:, c] -= beta v (v^T A[j+1:, c]) for c > j (column j is already final)
+  for (int c = j + 1 + hw; c < n; c += hnw) {
+    float a[NV];
+    float dot = 0.f;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      const int r = hl + 32 * q;
+      a[q] = (r < len) ? A[(j + 1 + r) * ld + c] : 0.f;
+      dot = fmaf(a[q], vreg[q], dot);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+    const float sc = dot * beta;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      const int r = hl + 32 * q;
+      if (r < len) A[(j + 1 + r) * ld + c] = fmaf(-sc, vreg[q], a[q]);
+    }
+  }
+  __syncthreads();
+  // right: A[r, j+1:] -= beta (A[r, j+1:] v) v^T for all rows
+  for (int r = hw; r < n; r += hnw) {
+    float a[NV];
+    float dot = 0.f;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      const int c = hl + 32 * q;
+      a[q] = (c < len) ? A[r * ld + j + 1 + c] : 0.f;
+      dot = fmaf(a[q], vreg[q], dot);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+    const float sc = dot * beta;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      const int c = hl + 32 * q;
+      if (c < len) A[r * ld + j + 1 + c] = fmaf(-sc, vreg[q], a[q]);
+    }
+  }
+}
+
+// BIG: orders above SMEM_N_MAX, A in the realisation's global scratch (a separate
+// instantiation, so that the shared-memory kernel of the smaller orders is unchanged).
+// Work items count from item_base: largest orders first.
+template <bool BIG>
 __global__ void __launch_bounds__(EIG_THREADS, 1)
-    k_eig(EigParams p) {
+    k_eig(EigParams p, int item_base) {
   extern __shared__ float smem[];
   // work item: largest orders first
-  const int item = blockIdx.x;
+  const int item = blockIdx.x + item_base;
   const int mi = p.n_orders - 1 - (item / p.lt.n_lags);
   const int t = item % p.lt.n_lags;
   const int n = p.orders[mi];
@@ -304,7 +383,10 @@ __global__ void __launch_bounds__(EIG_THREADS, 1)
   float* hv = work + EIG_HDR;                 // Hessenberg reflectors: n x n (v, beta in [j*n + n-1])
   float* X = hv + (size_t)n * n;              // eigenvectors of T, n x (2 m)
   float* zlog = X + (size_t)n * n;            // window factors of the QR iteration
-  float* A = smem;                            // n x (n+1), orders <= SMEM_N_MAX
+  // A (n x (n+1)): shared memory up to SMEM_N_MAX, else the realisation's global scratch
+  // (L2-resident), same code either way
+  float* A = BIG ? zlog + zlog_cap(n) * ZREC : smem;
+  const int xbuf_off = eig_xbuf_off(n), log_off = eig_log_off(n);
   __shared__ float sh[16];
   __shared__ int shi[16];
   __shared__ int s_pos[256];                  // position p of the 2x2 block of pole j
@@ -343,7 +425,7 @@ __global__ void __launch_bounds__(EIG_THREADS, 1)
 
   // ---- 2. Householder reduction to upper Hessenberg form (v kept in shared memory and
   //         logged to global memory for the back transformation)
-  float* sv = smem + p.xbuf_off;   // n floats (the vector buffers are not in use yet)
+  float* sv = smem + xbuf_off;   // n floats (the vector buffers are not in use yet)
   __shared__ float s_part[EIG_THREADS / 32];
   for (int j = 0; j + 2 < n; ++j) {
     const int len = n - j - 1;
@@ -375,59 +457,9 @@ __global__ void __launch_bounds__(EIG_THREADS, 1)
     }
     if (tid == 0) v[n - 1] = beta;   // v has len <= n-2 entries; beta stored at the end
     __syncthreads();
-    if (beta != 0.f) {
-      // v in registers: entry c on lane c % 32, slot c / 32 (the same layout serves the rows
-      // of the left update and the columns of the right update); a warp owns whole
-      // columns (rows), forms the dot product, reduces it, and updates the elements it
-      // still holds in registers
-      constexpr int NV = (SMEM_N_MAX + 31) / 32;
-      const int hw = tid >> 5, hl = tid & 31, hnw = nth >> 5;
-      float vreg[NV];
-#pragma unroll
-      for (int q = 0; q < NV; ++q) {
-        const int c = hl + 32 * q;
-        vreg[q] = (c < len) ? sv[c] : 0.f;
-      }
-      // left: A[j+1:, c] -= beta v (v^T A[j+1:, c]) for c > j (column j is already final)
-      for (int c = j + 1 + hw; c < n; c += hnw) {
-        float a[NV];
-        float dot = 0.f;
-#pragma unroll
-        for (int q = 0; q < NV; ++q) {
-          const int r = hl + 32 * q;
-          a[q] = (r < len) ? A[(j + 1 + r) * ld + c] : 0.f;
-          dot = fmaf(a[q], vreg[q], dot);
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
-        const float sc = dot * beta;
-#pragma unroll
-        for (int q = 0; q < NV; ++q) {
-          const int r = hl + 32 * q;
-          if (r < len) A[(j + 1 + r) * ld + c] = fmaf(-sc, vreg[q], a[q]);
-        }
-      }
-      __syncthreads();
-      // right: A[r, j+1:] -= beta (A[r, j+1:] v) v^T for all rows
-      for (int r = hw; r < n; r += hnw) {
-        float a[NV];
-        float dot = 0.f;
-#pragma unroll
-        for (int q = 0; q < NV; ++q) {
-          const int c = hl + 32 * q;
-          a[q] = (c < len) ? A[r * ld + j + 1 + c] : 0.f;
-          dot = fmaf(a[q], vreg[q], dot);
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
-        const float sc = dot * beta;
-#pragma unroll
-        for (int q = 0; q < NV; ++q) {
-          const int c = hl + 32 * q;
-          if (c < len) A[r * ld + j + 1 + c] = fmaf(-sc, vreg[q], a[q]);
-        }
-      }
-    }
+    if (beta != 0.f)
+      hess_update<((BIG ? N_MAX : SMEM_N_MAX) + 31) / 32>(A, ld, n, j, len, beta, sv, tid >> 5,
+                                                         tid & 31, nth >> 5);
     __syncthreads();
   }
 
@@ -446,8 +478,8 @@ __global__ void __launch_bounds__(EIG_THREADS, 1)
   //  columns of the next window itself (the helpers skip them).  A sweep starts only when
   //  every window has been applied.  Same arithmetic as the unwindowed sweep.  Hand-offs
   //  are shared counters with bounded waits.
-  float* Zbuf = smem + p.log_off;     // 2 window factors, WN x (WN + 4) each (16-byte aligned rows)
-  float* ZT = smem + p.xbuf_off;      // the helpers' transposed factor (vector buffers idle here)
+  float* Zbuf = smem + log_off;       // 2 window factors, WN x (WN + 4) each (16-byte aligned rows)
+  float* ZT = smem + xbuf_off;        // the helpers' transposed factor (vector buffers idle here)
   __shared__ volatile int s_posted, s_taken, s_applied, s_state, s_go, s_nwin;
   __shared__ int s_desc[2][4];        // per factor buffer: b, e, kend, end of the chaser's columns
   __shared__ float s_sh[3];           // shift vector of the first step of the sweep
@@ -1024,8 +1056,8 @@ __global__ void __launch_bounds__(EIG_THREADS, 1)
   const int warp = tid >> 5, lane = tid & 31;
   const int ncx = 2 * npole;   // columns of X
   constexpr int VEC_WARPS = 8;  // warps with a vector buffer (shared memory)
-  float* xr = smem + p.xbuf_off + (warp % VEC_WARPS) * 2 * p.nmax;
-  float* xi = xr + p.nmax;
+  float* xr = smem + xbuf_off + (warp % VEC_WARPS) * 2 * n;
+  float* xi = xr + n;
   for (int j = warp; j < npole && warp < VEC_WARPS; j += VEC_WARPS) {
     const int pos = s_pos[j];
     const float mr = s_mur[j], mu_i = s_mui[j];
@@ -1209,7 +1241,7 @@ __global__ void __launch_bounds__(VEC_THREADS)
   }
   float* Xs = vsm;                                         // n x XLD
   float* Zs = Xs + (((size_t)n * XLD + 3) & ~size_t(3));   // ZRING window records
-  float* vs = Zs + ZRING * ZREC;                           // VRING reflectors of SMEM_N_MAX
+  float* vs = Zs + ZRING * ZREC;                           // VRING reflectors of N_MAX
   for (int e = tid; e < n * VEC_COLS; e += VEC_THREADS) {
     const int r = e / VEC_COLS, c = e % VEC_COLS;
     Xs[r * XLD + c] = (c < nc) ? X[(size_t)r * ncx + c0 + c] : 0.f;
@@ -1262,7 +1294,7 @@ __global__ void __launch_bounds__(VEC_THREADS)
     auto issue = [&](int j) {
       if (j >= 0)
         for (int r = tid; r < n; r += VEC_THREADS)
-          cp_async4(vs + (j % VRING) * SMEM_N_MAX + r, hv + (size_t)j * n + r);
+          cp_async4(vs + (j % VRING) * N_MAX + r, hv + (size_t)j * n + r);
       cp_async_commit();
     };
     for (int a = 0; a < VRING - 1; ++a) issue(n - 3 - a);
@@ -1270,7 +1302,7 @@ __global__ void __launch_bounds__(VEC_THREADS)
       cp_async_wait<VRING - 2>();   // reflector j has landed
       __syncthreads();
       issue(j - (VRING - 1));       // into the slot of reflector j + 1, done by every thread
-      const float* v = vs + (j % VRING) * SMEM_N_MAX;
+      const float* v = vs + (j % VRING) * N_MAX;
       const int len = n - j - 1;
       const float beta = v[n - 1];
       float part = 0.f;
@@ -1395,12 +1427,12 @@ RealizePlan realize_plan(int n_lags, const int* lags, int l, int k, const int* o
   }
   for (int t = 0; t < n_lags; ++t) max_i = std::max(max_i, lags[t]);
   const int n_chunks = (int)ceil_div((int64_t)l * (max_i - 1), GR_ROWS);
-  (void)SMEM_N_MAX;
   WsPlan w;
   w.add<float>((size_t)n_lags * std::max(n_chunks, 1) * 2 * k * k);  // Gram partials
   w.add<float>((size_t)n_lags * 2 * k * k);                          // G | H
   w.add<float>((size_t)n_lags * 2 * k * k);                          // Rinv | M
   w.add<float>((size_t)n_lags * work);                               // eig scratch
+  if (k > FACTOR_SMEM_K) w.add<float>((size_t)n_lags * ((size_t)k * (k + 1) + k));  // factors
   r.ws_bytes = w.bytes;
   return r;
 }
@@ -1434,7 +1466,9 @@ ssi_status realize_ws(ssi_ctx* ctx, Workspace& ws, const RealizePlan& r, const i
     work += eig_work_floats(orders[m], r.l) + 64;
   }
   float* eigw = ws.take<float>((size_t)r.n_lags * work);
-  if (!partial || !GH || !RM || !eigw) {
+  float* Rg = (k > FACTOR_SMEM_K) ? ws.take<float>((size_t)r.n_lags * ((size_t)k * (k + 1) + k))
+                                  : nullptr;
+  if (!partial || !GH || !RM || !eigw || (k > FACTOR_SMEM_K && !Rg)) {
     set_error("realize: workspace too small");
     return SSI_E_NOMEM;
   }
@@ -1447,11 +1481,14 @@ ssi_status realize_ws(ssi_ctx* ctx, Workspace& ws, const RealizePlan& r, const i
   SSI_CUDA(cudaGetLastError());
   k_gram_reduce<<<ctx->num_sms * 4, 256, 0, stream>>>(partial, r.n_lags, n_chunks, k, GH);
   SSI_CUDA(cudaGetLastError());
-  const size_t fsmem = ((size_t)k * (k + 1) + k) * sizeof(float);
-  SSI_CHECK(fsmem <= 220 * 1024, "realize: k=%d too large for the per-lag factorisation", k);
-  SSI_CUDA(cudaFuncSetAttribute(k_lag_factor, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(220 * 1024)));
-  k_lag_factor<<<r.n_lags, 1024, fsmem, stream>>>(GH, k, RM, dev_status);
+  const size_t fsmem = Rg ? 0 : ((size_t)k * (k + 1) + k) * sizeof(float);
+  if (Rg) {
+    k_lag_factor<true><<<r.n_lags, 1024, 0, stream>>>(GH, k, RM, Rg, dev_status);
+  } else {
+    SSI_CUDA(cudaFuncSetAttribute(k_lag_factor<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)(220 * 1024)));
+    k_lag_factor<false><<<r.n_lags, 1024, fsmem, stream>>>(GH, k, RM, nullptr, dev_status);
+  }
   SSI_CUDA(cudaGetLastError());
   }
   ep.lt = lt;
@@ -1469,13 +1506,21 @@ ssi_status realize_ws(ssi_ctx* ctx, Workspace& ws, const RealizePlan& r, const i
   ep.poles = poles;
   ep.phi = phi;
   ep.status = dev_status;
-  const int nsm_max = std::min(r.max_order, SMEM_N_MAX);
-  ep.nmax = nsm_max;
-  ep.xbuf_off = (int)round_up((int64_t)nsm_max * (nsm_max + 1), 32);
-  ep.log_off = (int)round_up((int64_t)ep.xbuf_off + std::max<int64_t>(8LL * 2 * nsm_max, WN * (WN + 4)),
-                            32);   // 8 vector warps, or the transposed window factor
-  const size_t esmem = ((size_t)ep.log_off + (size_t)std::max(2 * WN * (WN + 4), SMEM_N_MAX)) * sizeof(float);
-  SSI_CUDA(cudaFuncSetAttribute(k_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)esmem));
+  // the CTAs' layouts differ by order; each launch reserves its largest.  Orders above
+  // SMEM_N_MAX (the largest of the diagram) run in their own launch, first.
+  int n_big = 0, esmem_s = 0, esmem_b = 0;
+  for (int m = 0; m < r.n_orders; ++m) {
+    if (orders[m] > SMEM_N_MAX) {
+      ++n_big;
+      esmem_b = std::max(esmem_b, eig_smem_floats(orders[m]));
+    } else {
+      esmem_s = std::max(esmem_s, eig_smem_floats(orders[m]));
+    }
+  }
+  SSI_CUDA(cudaFuncSetAttribute(k_eig<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(esmem_s * sizeof(float))));
+  SSI_CUDA(cudaFuncSetAttribute(k_eig<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(std::max(esmem_b, 1) * sizeof(float))));
   int vec_total = 0;
   for (int m = 0; m < r.n_orders; ++m) {
     ep.vec_blocks[m] = (int)ceil_div(orders[m], VEC_COLS);
@@ -1483,12 +1528,20 @@ ssi_status realize_ws(ssi_ctx* ctx, Workspace& ws, const RealizePlan& r, const i
   }
   ep.vec_blocks_per_lag = vec_total;
   const size_t vsmem =
-      ((((size_t)nsm_max * XLD + 3) & ~size_t(3)) + ZRING * ZREC + VRING * SMEM_N_MAX) * sizeof(float);
+      ((((size_t)r.max_order * XLD + 3) & ~size_t(3)) + ZRING * ZREC + VRING * N_MAX) * sizeof(float);
   SSI_CUDA(cudaFuncSetAttribute(k_eig_vectors, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vsmem));
   {
     ProfScope ps_eig(ctx, ST_EIG, stream);
-    k_eig<<<r.n_lags * r.n_orders, EIG_THREADS, esmem, stream>>>(ep);
-    SSI_CUDA(cudaGetLastError());
+    if (n_big > 0) {
+      count_launches(ctx, 1);
+      k_eig<true><<<r.n_lags * n_big, EIG_THREADS, (size_t)esmem_b * sizeof(float), stream>>>(ep, 0);
+      SSI_CUDA(cudaGetLastError());
+    }
+    if (n_big < r.n_orders) {
+      k_eig<false><<<r.n_lags * (r.n_orders - n_big), EIG_THREADS, (size_t)esmem_s * sizeof(float),
+                     stream>>>(ep, r.n_lags * n_big);
+      SSI_CUDA(cudaGetLastError());
+    }
   }
   ProfScope ps_vec(ctx, ST_EIG_VEC, stream);
   k_eig_vectors<<<r.n_lags * vec_total, VEC_THREADS, vsmem, stream>>>(ep);
@@ -1507,7 +1560,7 @@ extern "C" ssi_status ssi_realize_batch(ssi_ctx* ctx, int n_lags, const int* lag
   SSI_CHECK(n_lags >= 1 && n_lags <= MAX_LAGS, "ssi_realize_batch: 1 <= n_lags <= %d", MAX_LAGS);
   SSI_CHECK(n_orders >= 1 && n_orders <= 512, "ssi_realize_batch: 1 <= n_orders <= 512");
   SSI_CHECK(l >= 1 && k >= 2 && dt > 0, "ssi_realize_batch: bad l/k/dt");
-  SSI_CHECK(k <= 224, "ssi_realize_batch: k=%d > 224 not supported", k);
+  SSI_CHECK(k <= N_MAX, "ssi_realize_batch: k=%d > %d not supported", k, N_MAX);
   for (int t = 0; t < n_lags; ++t) {
     SSI_CHECK(lags[t] >= 2, "ssi_realize_batch: lag %d < 2", lags[t]);
     SSI_CHECK(U[t], "ssi_realize_batch: null U[%d]", t);
@@ -1516,8 +1569,8 @@ extern "C" ssi_status ssi_realize_batch(ssi_ctx* ctx, int n_lags, const int* lag
   for (int m = 0; m < n_orders; ++m) {
     SSI_CHECK(orders[m] >= 2 && orders[m] % 2 == 0 && orders[m] <= k,
               "ssi_realize_batch: order %d must be even and in [2, k]", orders[m]);
-    SSI_CHECK(orders[m] <= SMEM_N_MAX, "ssi_realize_batch: order %d > %d not supported", orders[m],
-              SMEM_N_MAX);
+    SSI_CHECK(orders[m] <= N_MAX, "ssi_realize_batch: order %d > %d not supported", orders[m],
+              N_MAX);
     SSI_CHECK(m == 0 || orders[m] > orders[m - 1], "ssi_realize_batch: orders must ascend");
   }
   SSI_CUDA(cudaSetDevice(ctx->device));

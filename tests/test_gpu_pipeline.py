@@ -8,6 +8,8 @@ agree to ~1e-6 absolute (bound 2e-5).
 """
 import ctypes
 
+import functools
+
 import numpy as np
 import pytest
 import torch
@@ -59,13 +61,20 @@ def test_rsvd_full_width_equals_full_svd_on_chain(P, ctx, prec):
 
 
 @pytest.mark.parametrize("prec", ["split_bf16", "fp32"])
-@pytest.mark.parametrize("l,i,k,p,q", [(24, 10, 40, 10, 2), (70, 7, 60, 20, 1), (9, 30, 30, 6, 3)])
-def test_rsvd_matches_oracle_rsvd(P, ctx, prec, l, i, k, p, q):
-    """Same Omega (Philox) on both sides: leading singular values agree to 1e-4."""
+@pytest.mark.parametrize("l,i,k,p,q", [(24, 10, 40, 10, 2), (70, 7, 60, 20, 1), (9, 30, 30, 6, 3),
+                                       (64, 10, 300, 20, 1)])
+@functools.lru_cache(maxsize=None)
+def _oracle_rsvd_case(l, i, k, p, q):
     rec = S.bridge_record(l, 8, 1.0, 12.0, 50.0, 40000, 0.05, seed=l + i)
     R = O.covariances(rec.Y, 2 * i - 1)
-    T = O.block_toeplitz(R, i)
-    _, s_ref = O.rsvd(T, k, p, q, seed=5)
+    _, s_ref = O.rsvd(O.block_toeplitz(R, i), k, p, q, seed=5)
+    return R, s_ref
+
+
+def test_rsvd_matches_oracle_rsvd(P, ctx, prec, l, i, k, p, q):
+    """Same Omega (Philox) on both sides: leading singular values agree to 1e-4.  The
+    K = 320 case runs the Jacobi SVD of the small matrix from global memory."""
+    R, s_ref = _oracle_rsvd_case(l, i, k, p, q)
     U, s = _rsvd_case(P, ctx, R, l, i, k, p, q, 5, prec)
     lead = 16
     assert np.allclose(s[:lead], s_ref[:lead], rtol=1e-4), np.abs(s[:lead] / s_ref[:lead] - 1).max()
@@ -249,3 +258,41 @@ def test_3d_diagram_matches_oracle(P, ctx):
                 n_flag += 1 + (t > 0 and n in gates[t - 1])
     assert n_cmp_total >= 18
     assert n_flag >= 24
+
+
+def test_realize_orders_above_shared_memory_recover_model_modes(P, ctx):
+    """Orders above 224 run with A in global scratch, and k = 240 factors each lag in
+    global scratch too.  From the exact covariances of a 240-state model (120-storey shear
+    chain, 2 % modal damping, white forces at every storey, accelerations of every storey)
+    the realisation of order 240 must return the model's 120 poles.  Order 230 (also the
+    global-scratch path) and order 200 (shared memory, same launch) must run without
+    failure flags."""
+    M, K = S.shear_chain(120, 1.0, 1e3)
+    model = S.chain_state_space(M, K, S.modal_damping(M, K, 0.02), 1.0 / 40.0, "floors")
+    i = 4
+    T = O.block_toeplitz(S.model_covariances(model, 2 * i - 1)[1:], i)
+    U, s = O.full_svd(T)
+    assert s[239] > 1e-9 * s[0] and s[240] < 1e-9 * s[0]   # rank 240 = 2 x 120 modes
+    orders = [200, 230, 240]
+    rec, phi = _realize(P, ctx, [U[:, :240]], [i], 120, 240, orders, model.dt)
+    cells = gpu_cells(rec, phi, [i], orders, 120)
+    c240 = cells[0][2]
+    assert len(c240["f"]) == 120
+    order = np.argsort(c240["f"])
+    f_gpu, xi_gpu, mu_gpu = c240["f"][order], c240["xi"][order], c240["mu"][order]
+    # the discrete poles themselves: FP32 eigenvalues of a 240 x 240 matrix, |d mu| ~ 1e-5
+    w_true = 2 * np.pi * model.f_true
+    lam = -model.xi_true * w_true + 1j * w_true * np.sqrt(1 - model.xi_true ** 2)
+    mu_true = np.exp(lam * model.dt)
+    assert np.abs(mu_gpu - mu_true).max() < 1e-4, np.abs(mu_gpu - mu_true).max()
+    # f and xi amplify d mu by 1 / (omega dt): the lowest modes (mu within 0.01 of 1) get
+    # looser gates, the modes above 1 Hz the parity gates
+    hi = model.f_true >= 1.0
+    assert np.allclose(f_gpu[hi], model.f_true[hi], rtol=1e-4), np.abs(f_gpu / model.f_true - 1)[hi].max()
+    assert np.allclose(f_gpu, model.f_true, rtol=5e-3)
+    assert np.allclose(xi_gpu[hi], model.xi_true[hi], atol=2e-3)
+    assert np.allclose(xi_gpu, model.xi_true, atol=1e-2)
+    macs = np.array([O.mac(c240["Phi"][:, order[j]], model.phi_true[:, j]) for j in range(120)])
+    assert macs[hi].min() > 0.999 and macs.min() > 0.99, (macs[hi].min(), macs.min())
+    for c in (cells[0][0], cells[0][1]):
+        assert len(c["f"]) >= 90
