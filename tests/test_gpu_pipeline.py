@@ -7,7 +7,6 @@ the Box-Muller transform runs in FP32 on the GPU and FP64 in the oracle, so entr
 agree to ~1e-6 absolute (bound 2e-5).
 """
 import ctypes
-
 import functools
 
 import numpy as np
@@ -60,9 +59,6 @@ def test_rsvd_full_width_equals_full_svd_on_chain(P, ctx, prec):
     assert np.abs(U[:, :8].T @ U[:, :8] - np.eye(8)).max() < 1e-4
 
 
-@pytest.mark.parametrize("prec", ["split_bf16", "fp32"])
-@pytest.mark.parametrize("l,i,k,p,q", [(24, 10, 40, 10, 2), (70, 7, 60, 20, 1), (9, 30, 30, 6, 3),
-                                       (64, 10, 300, 20, 1)])
 @functools.lru_cache(maxsize=None)
 def _oracle_rsvd_case(l, i, k, p, q):
     rec = S.bridge_record(l, 8, 1.0, 12.0, 50.0, 40000, 0.05, seed=l + i)
@@ -71,6 +67,9 @@ def _oracle_rsvd_case(l, i, k, p, q):
     return R, s_ref
 
 
+@pytest.mark.parametrize("prec", ["split_bf16", "fp32"])
+@pytest.mark.parametrize("l,i,k,p,q", [(24, 10, 40, 10, 2), (70, 7, 60, 20, 1), (9, 30, 30, 6, 3),
+                                       (64, 10, 300, 20, 1)])
 def test_rsvd_matches_oracle_rsvd(P, ctx, prec, l, i, k, p, q):
     """Same Omega (Philox) on both sides: leading singular values agree to 1e-4.  The
     K = 320 case runs the Jacobi SVD of the small matrix from global memory."""
