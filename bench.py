@@ -20,6 +20,10 @@ Lines printed (one JSON line on rank 0):
   fp32_path  the same pipeline with plain FP32 CUDA-core GEMMs (the plain FP32 GPU path)
   cpu_baseline  the FP64 oracle on the host cores, stage by stage on a bounded sample
 
+--workload serving_mix runs the serving configuration instead: a seeded stream of
+heterogeneous jobs through ssi_submit / ssi_poll under an HBM budget, capacity with all
+jobs submitted at once and p50/p99 latency under Poisson arrivals at 0.5 / 0.8 / 1.0 of it.
+
 --impl reference times the FP64 oracle (the CPU reference of the method) on the same
 workload, each step one sampled estimate of a full solve.
 """
@@ -275,6 +279,96 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------------------- serving mix
+def run_serving_mix(args, world, rank):
+    """The serving configuration: a seeded stream of heterogeneous jobs (16/48/96/186
+    channels, N 30000-360000, i 20-80, 5-30 modes), records in pinned host memory, admitted
+    by the serving loop under an HBM budget of half the free memory, J slots.  Capacity:
+    all jobs submitted at once.  Then Poisson arrivals at 0.5, 0.8 and 1.0 of that capacity:
+    achieved solves/s and each job's submit-to-result latency (p50/p99)."""
+    import torch
+    import torch.distributed as dist
+    import paper_2411_05510_gb300 as P
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    n_jobs = max(64, args.steps)
+    mix = S.serving_mix(n_jobs, seed=4 + rank)
+    recs = []
+    for w in mix:
+        Y, *_ = S.record(w, np.float32)
+        recs.append(torch.from_numpy(Y).pin_memory())
+    free, _ = torch.cuda.mem_get_info(dev)
+    ctx = P.Context(local, int(free * 0.5))
+    J = max(1, args.inflight)
+    P.ssi_serve_config(ctx, J, 4 * n_jobs)
+
+    def desc_of(w, Yh):
+        return P.job_desc(Yh, w["fs"], w["lags"], w["orders"], k=w["k"], oversample=w["oversample"],
+                          q=w["q"], prec=args.prec, seed=12345)
+
+    descs = [desc_of(w, Yh) for w, Yh in zip(mix, recs)]
+
+    def run(arrivals):
+        """Submit job j at arrivals[j] seconds (host clock); wait for all."""
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        ids = []
+        for j, d in enumerate(descs):
+            wait = arrivals[j] - (time.perf_counter() - t0)
+            if wait > 0:
+                time.sleep(wait)
+            ids.append(P.ssi_submit(ctx, d))
+        lat = []
+        for jid in ids:
+            _, _, lu = P.ssi_poll(ctx, jid, -1)
+            P.ssi_release(ctx, jid)
+            lat.append(lu / 1e3)
+        t = max_over_ranks((time.perf_counter() - t0) * 1e3, dev)
+        return t, lat
+
+    for _ in range(max(1, min(args.warmup, 2))):   # warm-up: slot buffers grow to the mix
+        run([0.0] * n_jobs)
+    t_cap, lat_cap = run([0.0] * n_jobs)
+    capacity = whole_job_rate(n_jobs, world, t_cap)
+    per_rank = capacity / world
+    rng = np.random.Generator(np.random.PCG64(99 + rank))
+    loads = {}
+    for frac in (0.5, 0.8, 1.0):
+        gaps = rng.exponential(1.0 / (frac * per_rank), size=n_jobs)
+        arrivals = list(np.cumsum(gaps) - gaps[0])
+        t, lat = run(arrivals)
+        loads[str(frac)] = {"offered_solves_per_s": frac * capacity,
+                            "achieved_solves_per_s": whole_job_rate(n_jobs, world, t),
+                            "latency_ms": {"p50": pct(lat, 50), "p99": pct(lat, 99)}}
+    if rank == 0:
+        line = {"metric": "SSI solves/s", "value": capacity, "unit": "solves/s", "n_gpus": world,
+                "steps": n_jobs, "warmup": max(1, min(args.warmup, 2)),
+                "ms_per_step": t_cap / n_jobs, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "bf16" if args.prec == "split_bf16" else "f32",
+                "data": "synthetic",
+                "config": {"workload": "serving_mix", "jobs": n_jobs, "slots": J,
+                           "channels": [16, 48, 96, 186], "N": [30000, 360000], "i": [20, 80],
+                           "modes": [5, 30], "hbm_budget_bytes": int(free * 0.5),
+                           "prec": args.prec, "records": "pinned host memory"},
+                "latency_ms": {"p50": pct(lat_cap, 50), "p99": pct(lat_cap, 99),
+                               "kind": "submit to result, all jobs submitted at once"},
+                "poisson": loads,
+                "e2e": {"value": capacity, "unit": "solves/s",
+                        "h2d_bytes_per_step": int(sum(w["l"] * w["N"] * 4 for w in mix) / n_jobs),
+                        "d2h_bytes_per_step": None,
+                        "api": "ssi_submit/ssi_poll, host clock around all jobs"}}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
 def l2_note(w):
     mb = w.get("l", w.get("n_dof", 0)) * w["N"] * 4 / 1e6
     if mb > 129:
@@ -304,6 +398,10 @@ def main():
             import torch.distributed as dist
             dist.barrier()
             dist.destroy_process_group()
+        return
+
+    if args.workload == "serving_mix":
+        run_serving_mix(args, world, rank)
         return
 
     import torch
