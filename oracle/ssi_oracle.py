@@ -33,6 +33,15 @@ again in the design notes):
 * Only eigenvalues with Im(mu) > 0 become poles (one per conjugate pair).
 * "int(.)" in the time-lag rules is the ceiling (reproduces 189, 170, 76, 69,
   104 and 512 quoted in Sec. 3).
+* Two-stage clustering (Sec. 2.3 "3D clustering", Sec. 3.1):
+  * Stage I features of a stable pole: (d_f, d_xi, 1 - MAC) to its nearest HC-passing
+    neighbour (previous order of the same lag or same order of the previous lag),
+    nearest in d_f + d_xi + (1 - MAC), then 1 - MPC and MPD of the pole.
+  * Fuzzy C-means with two clusters and fuzzifier 2, started from the feature-wise
+    minimum and maximum.  The cluster whose centroid is nearer the origin is the
+    possibly physical one; poles with membership >= 0.5 in it are kept.
+  * Stage II: single linkage in d_f + d_xi + (1 - MAC), cut at a distance tau;
+    clusters of at least min_size poles are modes (mean f and xi, medoid pole).
 """
 from __future__ import annotations
 
@@ -47,6 +56,8 @@ __all__ = [
     "realize", "poles_from_eig", "mpc", "mpd", "mac", "normalize_shape",
     "hard_criteria", "stability", "rank_rule", "lag_rule", "time_lag",
     "ssi_solve", "HC_XI", "HC_MPC", "HC_MPD", "ST_HC", "ST_ORDER", "ST_LAG",
+    "rel_diff", "pole_distance", "stage1_features", "fuzzy_c_means", "stage1",
+    "single_linkage_labels", "stage2", "cluster_modes",
 ]
 
 # ---------------------------------------------------------------------------
@@ -419,6 +430,166 @@ def stability(diagram, a_f=0.01, a_xi=0.03, a_mac=0.02, use_lag_axis=True, **hc)
                             cell["flags"][i] |= bit
                             break
     return diagram
+
+
+# ---------------------------------------------------------------------------
+# Sec. 2.3 ("3D clustering") and Sec. 3.1: two-stage clustering of the stable poles
+# ---------------------------------------------------------------------------
+def rel_diff(a: float, b: float) -> float:
+    """d = |a - b| / max(a, b): the relative differences d_f, d_xi of Sec. 3.1."""
+    return abs(a - b) / max(a, b)
+
+
+def pole_distance(f1, xi1, p1, f2, xi2, p2) -> float:
+    """Stage II metric (Sec. 2.3): the sum of the relative differences in frequency and
+    damping and of 1 - MAC between two poles."""
+    return rel_diff(f1, f2) + rel_diff(xi1, xi2) + (1.0 - mac(p1, p2))
+
+
+def stage1_features(diagram):
+    """Stage I inputs (Sec. 2.3, Sec. 3.1).  For every pole that passes HC and is stable
+    along orders or lags (bits 16/32, as set by ``stability``), the feature vector
+        x = (d_f, d_xi, 1 - MAC, 1 - MPC, MPD),
+    where the first three are taken against the pole's nearest HC-passing neighbour in the
+    sense of ``pole_distance``, among the poles of the previous order of the same lag and
+    of the same order of the previous lag (the neighbourhoods of Eq. (stabcriteria3D)).
+    MPC enters as 1 - MPC so that every feature is 0 for an ideal physical pole.
+    Returns X (n, 5) and the list of (t, m, i) of those poles, in diagram order."""
+    X, idx = [], []
+    for t, row in enumerate(diagram):
+        for m, cell in enumerate(row):
+            for i in range(len(cell["f"])):
+                fl = cell["flags"][i]
+                if not (fl & ST_HC) or not (fl & (ST_ORDER | ST_LAG)):
+                    continue
+                best = None
+                nbrs = []
+                if m > 0:
+                    nbrs.append(row[m - 1])
+                if t > 0:
+                    nbrs.append(diagram[t - 1][m])
+                for nb in nbrs:
+                    for j in range(len(nb["f"])):
+                        if not nb["flags"][j] & ST_HC:
+                            continue
+                        df = rel_diff(cell["f"][i], nb["f"][j])
+                        dxi = rel_diff(cell["xi"][i], nb["xi"][j])
+                        dmac = 1.0 - mac(cell["Phi"][:, i], nb["Phi"][:, j])
+                        if best is None or df + dxi + dmac < best[0]:
+                            best = (df + dxi + dmac, df, dxi, dmac)
+                if best is None:
+                    continue
+                X.append([best[1], best[2], best[3], 1.0 - cell["mpc"][i], cell["mpd"][i]])
+                idx.append((t, m, i))
+    return np.array(X, dtype=np.float64).reshape(-1, 5), idx
+
+
+def fuzzy_c_means(X, m: float = 2.0, tol: float = 1e-10, max_iter: int = 500):
+    """Fuzzy C-means with two clusters (Bezdek): alternate
+        u_ck = 1 / sum_j (||x_k - v_c|| / ||x_k - v_j||)^(2 / (m - 1)),
+        v_c  = sum_k u_ck^m x_k / sum_k u_ck^m,
+    from v_1 = the feature-wise minimum and v_2 = the feature-wise maximum of X, until
+    the largest change of a membership is below tol.  A point on a centroid belongs to it
+    alone.  Returns U (n, 2), V (2, d) and the number of iterations."""
+    X = np.asarray(X, dtype=np.float64)
+    n = X.shape[0]
+    V = np.stack([X.min(axis=0), X.max(axis=0)])
+    U = np.full((n, 2), 0.5)
+    it = 0
+    for it in range(1, max_iter + 1):
+        D = np.sqrt(((X[:, None, :] - V[None, :, :]) ** 2).sum(axis=2))
+        Un = np.empty_like(U)
+        for k in range(n):
+            zero = np.nonzero(D[k] == 0.0)[0]
+            if len(zero):
+                Un[k] = 0.0
+                Un[k, zero[0]] = 1.0
+            else:
+                for c in range(2):
+                    Un[k, c] = 1.0 / sum((D[k, c] / D[k, j]) ** (2.0 / (m - 1.0)) for j in range(2))
+        Wm = Un ** m
+        V = (Wm.T @ X) / Wm.sum(axis=0)[:, None]
+        delta = np.abs(Un - U).max() if n else 0.0
+        U = Un
+        if delta < tol:
+            break
+    return U, V, it
+
+
+def stage1(X, **fcm):
+    """Stage I (Sec. 2.3, Sec. 3.1): the possibly physical cluster is the one whose centroid
+    lies nearer the origin; a pole is kept when its membership P of that cluster is
+    >= 0.5.  Returns (keep mask, P, V, index of the physical cluster, iterations)."""
+    U, V, it = fuzzy_c_means(X, **fcm)
+    phys = int(np.argmin(np.linalg.norm(V, axis=1)))
+    P = U[:, phys]
+    return P >= 0.5, P, V, phys, it
+
+
+def single_linkage_labels(D, tau: float):
+    """Clusters of the single-linkage dendrogram cut at distance tau: the connected
+    components of the graph joining i and j whenever D[i, j] <= tau.  Each pole is
+    labelled with the smallest index of its component."""
+    n = D.shape[0]
+    label = np.full(n, -1, dtype=np.int64)
+    for s in range(n):
+        if label[s] >= 0:
+            continue
+        label[s] = s
+        stack = [s]
+        while stack:
+            a = stack.pop()
+            for b in np.nonzero(D[a] <= tau)[0]:
+                if label[b] < 0:
+                    label[b] = s
+                    stack.append(b)
+    return label
+
+
+def stage2(f, xi, Phi, tau: float, min_size: int):
+    """Stage II (Sec. 2.3): single-linkage hierarchical clustering of the kept poles in
+    ``pole_distance``, cut at tau; clusters of at least min_size poles are modes.
+    A mode reports the mean frequency and damping of its poles, its size and its medoid
+    (the member with the smallest sum of distances to the others; ties to the smaller
+    index).  Returns (modes sorted by frequency, labels, D)."""
+    n = len(f)
+    D = np.zeros((n, n))
+    for a in range(n):
+        for b in range(a + 1, n):
+            D[a, b] = D[b, a] = pole_distance(f[a], xi[a], Phi[:, a], f[b], xi[b], Phi[:, b])
+    labels = single_linkage_labels(D, tau)
+    modes = []
+    for lab in np.unique(labels):
+        mem = np.nonzero(labels == lab)[0]
+        if len(mem) < min_size:
+            continue
+        sums = D[np.ix_(mem, mem)].sum(axis=1)
+        medoid = int(mem[int(np.argmin(sums))])
+        modes.append(dict(f=float(np.mean(np.asarray(f, dtype=np.float64)[mem])),
+                          xi=float(np.mean(np.asarray(xi, dtype=np.float64)[mem])),
+                          size=int(len(mem)), medoid=medoid, members=mem))
+    modes.sort(key=lambda d: d["f"])
+    return modes, labels, D
+
+
+def cluster_modes(diagram, tau: float = 0.05, min_size: int = 10, **fcm):
+    """Both stages on a stabilization diagram whose flags come from ``stability``.
+    Returns (modes, stage I keep mask, P, the (t, m, i) of the stage I poles)."""
+    X, idx = stage1_features(diagram)
+    if len(idx) == 0:
+        return [], np.zeros(0, bool), np.zeros(0), idx
+    keep, P, V, phys, it = stage1(X, **fcm)
+    kept = [idx[q] for q in np.nonzero(keep)[0]]
+    f = np.array([diagram[t][m]["f"][i] for t, m, i in kept])
+    xi = np.array([diagram[t][m]["xi"][i] for t, m, i in kept])
+    l = diagram[0][0]["Phi"].shape[0]
+    Phi = np.stack([diagram[t][m]["Phi"][:, i] for t, m, i in kept], axis=1) if kept else \
+        np.zeros((l, 0), complex)
+    modes, labels, D = stage2(f, xi, Phi, tau, min_size)
+    for md in modes:
+        md["medoid"] = kept[md["medoid"]]
+        md["members"] = [kept[q] for q in md["members"]]
+    return modes, keep, P, idx
 
 
 # ---------------------------------------------------------------------------
