@@ -82,7 +82,8 @@ ssi_status ssi_set_concurrency(ssi_ctx* ctx, int solves_in_flight);
  * the previous read, plus the number of kernels the context launched (also reset).
  * Stage ids: 0 split/transpose, 1 lag GEMM, 2 lag reduction, 3 Toeplitz sketch GEMMs,
  * 4 QR, 5 small SVD, 6 Gram/factorisation, 7 eig (Hessenberg, QR iteration, Schur
- * vectors), 8 stability, 9 other, 10 eigenvector back transformation and mode shapes;
+ * vectors), 8 stability, 9 other, 10 eigenvector back transformation and mode shapes,
+ * 11 clustering;
  * stages with ids >= n are not reported. */
 ssi_status ssi_profile(ssi_ctx* ctx, int enable);
 ssi_status ssi_profile_read(ssi_ctx* ctx, double* ms, int64_t* counts, int n, int64_t* launches);
@@ -222,6 +223,68 @@ typedef struct {
 ssi_status ssi_stabilize(ssi_ctx* ctx, int n_lags, int n_orders, const int* orders, int l,
                          ssi_pole* poles, const float* phi, const ssi_stab_params* params,
                          void* stream);
+
+/* ------------------------------------------------------------------------------
+ * Stage (e): two-stage clustering of the stable poles (Sec. 2.3 "3D clustering",
+ * Sec. 3.1) into modes.
+ * Stage I: every pole with SSI_POLE_VALID, SSI_POLE_HC and SSI_POLE_ORDER or
+ * SSI_POLE_LAG (a candidate) gets x = (d_f, d_xi, 1 - MAC, 1 - MPC, MPD), the first three
+ * against its nearest HC-passing neighbour in d_f + d_xi + (1 - MAC) among the poles of
+ * (t, m-1) and (t-1, m), first minimum in slot order, d = |a - b| / max(a, b).  Fuzzy
+ * C-means with two clusters, fuzzifier fcm_m, from the feature-wise minimum and
+ * maximum, stops when no membership changes by fcm_tol or more (or after fcm_max_iter
+ * iterations).  The physical cluster is the one whose centroid is nearer the origin;
+ * a candidate is kept when its membership P of it is >= 1/2.
+ * Stage II: single linkage in d_f + d_xi + (1 - MAC) over the kept poles, cut at tau:
+ * connected components of the graph joining poles at distance <= tau.  Components of
+ * >= min_size poles are the modes, sorted by mean frequency.  Decisions are taken on
+ * FP64 distances.
+ * poles / phi   device, as written by ssi_realize_batch or ssi_solve and flagged by
+ *               ssi_stabilize (phi 8-byte aligned); not modified.
+ * modes         host, max_modes entries; *n_modes receives the number of modes (may
+ *               exceed max_modes: only the first max_modes are written).
+ * features      optional device, 5 doubles per slot: the Stage I features of the
+ *               candidates, zero elsewhere.
+ * membership    optional device, one double per slot: P of the candidates, -1 elsewhere.
+ * label         optional device, one int32 per slot: for a kept pole the slot of the
+ *               first kept pole of its component, -1 elsewhere.
+ * info          optional host: counts, C-means iterations and centroids.
+ * Synchronises `stream` (the mode table is returned on the host); uses the context's
+ * workspace.  SSI_E_INVALID for bad shapes or parameters, SSI_E_TIMEOUT if the C-means
+ * grid barrier gave up.
+ * ---------------------------------------------------------------------------- */
+typedef struct {
+  double tau;              /* Stage II cut distance, e.g. 0.05 */
+  int32_t min_size;        /* smallest component reported as a mode, e.g. 10 */
+  int32_t fcm_max_iter;    /* C-means iteration cap, e.g. 500 */
+  double fcm_m;            /* fuzzifier, > 1; e.g. 2 */
+  double fcm_tol;          /* membership change that ends the iteration, e.g. 1e-10 */
+} ssi_cluster_params;
+
+typedef struct {
+  double f_hz;             /* mean natural frequency of the members [Hz] */
+  double xi;               /* mean damping ratio of the members */
+  int32_t size;            /* number of member poles */
+  int32_t medoid_slot;     /* slot of the medoid (smallest sum of distances to the others,
+                              ties to the earlier pole); its phi is the mode shape */
+} ssi_mode;
+
+typedef struct {
+  int32_t n_candidates;    /* poles entering Stage I */
+  int32_t n_kept;          /* poles kept by Stage I */
+  int32_t n_components;    /* Stage II components before the size cut */
+  int32_t n_modes;
+  int32_t fcm_iterations;
+  int32_t fcm_converged;   /* 0 if fcm_max_iter was reached */
+  int32_t physical;        /* index (0 or 1) of the physical C-means cluster */
+  int32_t reserved;
+  double centroids[2][5];  /* final C-means centroids */
+} ssi_cluster_info;
+
+ssi_status ssi_cluster(ssi_ctx* ctx, int n_lags, int n_orders, const int* orders, int l,
+                       const ssi_pole* poles, const float* phi, const ssi_cluster_params* params,
+                       ssi_mode* modes, int max_modes, int* n_modes, double* features,
+                       double* membership, int32_t* label, ssi_cluster_info* info, void* stream);
 
 /* ------------------------------------------------------------------------------
  * One complete solve (stages a-d) of one record: covariances up to 2*max(lags)-1,

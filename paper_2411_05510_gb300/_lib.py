@@ -39,6 +39,25 @@ class SsiStabParams(ctypes.Structure):
                 ("reserved", ctypes.c_int32)]
 
 
+class SsiClusterParams(ctypes.Structure):
+    _fields_ = [("tau", ctypes.c_double), ("min_size", ctypes.c_int32),
+                ("fcm_max_iter", ctypes.c_int32), ("fcm_m", ctypes.c_double),
+                ("fcm_tol", ctypes.c_double)]
+
+
+class SsiMode(ctypes.Structure):
+    _fields_ = [("f_hz", ctypes.c_double), ("xi", ctypes.c_double), ("size", ctypes.c_int32),
+                ("medoid_slot", ctypes.c_int32)]
+
+
+class SsiClusterInfo(ctypes.Structure):
+    _fields_ = [("n_candidates", ctypes.c_int32), ("n_kept", ctypes.c_int32),
+                ("n_components", ctypes.c_int32), ("n_modes", ctypes.c_int32),
+                ("fcm_iterations", ctypes.c_int32), ("fcm_converged", ctypes.c_int32),
+                ("physical", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("centroids", (ctypes.c_double * 5) * 2)]
+
+
 class SsiJobDesc(ctypes.Structure):
     _fields_ = [("Y", ctypes.c_void_p), ("y_on_host", ctypes.c_int32), ("l", ctypes.c_int32),
                 ("N", ctypes.c_int64), ("fs", ctypes.c_double), ("n_lags", ctypes.c_int32),
@@ -72,6 +91,9 @@ PROTOTYPES = {
                                      _P]),
     "ssi_stabilize": (_c.c_int, [_P, _c.c_int, _c.c_int, _c.POINTER(_c.c_int), _c.c_int, _P, _P,
                                  _c.POINTER(SsiStabParams), _P]),
+    "ssi_cluster": (_c.c_int, [_P, _c.c_int, _c.c_int, _c.POINTER(_c.c_int), _c.c_int, _P, _P,
+                               _c.POINTER(SsiClusterParams), _c.POINTER(SsiMode), _c.c_int,
+                               _c.POINTER(_c.c_int), _P, _P, _P, _c.POINTER(SsiClusterInfo), _P]),
     "ssi_job_sizes": (_c.c_int, [_c.POINTER(SsiJobDesc), _c.POINTER(_c.c_int64),
                                  _c.POINTER(_c.c_int64)]),
     "ssi_solve": (_c.c_int, [_P, _c.POINTER(SsiJobDesc), _P, _P, _P, _P]),

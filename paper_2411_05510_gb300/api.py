@@ -13,13 +13,15 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import SSI_PREC_FP32, SSI_PREC_SPLIT_BF16, SsiJobDesc, SsiStabParams, check, lib
+from ._lib import (SSI_PREC_FP32, SSI_PREC_SPLIT_BF16, SsiClusterInfo, SsiClusterParams, SsiJobDesc,
+                   SsiMode, SsiStabParams, check, lib)
 
 __all__ = [
     "Context", "PREC", "ssi_covariances", "ssi_gaussian_omega", "ssi_toeplitz_rsvd",
     "ssi_realize_batch", "ssi_stabilize", "ssi_solve", "ssi_pole_slots", "poles_to_numpy",
     "stab_params", "job_desc", "ssi_rank_rule", "ssi_lag_rule", "ssi_time_lag", "check_sync",
     "ssi_job_sizes", "ssi_serve_config", "ssi_submit", "ssi_poll", "ssi_release",
+    "cluster_params", "ssi_cluster",
 ]
 
 PREC = {"fp32": SSI_PREC_FP32, "split_bf16": SSI_PREC_SPLIT_BF16}
@@ -67,7 +69,7 @@ class Context:
         check(lib.ssi_set_concurrency(self.ptr, int(solves_in_flight)), "ssi_set_concurrency")
 
     STAGES = ["split", "lag_gemm", "lag_reduce", "sketch_gemm", "qr", "small_svd", "gram_factor",
-              "eig", "stability", "other", "eig_vectors"]
+              "eig", "stability", "other", "eig_vectors", "cluster"]
 
     def profile(self, enable: bool = True) -> None:
         check(lib.ssi_profile(self.ptr, 1 if enable else 0), "ssi_profile")
@@ -152,6 +154,41 @@ def ssi_stabilize(ctx: Context, n_lags: int, orders: Sequence[int], l: int, pole
                             ctypes.c_void_p(poles.data_ptr()), ctypes.c_void_p(phi.data_ptr()),
                             ctypes.byref(params), _stream(poles.device)), "ssi_stabilize")
     return poles
+
+
+def cluster_params(tau=0.05, min_size=10, fcm_max_iter=500, fcm_m=2.0,
+                   fcm_tol=1e-10) -> SsiClusterParams:
+    return SsiClusterParams(tau, min_size, fcm_max_iter, fcm_m, fcm_tol)
+
+
+def ssi_cluster(ctx: Context, n_lags: int, orders: Sequence[int], l: int, poles: torch.Tensor,
+                phi: torch.Tensor, params: SsiClusterParams | None = None, max_modes: int = 1024,
+                per_pole: bool = False):
+    """Two-stage clustering of a flagged diagram.  Returns (modes, info, per_pole) where modes
+    is a list of dicts (f_hz, xi, size, medoid_slot) sorted by frequency, info a dict of
+    ssi_cluster_info, and per_pole (when asked) the device tensors features (slots x 5),
+    membership and label."""
+    params = params or cluster_params()
+    n_slots = poles.numel() * poles.element_size() // _lib.POLE_BYTES
+    feats = memb = lab = None
+    if per_pole:
+        feats = torch.empty((n_slots, 5), dtype=torch.float64, device=poles.device)
+        memb = torch.empty(n_slots, dtype=torch.float64, device=poles.device)
+        lab = torch.empty(n_slots, dtype=torch.int32, device=poles.device)
+    buf = (SsiMode * max(1, max_modes))()
+    n_modes = ctypes.c_int()
+    info = SsiClusterInfo()
+    ptr = (lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None)
+    check(lib.ssi_cluster(ctx.ptr, n_lags, len(orders), _int_array(orders), l,
+                          ctypes.c_void_p(poles.data_ptr()), ctypes.c_void_p(phi.data_ptr()),
+                          ctypes.byref(params), buf, max_modes, ctypes.byref(n_modes), ptr(feats),
+                          ptr(memb), ptr(lab), ctypes.byref(info), _stream(poles.device)),
+          "ssi_cluster")
+    modes = [dict(f_hz=buf[i].f_hz, xi=buf[i].xi, size=buf[i].size, medoid_slot=buf[i].medoid_slot)
+             for i in range(min(n_modes.value, max_modes))]
+    inf = {f: getattr(info, f) for f, _ in SsiClusterInfo._fields_ if f not in ("centroids", "reserved")}
+    inf["centroids"] = np.array([[info.centroids[c][d] for d in range(5)] for c in range(2)])
+    return modes, inf, (dict(features=feats, membership=memb, label=lab) if per_pole else None)
 
 
 def job_desc(Y, fs: float, lags: Sequence[int], orders: Sequence[int], k: int, oversample: int = 0,

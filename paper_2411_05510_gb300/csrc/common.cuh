@@ -80,7 +80,7 @@ namespace ssi {
 // stage ids of the optional per-stage timers (ssi_profile / ssi_profile_read)
 enum Stage : int {
   ST_SPLIT = 0, ST_LAG_GEMM = 1, ST_LAG_REDUCE = 2, ST_SKETCH_GEMM = 3, ST_QR = 4, ST_SMALL_SVD = 5,
-  ST_GRAM = 6, ST_EIG = 7, ST_STAB = 8, ST_OTHER = 9, ST_EIG_VEC = 10, ST_COUNT = 11
+  ST_GRAM = 6, ST_EIG = 7, ST_STAB = 8, ST_OTHER = 9, ST_EIG_VEC = 10, ST_CLUSTER = 11, ST_COUNT = 12
 };
 }  // namespace ssi
 

@@ -51,3 +51,20 @@ def test_invalid_arguments_fail_before_any_device_work():
         P.ssi_rank_rule(0)
     with pytest.raises(P._lib.SsiError):
         P.ssi_lag_rule(100.0, -1.0)
+
+
+def test_cluster_abi_layout_and_argument_checks():
+    import ctypes
+
+    import paper_2411_05510_gb300 as P
+    L = P._lib
+    assert ctypes.sizeof(L.SsiClusterParams) == 32
+    assert ctypes.sizeof(L.SsiMode) == 24
+    assert ctypes.sizeof(L.SsiClusterInfo) == 32 + 80
+    orders = (ctypes.c_int * 2)(2, 4)
+    n_modes = ctypes.c_int(-1)
+    params = P.cluster_params()
+    # a null context, poles or phi is refused before any device work
+    st = L.lib.ssi_cluster(None, 1, 2, orders, 4, None, None, ctypes.byref(params), None, 0,
+                           ctypes.byref(n_modes), None, None, None, None, None)
+    assert st == 1
