@@ -16,7 +16,8 @@
 // mean frequency and damping of its poles, its size and its medoid (the member with the
 // smallest sum of distances to the others, ties to the earlier pole).
 //
-// Every decision (nearest neighbour, link, medoid) is taken on FP64 distances.  MACs are
+// Every decision (nearest neighbour, link) is taken on FP64 distances, the medoid on sums
+// of double-float-accurate distances (~1e-13 relative).  MACs are
 // first screened in FP32 (lanes over channels, FP32 FMA): the FP32 MAC of unit vectors
 // differs from the exact one by at most eps = 2 (5 gamma + 4 u), gamma = (2 ceil(l/32) + 5) u,
 // u = 2^-24 (the per-lane FMA chain plus the shuffle tree; the bound is relative to
@@ -30,14 +31,19 @@
 //   k_fcm           cooperative persistent kernel: candidate min/max, the C-means
 //                   iterations with a fixed-order reduction over fixed slot chunks (bit-
 //                   identical for any grid size), memberships, the ordered list of kept poles
+//   k_prelink       join each kept pole to its Stage I nearest neighbour when that one is
+//                   kept and within tau (an exact Stage II link found for free)
+//   k_compress      point every kept pole at its root
 //   k_link          tiles of 32 x 32 kept-pole pairs: screen by d_f + d_xi, skip pairs
 //                   already connected, decide d <= tau, join components (lock-free union-
 //                   find whose roots are the smallest index of their component)
 //   k_label         component root and size of every kept pole
 //   k_modes_scan    one CTA: components in index order, those with >= min_size poles
 //   k_mode_members  one CTA per mode: its members in index order, mean f and xi
-//   k_medoid_sums   one warp per member: FP32-screened sum of distances to its mode
-//   k_medoid_pick   one CTA per mode: medoid candidates, FP64 sums, first minimum
+//   k_medoid_prep   one warp per member: FP64 reciprocals of f, xi and |phi|^2
+//   k_medoid_sums   one warp per member: sum of distances to its mode (double-float
+//                   cross products, FP64 finish of 32 partners side by side)
+//   k_medoid_pick   one CTA per mode: first minimum
 #include "common.cuh"
 #include "blackwell.cuh"
 
@@ -78,7 +84,6 @@ __device__ __forceinline__ double rel_diff(double a, double b) { return fabs(a -
 __device__ __forceinline__ float rel_sum32(float fa, float fb, float xa, float xb) {
   return fabsf(fa - fb) / fmaxf(fa, fb) + fabsf(xa - xb) / fmaxf(xa, xb);
 }
-constexpr float SCREEN_REL = 1e-6f;   // margin of the FP32 screen (>> 3 ulp)
 
 __device__ __forceinline__ bool pole_live(uint32_t fl) {
   return (fl & SSI_POLE_VALID) && (fl & SSI_POLE_HC);
@@ -146,8 +151,10 @@ __device__ __forceinline__ double mac64(const float2* __restrict__ a, const floa
 // ---------------------------------------------------------------------------------
 __global__ void __launch_bounds__(CL_THREADS) k_features(const ssi_pole* __restrict__ poles,
                                                          const float* __restrict__ phi, Grid g,
-                                                         double eps, double* __restrict__ feat,
-                                                         unsigned char* __restrict__ cand) {
+                                                         float E, double* __restrict__ feat,
+                                                         unsigned char* __restrict__ cand,
+                                                         int* __restrict__ nbr,
+                                                         double* __restrict__ ndist) {
   const int lane = threadIdx.x & 31;
   const long long warp0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -176,48 +183,76 @@ __global__ void __launch_bounds__(CL_THREADS) k_features(const ssi_pole* __restr
     }
     const double fq = q.f_hz, xq = q.xi;
     const float2* pq = ph + (size_t)e * pstride;
-    // pass 1: the smallest FP32-screened total
-    double best32 = INFINITY;
+    // Pass 1 (FP32 only): the smallest screened total t32 = s32 + (1 - MAC32), which is
+    // within E of the FP64 total.  Lanes take 32 neighbours at a time for the scalar
+    // part; the warp then computes the MACs of the survivors in order.  A neighbour is
+    // skipped only when s32 alone exceeds best32 + 3 E.
+    float best32 = INFINITY;
     for (int c = 0; c < nn; ++c) {
-      for (int j = 0; j < nb_cnt[c]; ++j) {
-        const long long o_e = nb_base[c] + j;
-        const ssi_pole o = poles[o_e];
-        if (!pole_live(o.flags)) continue;
-        const float s32 = rel_sum32(q.f_hz, o.f_hz, q.xi, o.xi);
-        if ((double)s32 * (1.0 - SCREEN_REL) > best32 + 3.0 * eps) continue;
-        const double s = rel_diff(fq, (double)o.f_hz) + rel_diff(xq, (double)o.xi);
-        if (s > best32 + 3.0 * eps) continue;
-        const float mc = mac32(pq, ph + (size_t)o_e * pstride, g.l, lane);
-        const double tt = s + (1.0 - (double)mc);
-        if (tt < best32) best32 = tt;
+      for (int j0 = 0; j0 < nb_cnt[c]; j0 += 32) {
+        const int j = j0 + lane;
+        bool ok = j < nb_cnt[c];
+        float s32 = 0.f;
+        if (ok) {
+          const ssi_pole o = poles[nb_base[c] + j];
+          ok = pole_live(o.flags);
+          if (ok) {
+            s32 = rel_sum32(q.f_hz, o.f_hz, q.xi, o.xi);
+            ok = s32 <= best32 + 3.f * E;
+          }
+        }
+        unsigned bal = __ballot_sync(0xffffffffu, ok);
+        while (bal) {
+          const int jj = __ffs(bal) - 1;
+          bal &= bal - 1;
+          const float sj = __shfl_sync(0xffffffffu, s32, jj);
+          if (sj > best32 + 3.f * E) continue;
+          const float mc = mac32(pq, ph + (size_t)(nb_base[c] + j0 + jj) * pstride, g.l, lane);
+          best32 = fminf(best32, sj + (1.f - mc));
+        }
       }
     }
     if (!(best32 < INFINITY)) {
       if (lane == 0) cand[e] = 0;
       continue;
     }
-    // pass 2: FP64 totals of the neighbours within 2 eps of it; first minimum
+    // Pass 2: FP64 totals of the neighbours whose screened total lies within 2 E of
+    // best32 (the FP64 minimum is among them); first minimum in scan order.
     double best = INFINITY, bf = 0.0, bx = 0.0, bm = 0.0;
+    long long barg = -1;
     for (int c = 0; c < nn; ++c) {
-      for (int j = 0; j < nb_cnt[c]; ++j) {
-        const long long o_e = nb_base[c] + j;
-        const ssi_pole o = poles[o_e];
-        if (!pole_live(o.flags)) continue;
-        const float s32 = rel_sum32(q.f_hz, o.f_hz, q.xi, o.xi);
-        if ((double)s32 * (1.0 - SCREEN_REL) > best32 + 3.0 * eps) continue;
-        const double df = rel_diff(fq, (double)o.f_hz), dx = rel_diff(xq, (double)o.xi);
-        const double s = df + dx;
-        if (s > best32 + 3.0 * eps) continue;
-        const float2* po = ph + (size_t)o_e * pstride;
-        const float mc = mac32(pq, po, g.l, lane);
-        if (s + (1.0 - (double)mc) > best32 + 2.0 * eps) continue;
-        const double dm = 1.0 - mac64(pq, po, g.l, lane);
-        const double tot = s + dm;
-        if (tot < best) {
-          best = tot;
-          bf = df;
-          bx = dx;
-          bm = dm;
+      for (int j0 = 0; j0 < nb_cnt[c]; j0 += 32) {
+        const int j = j0 + lane;
+        bool ok = j < nb_cnt[c];
+        float s32 = 0.f;
+        if (ok) {
+          const ssi_pole o = poles[nb_base[c] + j];
+          ok = pole_live(o.flags);
+          if (ok) {
+            s32 = rel_sum32(q.f_hz, o.f_hz, q.xi, o.xi);
+            ok = s32 <= best32 + 3.f * E;
+          }
+        }
+        unsigned bal = __ballot_sync(0xffffffffu, ok);
+        while (bal) {
+          const int jj = __ffs(bal) - 1;
+          bal &= bal - 1;
+          const float sj = __shfl_sync(0xffffffffu, s32, jj);
+          const long long o_e = nb_base[c] + j0 + jj;
+          const float2* po = ph + (size_t)o_e * pstride;
+          const float mc = mac32(pq, po, g.l, lane);
+          if (sj + (1.f - mc) > best32 + 2.f * E) continue;
+          const ssi_pole o = poles[o_e];
+          const double dfj = rel_diff(fq, (double)o.f_hz), dxj = rel_diff(xq, (double)o.xi);
+          const double dm = 1.0 - mac64(pq, po, g.l, lane);
+          const double tot = (dfj + dxj) + dm;
+          if (tot < best) {
+            best = tot;
+            bf = dfj;
+            bx = dxj;
+            bm = dm;
+            barg = o_e;
+          }
         }
       }
     }
@@ -229,6 +264,8 @@ __global__ void __launch_bounds__(CL_THREADS) k_features(const ssi_pole* __restr
       x[3] = 1.0 - (double)q.mpc;
       x[4] = (double)q.mpd;
       cand[e] = 1;
+      nbr[e] = (int)barg;
+      ndist[e] = best;
     }
   }
 }
@@ -251,6 +288,7 @@ struct FcmParams {
   int* label_out;         // per slot (optional): -1 here, kept poles relabelled later
   int* kept_slot;         // n
   int* parent;            // n
+  int* slot2kept;         // n: position in the kept list, or -1
   Hdr* hdr;
   unsigned* bar;
   int* abort_flag;
@@ -535,6 +573,7 @@ __global__ void __launch_bounds__(CL_THREADS, 1) k_fcm(FcmParams p) {
       const bool keep = is_c && P >= 0.5;
       if (in && p.membership) p.membership[e] = P;
       if (in && p.label_out) p.label_out[e] = -1;
+      if (in && !keep) p.slot2kept[e] = -1;
       const unsigned bal = __ballot_sync(0xffffffffu, keep);
       if (lane == 0) sw[wid] = __popc(bal);
       __syncthreads();
@@ -546,6 +585,7 @@ __global__ void __launch_bounds__(CL_THREADS, 1) k_fcm(FcmParams p) {
         const int pos = off + __popc(bal & ((1u << lane) - 1u));
         p.kept_slot[pos] = (int)e;
         p.parent[pos] = pos;
+        p.slot2kept[e] = pos;
       }
       base += tot;
       __syncthreads();
@@ -611,6 +651,8 @@ struct LinkParams {
   const int* n_kept;     // device
   int* parent;
   double tau, eps;
+  float tau32;           // FP32 screen of d_f + d_xi <= tau
+  float tau_lo, tau_hi;  // FP32 distances <= tau_lo link, > tau_hi do not
   long long n_tiles;
   int nb;                // tiles per side
   int* status;
@@ -656,34 +698,54 @@ __global__ void __launch_bounds__(CL_THREADS) k_link(LinkParams p) {
       const int a = bi * 32 + ar;
       if (a >= nk) break;                         // warp-uniform
       bool need = b < nk && b > a;
-      double s = 0.0;
+      float s = 0.f;
       if (need) {
-        const float fa = s_f[0][ar], fb = s_f[1][lane], xa = s_x[0][ar], xb = s_x[1][lane];
-        need = (double)rel_sum32(fa, fb, xa, xb) * (1.0 - SCREEN_REL) <= p.tau + 1e-12;
-        if (need) {
-          s = rel_diff(fa, fb) + rel_diff(xa, xb);
-          need = s <= p.tau + 1e-12;
-        }
+        s = rel_sum32(s_f[0][ar], s_f[1][lane], s_x[0][ar], s_x[1][lane]);
+        need = s <= p.tau32;
+        // already connected: nothing to decide (each lane looks up its own pair)
+        if (need) need = uf_find(p.parent, a) != uf_find(p.parent, b);
       }
       unsigned bal = __ballot_sync(0xffffffffu, need);
       while (bal) {
         const int j = __ffs(bal) - 1;
         bal &= bal - 1;
-        const double sj = __shfl_sync(0xffffffffu, s, j);
+        const float sj = __shfl_sync(0xffffffffu, s, j);
         const int bb = bj * 32 + j;
-        // already connected: nothing to decide
-        int same = 0;
-        if (lane == 0) same = uf_find(p.parent, a) == uf_find(p.parent, bb);
-        same = __shfl_sync(0xffffffffu, same, 0);
-        if (same) continue;
         const float2* pa = p.phi + (size_t)s_slot[0][ar] * p.l;
         const float2* pb = p.phi + (size_t)s_slot[1][j] * p.l;
-        const double d32 = sj + (1.0 - (double)mac32(pa, pb, p.l, lane));
-        bool link = d32 <= p.tau - p.eps;
-        if (!link && d32 <= p.tau + p.eps) link = sj + (1.0 - mac64(pa, pb, p.l, lane)) <= p.tau;
+        const float d32 = sj + (1.f - mac32(pa, pb, p.l, lane));
+        bool link = d32 <= p.tau_lo;
+        if (!link && d32 <= p.tau_hi) {
+          // inconclusive in FP32: the FP64 distance decides
+          const double s64 = rel_diff(s_f[0][ar], s_f[1][j]) + rel_diff(s_x[0][ar], s_x[1][j]);
+          link = s64 + (1.0 - mac64(pa, pb, p.l, lane)) <= p.tau;
+        }
         if (link && lane == 0) uf_union(p.parent, a, bb, p.status);
       }
     }
+  }
+}
+
+// Stage I already found each candidate's nearest neighbour and its FP64 distance (the
+// Stage II metric): kept pairs within tau are joined first, which connects most of each
+// mode's poles at linear cost.  Then every pole points at its root.
+__global__ void k_prelink(const int* __restrict__ kept_slot, const int* __restrict__ n_kept,
+                          const int* __restrict__ nbr, const double* __restrict__ ndist,
+                          const int* __restrict__ slot2kept, double tau, int* parent, int* status) {
+  const int nk = *n_kept;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nk; i += gridDim.x * blockDim.x) {
+    const int e = kept_slot[i];
+    if (!(ndist[e] <= tau)) continue;
+    const int j = slot2kept[nbr[e]];
+    if (j >= 0) uf_union(parent, i, j, status);
+  }
+}
+
+__global__ void k_compress(int* parent, const int* __restrict__ n_kept) {
+  const int nk = *n_kept;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nk; i += gridDim.x * blockDim.x) {
+    const int r = uf_find(parent, i);
+    parent[i] = r;
   }
 }
 
@@ -828,83 +890,141 @@ struct MedoidParams {
   const int* member_mode;
   const int* mode_off;
   int n_members;
-  double eps;
-  double* sum32;
-  double* sum64;
+  double* inv;        // per member: 1/f, 1/xi, 1/|phi|^2 (FP64)
+  double* sum;        // per member: sum of distances to the other members
   int* medoid;        // per mode: slot of the medoid
 };
 
-// Distance between two members: FP64 throughout, or the FP32 screen (d_f + d_xi within
-// 3 ulp, the MAC within eps; the caller's bound adds 1e-6 per distance for both).
-__device__ __forceinline__ double member_dist(const MedoidParams& p, int ea, float fa, float xa,
-                                              int eb, bool fp64, int lane) {
-  const ssi_pole qb = p.poles[eb];
-  const float2* pa = p.phi + (size_t)ea * p.l;
-  const float2* pb = p.phi + (size_t)eb * p.l;
-  if (fp64) {
-    const double s = rel_diff(fa, qb.f_hz) + rel_diff(xa, qb.xi);
-    return s + (1.0 - mac64(pa, pb, p.l, lane));
+// Error-free transformations in FP32 (Knuth's two-sum; the product split by an FMA).
+// Intrinsics keep the compiler from contracting or reassociating them.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bp = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp));
+}
+// (hi, lo) += a * b
+__device__ __forceinline__ void df_fma(float& hi, float& lo, float a, float b) {
+  const float p = __fmul_rn(a, b);
+  const float pe = __fmaf_rn(a, b, -p);
+  float s, e;
+  two_sum(hi, p, s, e);
+  hi = s;
+  lo = __fadd_rn(lo, __fadd_rn(e, pe));
+}
+// One warp per member: 1/f, 1/xi and 1/|phi|^2 in FP64 (exact products, FP64 sum).
+__global__ void __launch_bounds__(CL_THREADS) k_medoid_prep(MedoidParams p) {
+  const int lane = threadIdx.x & 31;
+  const long long warp0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long q = warp0; q < p.n_members; q += nwarps) {
+    const int e = p.kept_slot[p.members[q]];
+    const float2* pa = p.phi + (size_t)e * p.l;
+    double na = 0.0;
+    for (int c = lane; c < p.l; c += 32) {
+      const float2 x = pa[c];
+      na += (double)x.x * x.x + (double)x.y * x.y;
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) na += __shfl_xor_sync(0xffffffffu, na, o);
+    if (lane == 0) {
+      const ssi_pole qa = p.poles[e];
+      p.inv[q * 3] = 1.0 / (double)qa.f_hz;
+      p.inv[q * 3 + 1] = 1.0 / (double)qa.xi;
+      p.inv[q * 3 + 2] = na > 0.0 ? 1.0 / na : 0.0;
+    }
   }
-  return (double)rel_sum32(fa, qb.f_hz, xa, qb.xi) + (1.0 - (double)mac32(pa, pb, p.l, lane));
 }
 
-// One warp per member: FP32-screened sum of distances to the other members of its mode.
+// (hi, lo) summed over the warp (butterfly: every lane gets the total)
+__device__ __forceinline__ void df_warp_allsum(float& hi, float& lo) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+    const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+    float s, e;
+    two_sum(hi, h2, s, e);
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(l2, e));
+  }
+}
+
+// One warp per member: the sum of its distances to the other members of its mode.  The
+// cross products a^H b are accumulated in double-float (FP32 pairs, ~1e-13 relative),
+// 32 partners at a time with lanes over channels; lane j keeps partner j's products and
+// the 32 distances are then finished in FP64 side by side (1/max(a, b) = min(1/a, 1/b)
+// from the FP64 reciprocals) and added by a fixed butterfly.
 __global__ void __launch_bounds__(CL_THREADS) k_medoid_sums(MedoidParams p) {
   const int lane = threadIdx.x & 31;
   const long long warp0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-  for (long long pa = warp0; pa < p.n_members; pa += nwarps) {
-    const int md = p.member_mode[pa];
+  for (long long qa = warp0; qa < p.n_members; qa += nwarps) {
+    const int md = p.member_mode[qa];
     const int b0 = p.mode_off[md], b1 = p.mode_off[md + 1];
-    const int ea = p.kept_slot[p.members[pa]];
-    const ssi_pole qa = p.poles[ea];
+    const int ea = p.kept_slot[p.members[qa]];
+    const float2* pa = p.phi + (size_t)ea * p.l;
     double sum = 0.0;
-    for (int pb = b0; pb < b1; ++pb) {
-      if (pb == pa) continue;
-      sum += member_dist(p, ea, qa.f_hz, qa.xi, p.kept_slot[p.members[pb]], false, lane);
+    for (int qb0 = b0; qb0 < b1; qb0 += 32) {
+      const int cnt = min(32, b1 - qb0);
+      float kr_h = 0.f, kr_l = 0.f, ki_h = 0.f, ki_l = 0.f;
+      for (int jj = 0; jj < cnt; ++jj) {
+        if (qb0 + jj == qa) continue;                     // warp-uniform
+        const float2* pb = p.phi + (size_t)p.kept_slot[p.members[qb0 + jj]] * p.l;
+        float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+        for (int c = lane; c < p.l; c += 32) {
+          const float2 x = pa[c], y = pb[c];
+          df_fma(rh, rl, x.x, y.x);
+          df_fma(rh, rl, x.y, y.y);
+          df_fma(ih, il, x.x, y.y);
+          df_fma(ih, il, -x.y, y.x);
+        }
+        df_warp_allsum(rh, rl);
+        df_warp_allsum(ih, il);
+        if (lane == jj) {
+          kr_h = rh; kr_l = rl; ki_h = ih; ki_l = il;
+        }
+      }
+      double d = 0.0;
+      const int qb = qb0 + lane;
+      if (lane < cnt && qb != qa) {
+        const ssi_pole pola = p.poles[ea];
+        const ssi_pole polb = p.poles[p.kept_slot[p.members[qb]]];
+        const double dr = (double)kr_h + (double)kr_l, di = (double)ki_h + (double)ki_l;
+        const double s = fabs((double)pola.f_hz - (double)polb.f_hz) * fmin(p.inv[qa * 3], p.inv[qb * 3]) +
+                         fabs((double)pola.xi - (double)polb.xi) * fmin(p.inv[qa * 3 + 1], p.inv[qb * 3 + 1]);
+        const double mac = (dr * dr + di * di) * p.inv[qa * 3 + 2] * p.inv[qb * 3 + 2];
+        d = s + (1.0 - mac);
+      }
+#pragma unroll
+      for (int o = 16; o; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+      sum += d;
     }
-    if (lane == 0) p.sum32[pa] = sum;
+    if (lane == 0) p.sum[qa] = sum;
   }
 }
 
-// One CTA per mode: members whose screened sum lies within 2 (size - 1) (eps + 1e-6) of
-// the smallest get their FP64 sums; the medoid is the first of those with the smallest.
+// One CTA per mode: the member with the smallest sum, ties to the earlier one.
 __global__ void __launch_bounds__(CL_THREADS) k_medoid_pick(MedoidParams p) {
-  __shared__ double sh[CL_WARPS];
-  __shared__ double s_min;
-  __shared__ int s_arg[CL_WARPS];
   __shared__ double s_val[CL_WARPS];
+  __shared__ int s_arg[CL_WARPS];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int md = blockIdx.x;
   const int b0 = p.mode_off[md], b1 = p.mode_off[md + 1];
-  double mn = INFINITY;
-  for (int q = b0 + threadIdx.x; q < b1; q += CL_THREADS) mn = fmin(mn, p.sum32[q]);
-  for (int o = 16; o; o >>= 1) mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
-  if (lane == 0) sh[wid] = mn;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double a = sh[0];
-    for (int w = 1; w < CL_WARPS; ++w) a = fmin(a, sh[w]);
-    s_min = a;
-  }
-  __syncthreads();
-  const double thr = s_min + 2.0 * (double)(b1 - b0 - 1) * (p.eps + 1e-6);
-  // FP64 sums of the candidates, one warp each, in member order
   double best = INFINITY;
   int arg = 0x7fffffff;
-  for (int q = b0 + wid; q < b1; q += CL_WARPS) {
-    if (p.sum32[q] > thr) continue;                 // warp-uniform
-    const int ea = p.kept_slot[p.members[q]];
-    const ssi_pole qa = p.poles[ea];
-    double sum = 0.0;
-    for (int pb = b0; pb < b1; ++pb) {
-      if (pb == q) continue;
-      sum += member_dist(p, ea, qa.f_hz, qa.xi, p.kept_slot[p.members[pb]], true, lane);
-    }
-    if (lane == 0) p.sum64[q] = sum;
-    if (sum < best) {                               // q ascends within the warp
-      best = sum;
+  for (int q = b0 + threadIdx.x; q < b1; q += CL_THREADS) {
+    const double v = p.sum[q];
+    if (v < best) {            // q ascends within the thread
+      best = v;
       arg = q;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    const double v2 = __shfl_xor_sync(0xffffffffu, best, o);
+    const int a2 = __shfl_xor_sync(0xffffffffu, arg, o);
+    if (v2 < best || (v2 == best && a2 < arg)) {
+      best = v2;
+      arg = a2;
     }
   }
   if (lane == 0) {
@@ -957,6 +1077,9 @@ ssi_status cluster_run(ssi_ctx* ctx, int n_lags, int n_orders, const int* orders
   SSI_CHECK(n <= (1ll << 30), "ssi_cluster: too many pole slots");
   const int n_chunks = (int)ceil_div(n, FCM_CH);
   const double eps = mac_screen_eps(l);
+  // bound on |t32 - t64| for a screened distance t = d_f + d_xi + (1 - MAC): the MAC
+  // bound plus the FP32 rounding of d_f + d_xi (<= 2, 3 ulp) and of the final sum
+  const float E32 = (float)(eps + 1e-6);
 
   // workspace
   WsPlan wp;
@@ -969,8 +1092,11 @@ ssi_status cluster_run(ssi_ctx* ctx, int n_lags, int n_orders, const int* orders
   for (int k = 0; k < 7; ++k) wp.add<int>((size_t)n + 1);   // kept, parent, lab, size, roots, offsets, members
   wp.add<int>((size_t)n + 1);                               // member_mode
   wp.add<double>((size_t)n * 2);                            // mode f / xi
-  wp.add<double>((size_t)n * 2);                            // sum32, sum64
+  wp.add<double>((size_t)n * 4);                            // medoid reciprocals, sums
   wp.add<int>((size_t)n + 1);                               // medoid
+  wp.add<int>((size_t)n);                                   // nearest neighbour
+  wp.add<double>((size_t)n);                                // its distance
+  wp.add<int>((size_t)n);                                   // slot -> kept index
   wp.add<Hdr>(1);
   wp.add<unsigned>(64);
   SSI_TRY(ws_reserve(ctx, ctx->ws, wp.bytes, stream));
@@ -991,13 +1117,16 @@ ssi_status cluster_run(ssi_ctx* ctx, int n_lags, int n_orders, const int* orders
   int* members = ws.take<int>((size_t)n + 1);
   int* member_mode = ws.take<int>((size_t)n + 1);
   double* mode_fx = ws.take<double>((size_t)n * 2);
-  double* sums = ws.take<double>((size_t)n * 2);
+  double* sums = ws.take<double>((size_t)n * 4);
   int* medoid = ws.take<int>((size_t)n + 1);
+  int* nbr = ws.take<int>((size_t)n);
+  double* ndist = ws.take<double>((size_t)n);
+  int* slot2kept = ws.take<int>((size_t)n);
   Hdr* hdr = ws.take<Hdr>(1);
   unsigned* bar = ws.take<unsigned>(64);
   if (!feat || !cand || !u || !part || !mm || !kcount || !kept || !parent || !lab || !csize ||
       !mode_root || !mode_off || !members || !member_mode || !mode_fx || !sums || !medoid || !hdr ||
-      !bar) {
+      !bar || !nbr || !ndist || !slot2kept) {
     set_error("ssi_cluster: workspace too small");
     return SSI_E_NOMEM;
   }
@@ -1008,7 +1137,8 @@ ssi_status cluster_run(ssi_ctx* ctx, int n_lags, int n_orders, const int* orders
   {
     const int blocks = (int)std::min<long long>(ceil_div(n * 32, CL_THREADS), (long long)ctx->num_sms * 16);
     count_launches(ctx, 1);
-    k_features<<<std::max(blocks, 1), CL_THREADS, 0, stream>>>(poles, phi, g, eps, feat, cand);
+    k_features<<<std::max(blocks, 1), CL_THREADS, 0, stream>>>(poles, phi, g, E32, feat, cand, nbr,
+                                                               ndist);
     SSI_CUDA(cudaGetLastError());
   }
   // Stage I C-means and the kept list
@@ -1031,6 +1161,7 @@ ssi_status cluster_run(ssi_ctx* ctx, int n_lags, int n_orders, const int* orders
     fp.label_out = label;
     fp.kept_slot = kept;
     fp.parent = parent;
+    fp.slot2kept = slot2kept;
     fp.hdr = hdr;
     fp.bar = bar;
     fp.abort_flag = reinterpret_cast<int*>(bar + 8);
@@ -1070,12 +1201,21 @@ ssi_status cluster_run(ssi_ctx* ctx, int n_lags, int n_orders, const int* orders
     lp.parent = parent;
     lp.tau = cp->tau;
     lp.eps = eps;
+    lp.tau32 = std::nextafter((float)((cp->tau + 1e-12) / (1.0 - 1e-6)), INFINITY);
+    lp.tau_lo = std::nextafter((float)(cp->tau - 2.0 * E32), -INFINITY);
+    lp.tau_hi = std::nextafter((float)(cp->tau + 2.0 * E32), INFINITY);
     lp.nb = nb;
     lp.n_tiles = (long long)nb * (nb + 1) / 2;
     lp.status = ctx->dev_status;
     const int lblocks = (int)std::min<long long>(lp.n_tiles, (long long)ctx->num_sms * 8);
     SSI_CUDA(cudaMemsetAsync(csize, 0, sizeof(int) * (size_t)nk, stream));
-    count_launches(ctx, 3);
+    const int pb = (int)std::min<long long>(ceil_div(nk, 256), (long long)ctx->num_sms * 4);
+    count_launches(ctx, 5);
+    k_prelink<<<pb, 256, 0, stream>>>(kept, &hdr->n_kept, nbr, ndist, slot2kept, cp->tau, parent,
+                                      ctx->dev_status);
+    SSI_CUDA(cudaGetLastError());
+    k_compress<<<pb, 256, 0, stream>>>(parent, &hdr->n_kept);
+    SSI_CUDA(cudaGetLastError());
     k_link<<<lblocks, CL_THREADS, 0, stream>>>(lp);
     SSI_CUDA(cudaGetLastError());
     const int lb = (int)std::min<long long>(ceil_div(nk, 256), (long long)ctx->num_sms * 4);
@@ -1104,12 +1244,14 @@ ssi_status cluster_run(ssi_ctx* ctx, int n_lags, int n_orders, const int* orders
       mp.member_mode = member_mode;
       mp.mode_off = mode_off;
       mp.n_members = off[n_modes];
-      mp.eps = eps;
-      mp.sum32 = sums;
-      mp.sum64 = sums + n;
+      mp.inv = sums;
+      mp.sum = sums + (size_t)3 * n;
       mp.medoid = medoid;
       const int mblocks = (int)std::min<long long>(ceil_div((long long)mp.n_members * 32, CL_THREADS),
                                                    (long long)ctx->num_sms * 16);
+      count_launches(ctx, 1);
+      k_medoid_prep<<<std::max(mblocks, 1), CL_THREADS, 0, stream>>>(mp);
+      SSI_CUDA(cudaGetLastError());
       k_medoid_sums<<<std::max(mblocks, 1), CL_THREADS, 0, stream>>>(mp);
       SSI_CUDA(cudaGetLastError());
       k_medoid_pick<<<n_modes, CL_THREADS, 0, stream>>>(mp);
