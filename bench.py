@@ -63,6 +63,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--no-cluster", action="store_true")
     ap.add_argument("--inflight", type=int, default=4,
                     help="solves in flight at once, each on its own stream and context")
     return ap.parse_args()
@@ -596,6 +597,37 @@ def main():
                                                 "jobs": n_e2e},
                           "api": f"ssi_submit/ssi_poll ({J} slots), record in pinned host "
                                  f"memory, host clock around all jobs"}
+
+    # the next stage of the method on the diagram of the solves above: two-stage clustering
+    # of the stable poles into modes (Sec. 2.3, Sec. 3.1), one synchronous call at a time
+    if not args.no_cluster:
+        ln = lanes[0]
+        ln["stream"].synchronize()
+        prm = P.cluster_params(tau=0.05, min_size=10 if len(w["lags"]) == 1 else 50)
+        n_cl = max(5, min(args.steps, 20))
+        tc = []
+        with torch.cuda.stream(ln["stream"]):
+            for _ in range(3):
+                P.ssi_cluster(ln["ctx"], len(w["lags"]), w["orders"], l, ln["poles"], ln["phi"], prm)
+            ln["ctx"].profile(True)
+            ln["ctx"].profile_read()
+            for _ in range(n_cl):
+                t0 = time.perf_counter()
+                modes, info, _ = P.ssi_cluster(ln["ctx"], len(w["lags"]), w["orders"], l,
+                                               ln["poles"], ln["phi"], prm)
+                tc.append((time.perf_counter() - t0) * 1e3)
+            st_ms, _, cl_launches = ln["ctx"].profile_read()
+            ln["ctx"].profile(False)
+        if rank == 0:
+            found = sum(any(abs(m["f_hz"] - f0) / f0 < 1e-2 for m in modes) for f0 in f_true)
+            out["cluster"] = {"ms_per_call": pct(tc, 50), "device_ms_per_call": st_ms["cluster"] / n_cl,
+                              "kernel_launches_per_call": cl_launches / n_cl, "calls": n_cl,
+                              "modes": len(modes), "generating_modes_within_1pct": int(found),
+                              "candidates": info["n_candidates"], "kept": info["n_kept"],
+                              "fcm_iterations": info["fcm_iterations"],
+                              "params": {"tau": 0.05, "min_size": prm.min_size, "fcm_m": 2.0,
+                                         "fcm_tol": 1e-10},
+                              "api": "ssi_cluster on one solve's poles (synchronous, host clock)"}
 
     # the plain FP32 path of the same pipeline on the same GPU, measured the same way
     if not args.no_fp32 and args.prec == "split_bf16":
