@@ -64,6 +64,7 @@ def parse():
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--no-cluster", action="store_true")
+    ap.add_argument("--no-stream", action="store_true")
     ap.add_argument("--inflight", type=int, default=4,
                     help="solves in flight at once, each on its own stream and context")
     return ap.parse_args()
@@ -628,6 +629,41 @@ def main():
                               "params": {"tau": 0.05, "min_size": prm.min_size, "fcm_m": 2.0,
                                          "fcm_tol": 1e-10},
                               "api": "ssi_cluster on one solve's poles (synchronous, host clock)"}
+
+    # continuous monitoring: sliding-window covariances of the record (window = the whole
+    # record, one-minute blocks), a push against recomputing the window from scratch
+    if not args.no_stream:
+        ln = lanes[0]
+        K = 2 * max(w["lags"]) - 1
+        B = int(round(60 * w["fs"]))
+        n_fill = N // B
+        with torch.cuda.stream(ln["stream"]):
+            blocks = [ln["Y"][:, j * B:(j + 1) * B].contiguous() for j in range(n_fill)]
+            Yw = ln["Y"][:, :n_fill * B].contiguous()
+            cs = P.CovStream(ln["ctx"], l, K, n_fill * B, B, args.prec)
+            for j in range(n_fill):
+                cs.push(blocks[j])
+            n_t = 10
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            ev[0].record(ln["stream"])
+            for j in range(n_t):
+                cs.push(blocks[j])
+            ev[1].record(ln["stream"])
+            Rw, n_win = cs.covariances()
+            ev[2].record(ln["stream"])
+            for _ in range(3):
+                P.ssi_covariances(ln["ctx"], Yw, K, args.prec)
+            ev[3].record(ln["stream"])
+            ln["stream"].synchronize()
+            cs.close()
+        if rank == 0:
+            push_ms = ev[0].elapsed_time(ev[1]) / n_t
+            full_ms = ev[2].elapsed_time(ev[3]) / 3
+            out["cov_stream"] = {"push_ms": push_ms, "window_recompute_ms": full_ms,
+                                 "speedup": full_ms / push_ms, "block_samples": B,
+                                 "window_samples": int(n_win), "max_lag": K, "pushes_timed": n_t,
+                                 "api": "ssi_cov_stream_push against ssi_covariances of the "
+                                        "window (CUDA events on the stream)"}
 
     # the plain FP32 path of the same pipeline on the same GPU, measured the same way
     if not args.no_fp32 and args.prec == "split_bf16":

@@ -105,6 +105,33 @@ ssi_status ssi_covariances(ssi_ctx* ctx, const float* Y, int l, int64_t N, int m
                            ssi_precision prec, double* R, void* stream);
 
 /* ------------------------------------------------------------------------------
+ * Sliding-window covariances for continuous monitoring (Sec. 3.2.2 identifies a
+ * continuously recorded bridge window after window; Sec. 1 cites sliding-window SSI).
+ * The object holds the last `window` samples of an l-channel stream and the
+ * unnormalised lag sums S_k over the pairs inside them.  A push of B samples adds the
+ * pairs that enter and, once the window is full, removes the B oldest samples' pairs,
+ * each as the difference of two segment covariances of about B + max_lag samples
+ * (cost O(l^2 (B + max_lag) max_lag) instead of O(l^2 window max_lag)).
+ * ssi_cov_stream_covariances writes R_k = S_k / (n - k), k = 1..max_lag, for the n
+ * samples in the window, in the layout of ssi_covariances.
+ * create   window > max_lag, 1 <= max_block; l and precision as ssi_covariances.
+ *          Allocates l x (window + max_block) floats of ring, the sums and a segment
+ *          buffer from the context's budget.
+ * push     Y: device, l x B channel-major, B <= max_block; the first push needs
+ *          B > max_lag.  Asynchronous on `stream`; Y may be reused once the stream
+ *          has passed the call.
+ * covariances  R: device, max_lag x l x l; *n_samples (host, optional): n.
+ * Pushes and reads of one object must be ordered (one stream, or synchronised).
+ * ---------------------------------------------------------------------------- */
+typedef struct ssi_cov_stream ssi_cov_stream;
+ssi_status ssi_cov_stream_create(ssi_ctx* ctx, int l, int max_lag, int64_t window,
+                                 int64_t max_block, ssi_precision prec, ssi_cov_stream** out);
+ssi_status ssi_cov_stream_push(ssi_cov_stream* st, const float* Y, int64_t B, void* stream);
+ssi_status ssi_cov_stream_covariances(ssi_cov_stream* st, double* R, int64_t* n_samples,
+                                      void* stream);
+ssi_status ssi_cov_stream_destroy(ssi_cov_stream* st);
+
+/* ------------------------------------------------------------------------------
  * Covariances without device allocation (no counterpart in the paper: an
  * interface for callers that cannot allocate device memory when they need the
  * covariances, e.g. code inside a CUDA-graph capture that must not add allocation

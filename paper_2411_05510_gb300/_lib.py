@@ -81,6 +81,11 @@ PROTOTYPES = {
     "ssi_profile_read": (_c.c_int, [_P, _c.POINTER(_c.c_double), _c.POINTER(_c.c_int64), _c.c_int,
                                     _c.POINTER(_c.c_int64)]),
     "ssi_covariances": (_c.c_int, [_P, _P, _c.c_int, _c.c_int64, _c.c_int, _c.c_int, _P, _P]),
+    "ssi_cov_stream_create": (_c.c_int, [_P, _c.c_int, _c.c_int, _c.c_int64, _c.c_int64, _c.c_int,
+                                         _c.POINTER(_P)]),
+    "ssi_cov_stream_push": (_c.c_int, [_P, _P, _c.c_int64, _P]),
+    "ssi_cov_stream_covariances": (_c.c_int, [_P, _P, _c.POINTER(_c.c_int64), _P]),
+    "ssi_cov_stream_destroy": (_c.c_int, [_P]),
     "ssi_covariances_noalloc": (_c.c_int, [_P, _c.c_int, _c.c_int64, _c.c_int, _P, _P]),
     "ssi_gaussian_omega": (_c.c_int, [_P, _c.c_int, _c.c_int, _c.c_uint64, _P, _P]),
     "ssi_toeplitz_rsvd": (_c.c_int, [_P, _P, _c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.c_int,

@@ -21,7 +21,7 @@ __all__ = [
     "ssi_realize_batch", "ssi_stabilize", "ssi_solve", "ssi_pole_slots", "poles_to_numpy",
     "stab_params", "job_desc", "ssi_rank_rule", "ssi_lag_rule", "ssi_time_lag", "check_sync",
     "ssi_job_sizes", "ssi_serve_config", "ssi_submit", "ssi_poll", "ssi_release",
-    "cluster_params", "ssi_cluster",
+    "cluster_params", "ssi_cluster", "CovStream",
 ]
 
 PREC = {"fp32": SSI_PREC_FP32, "split_bf16": SSI_PREC_SPLIT_BF16}
@@ -154,6 +154,39 @@ def ssi_stabilize(ctx: Context, n_lags: int, orders: Sequence[int], l: int, pole
                             ctypes.c_void_p(poles.data_ptr()), ctypes.c_void_p(phi.data_ptr()),
                             ctypes.byref(params), _stream(poles.device)), "ssi_stabilize")
     return poles
+
+
+class CovStream:
+    """Sliding-window covariances (ssi_cov_stream_*): push channel-major blocks, read R of
+    the last `window` samples."""
+
+    def __init__(self, ctx: Context, l: int, max_lag: int, window: int, max_block: int,
+                 prec="split_bf16"):
+        self.ptr = ctypes.c_void_p()
+        self.l, self.max_lag = l, max_lag
+        self._ctx = ctx
+        check(lib.ssi_cov_stream_create(ctx.ptr, l, max_lag, window, max_block, _prec(prec),
+                                        ctypes.byref(self.ptr)), "ssi_cov_stream_create")
+
+    def push(self, Y: torch.Tensor) -> None:
+        _need(Y, torch.float32, "Y")
+        check(lib.ssi_cov_stream_push(self.ptr, ctypes.c_void_p(Y.data_ptr()), Y.shape[1],
+                                      _stream(Y.device)), "ssi_cov_stream_push")
+
+    def covariances(self, R: torch.Tensor | None = None):
+        """(R as a (max_lag, l, l) float64 device tensor, samples in the window)."""
+        if R is None:
+            R = torch.empty((self.max_lag, self.l, self.l), dtype=torch.float64, device="cuda")
+        n = ctypes.c_int64()
+        check(lib.ssi_cov_stream_covariances(self.ptr, ctypes.c_void_p(R.data_ptr()),
+                                              ctypes.byref(n), _stream(R.device)),
+              "ssi_cov_stream_covariances")
+        return R, n.value
+
+    def close(self) -> None:
+        if self.ptr:
+            check(lib.ssi_cov_stream_destroy(self.ptr), "ssi_cov_stream_destroy")
+            self.ptr = ctypes.c_void_p()
 
 
 def cluster_params(tau=0.05, min_size=10, fcm_max_iter=500, fcm_m=2.0,
