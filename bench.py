@@ -607,6 +607,7 @@ def main():
         prm = P.cluster_params(tau=0.05, min_size=10 if len(w["lags"]) == 1 else 50)
         n_cl = max(5, min(args.steps, 20))
         tc = []
+        torch.cuda.nvtx.range_push("cluster")
         with torch.cuda.stream(ln["stream"]):
             for _ in range(3):
                 P.ssi_cluster(ln["ctx"], len(w["lags"]), w["orders"], l, ln["poles"], ln["phi"], prm)
@@ -619,6 +620,7 @@ def main():
                 tc.append((time.perf_counter() - t0) * 1e3)
             st_ms, _, cl_launches = ln["ctx"].profile_read()
             ln["ctx"].profile(False)
+        torch.cuda.nvtx.range_pop()
         if rank == 0:
             found = sum(any(abs(m["f_hz"] - f0) / f0 < 1e-2 for m in modes) for f0 in f_true)
             out["cluster"] = {"ms_per_call": pct(tc, 50), "device_ms_per_call": st_ms["cluster"] / n_cl,
@@ -637,6 +639,7 @@ def main():
         K = 2 * max(w["lags"]) - 1
         B = int(round(60 * w["fs"]))
         n_fill = N // B
+        torch.cuda.nvtx.range_push("cov_stream")
         with torch.cuda.stream(ln["stream"]):
             blocks = [ln["Y"][:, j * B:(j + 1) * B].contiguous() for j in range(n_fill)]
             Yw = ln["Y"][:, :n_fill * B].contiguous()
@@ -656,6 +659,7 @@ def main():
             ev[3].record(ln["stream"])
             ln["stream"].synchronize()
             cs.close()
+        torch.cuda.nvtx.range_pop()
         if rank == 0:
             push_ms = ev[0].elapsed_time(ev[1]) / n_t
             full_ms = ev[2].elapsed_time(ev[3]) / 3

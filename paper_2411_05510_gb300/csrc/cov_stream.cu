@@ -6,11 +6,11 @@
 // after every new block costs O(l^2 W K); this object keeps the unnormalised lag sums
 //     S_k = sum over pairs (t, t+k) inside the window of y_{t+k} y_t^T
 // and updates them with the pairs that enter and leave, at O(l^2 (B + K) K) per block of
-// B samples.  Both updates are differences of two whole-segment covariance computations
-// (the stage (a) kernels, unchanged):
+// B samples.  Both updates are differences of two whole-segment lag sums, which the stage
+// (a) kernels add straight into S (their reduction's accumulate mode):
 //   entering pairs, t + k in [e, e+B):   F([e-T, e+B)) - F([e-T, e))
 //   leaving pairs,  t in [s, s+D):       F([s, s+D+T)) - F([s+D, s+D+T))
-// where F(seg) = sum over pairs inside seg = (len - k) R_k(seg), e / s are the window's
+// where F(seg) = sum over the pairs inside seg, e / s are the window's
 // end / start and T = K + 1 >= K (every pair with one end in the block has its other end
 // within K samples).  R_k of the window is S_k / (n - k).
 //
@@ -28,28 +28,13 @@ struct ssi_cov_stream {
   float* ring = nullptr;      // l x C
   float* seg = nullptr;       // l x (Bmax + K + 1)
   double* S = nullptr;        // K x l x l
-  double* F = nullptr;        // 2 x K x l x l
   int64_t start = 0, n = 0;   // absolute index of the window's first sample; samples held
-  size_t bytes_ring = 0, bytes_seg = 0, bytes_S = 0, bytes_F = 0;
+  size_t bytes_ring = 0, bytes_seg = 0, bytes_S = 0;
   ssi::Workspace ws;
 };
 
 namespace ssi {
 namespace {
-
-// S (+)= sign * (F1 (len1 - k) - F2 (len2 - k)); F2 may be null; set: S is overwritten.
-__global__ void k_stream_update(double* __restrict__ S, const double* __restrict__ F1,
-                                const double* __restrict__ F2, long long per_lag, int K,
-                                long long len1, long long len2, double sign, int set) {
-  const long long total = per_lag * K;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const long long k = e / per_lag + 1;
-    double v = F1[e] * (double)(len1 - k);
-    if (F2) v -= F2[e] * (double)(len2 - k);
-    S[e] = set ? sign * v : S[e] + sign * v;
-  }
-}
 
 __global__ void k_stream_normalise(const double* __restrict__ S, long long per_lag, int K, long long n,
                                    double* __restrict__ R) {
@@ -76,32 +61,20 @@ ssi_status ring_gather(ssi_cov_stream* st, int64_t a, int64_t len, float* dst, c
   return SSI_OK;
 }
 
-// F of absolute samples [a, a + len) into Fout (K x l x l, normalised R of the segment).
-ssi_status segment_cov(ssi_cov_stream* st, int64_t a, int64_t len, double* Fout, cudaStream_t s) {
+// S += sign * F(absolute samples [a, a + len)).
+ssi_status segment_acc(ssi_cov_stream* st, int64_t a, int64_t len, double sign, cudaStream_t s) {
   SSI_TRY(ring_gather(st, a, len, st->seg, s));
   ssi_ctx* ctx = st->ctx;
   CovPlan plan = cov_plan(st->l, len, st->K, st->prec, ctx->num_sms);
   SSI_TRY(ws_reserve(ctx, st->ws, plan.ws_bytes, s));
   st->ws.reset();
-  return covariances_ws(ctx, st->ws, plan, st->seg, st->prec, Fout, ctx->dev_status, s);
-}
-
-ssi_status update(ssi_cov_stream* st, int64_t len1, int64_t len2, double sign, bool set,
-                  cudaStream_t s) {
-  const long long per_lag = (long long)st->l * st->l;
-  const double* F2 = len2 > 0 ? st->F + per_lag * st->K : nullptr;
-  const int blocks = (int)std::min<long long>(ceil_div(per_lag * st->K, 256), (long long)st->ctx->num_sms * 8);
-  count_launches(st->ctx, 1);
-  k_stream_update<<<blocks, 256, 0, s>>>(st->S, st->F, F2, per_lag, st->K, len1, len2, sign, set ? 1 : 0);
-  SSI_CUDA(cudaGetLastError());
-  return SSI_OK;
+  return covariances_ws(ctx, st->ws, plan, st->seg, st->prec, st->S, ctx->dev_status, s, sign);
 }
 
 void stream_free(ssi_cov_stream* st) {
   ctx_free(st->ctx, st->ring, st->bytes_ring);
   ctx_free(st->ctx, st->seg, st->bytes_seg);
   ctx_free(st->ctx, st->S, st->bytes_S);
-  ctx_free(st->ctx, st->F, st->bytes_F);
   if (st->ws.base) ctx_free(st->ctx, st->ws.base, st->ws.cap);
   delete st;
 }
@@ -133,11 +106,9 @@ extern "C" ssi_status ssi_cov_stream_create(ssi_ctx* ctx, int l, int max_lag, in
   st->bytes_ring = sizeof(float) * (size_t)l * st->C;
   st->bytes_seg = sizeof(float) * (size_t)l * (max_block + max_lag + 1 + max_lag + 1);
   st->bytes_S = sizeof(double) * (size_t)max_lag * l * l;
-  st->bytes_F = 2 * st->bytes_S;
   ssi_status rc = ctx_alloc(ctx, reinterpret_cast<void**>(&st->ring), st->bytes_ring);
   if (rc == SSI_OK) rc = ctx_alloc(ctx, reinterpret_cast<void**>(&st->seg), st->bytes_seg);
   if (rc == SSI_OK) rc = ctx_alloc(ctx, reinterpret_cast<void**>(&st->S), st->bytes_S);
-  if (rc == SSI_OK) rc = ctx_alloc(ctx, reinterpret_cast<void**>(&st->F), st->bytes_F);
   if (rc != SSI_OK) {
     stream_free(st);
     return rc;
@@ -167,25 +138,20 @@ extern "C" ssi_status ssi_cov_stream_push(ssi_cov_stream* st, const float* Y, in
                                cudaMemcpyDeviceToDevice, s));
     done += w;
   }
-  const long long per_lag = (long long)st->l * st->l;
-  double* F1 = st->F;
-  double* F2 = st->F + per_lag * st->K;
   if (st->n == 0) {
-    SSI_TRY(segment_cov(st, e, B, F1, s));
-    SSI_TRY(update(st, B, 0, 1.0, true, s));
+    SSI_CUDA(cudaMemsetAsync(st->S, 0, st->bytes_S, s));
+    SSI_TRY(segment_acc(st, e, B, 1.0, s));
   } else {
     // entering pairs: F([e-T, e+B)) - F([e-T, e)); n >= T since the first block
-    SSI_TRY(segment_cov(st, e - T, T + B, F1, s));
-    SSI_TRY(segment_cov(st, e - T, T, F2, s));
-    SSI_TRY(update(st, T + B, T, 1.0, false, s));
+    SSI_TRY(segment_acc(st, e - T, T + B, 1.0, s));
+    SSI_TRY(segment_acc(st, e - T, T, -1.0, s));
   }
   st->n += B;
   if (st->n > st->W) {
     // leaving pairs: F([s, s+D+T)) - F([s+D, s+D+T)); the window keeps W >= T samples
     const int64_t D = st->n - st->W;
-    SSI_TRY(segment_cov(st, st->start, D + T, F1, s));
-    SSI_TRY(segment_cov(st, st->start + D, T, F2, s));
-    SSI_TRY(update(st, D + T, T, -1.0, false, s));
+    SSI_TRY(segment_acc(st, st->start, D + T, -1.0, s));
+    SSI_TRY(segment_acc(st, st->start + D, T, 1.0, s));
     st->start += D;
     st->n = st->W;
   }

@@ -418,6 +418,34 @@ __global__ void k_reduce_partials(const float* __restrict__ partial, int n_split
   }
 }
 
+// Accumulating variant, R += acc_sign * (sum of the per-split partials), for callers that
+// add unnormalised lag sums over segments.  One block per (lag k, eight channels a), one
+// warp per a, lanes over b (no per-element index division); splits in the same order.
+__global__ void __launch_bounds__(256) k_accumulate_partials(const float* __restrict__ partial,
+                                                             int n_split, long long split_stride,
+                                                             int l, int l_pad, double acc_sign,
+                                                             double* __restrict__ R) {
+  const int k = blockIdx.y + 1;
+  const int a = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (a >= l) return;
+  const float* src = partial + ((long long)(k - 1) * l_pad + a) * l_pad;
+  double* dst = R + ((long long)(k - 1) * l + a) * l;
+  for (int b = lane; b < l; b += 32) {
+    float hi = 0.f, lo = 0.f;
+    int sp = 0;
+    for (; sp + 8 <= n_split; sp += 8) {
+      float x[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) x[u] = __ldcs(src + b + (long long)(sp + u) * split_stride);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) two_sum_acc(hi, lo, x[u]);
+    }
+    for (; sp < n_split; ++sp) two_sum_acc(hi, lo, __ldcs(src + b + (long long)sp * split_stride));
+    dst[b] += acc_sign * ((double)hi + (double)lo);
+  }
+}
+
 template <int NB>
 constexpr int tc_stages() {
   return (225 * 1024) / ((2 * A_ATOMS + 2 * NB) * ATOM_BYTES) > 4
@@ -485,7 +513,9 @@ CovPlan cov_plan(int l, int64_t N, int max_lag, ssi_precision prec, int num_sms)
 }
 
 ssi_status covariances_ws(ssi_ctx* ctx, Workspace& ws, const CovPlan& c, const float* Y,
-                          ssi_precision prec, double* R, int* dev_status, cudaStream_t stream) {
+                          ssi_precision prec, double* R, int* dev_status, cudaStream_t stream,
+                          double acc_sign) {
+  const dim3 red_grid((unsigned)ceil_div(c.l, 8), (unsigned)c.max_lag);
   ws.reset();
   const long long split_stride = (long long)c.max_lag * c.l_pad * c.l_pad;
   if (prec == SSI_PREC_SPLIT_BF16) {
@@ -537,8 +567,12 @@ ssi_status covariances_ws(ssi_ctx* ctx, Workspace& ws, const CovPlan& c, const f
     }
     {
       ProfScope ps(ctx, ST_LAG_REDUCE, stream);
-      k_reduce_partials<<<ctx->num_sms * 8, 256, 0, stream>>>(partial, c.n_split, split_stride, c.l,
-                                                              c.l_pad, c.max_lag, (int)c.N, R);
+      if (acc_sign == 0.0)
+        k_reduce_partials<<<ctx->num_sms * 8, 256, 0, stream>>>(partial, c.n_split, split_stride, c.l,
+                                                                c.l_pad, c.max_lag, (int)c.N, R);
+      else
+        k_accumulate_partials<<<red_grid, 256, 0, stream>>>(partial, c.n_split, split_stride, c.l,
+                                                            c.l_pad, acc_sign, R);
       SSI_CUDA(cudaGetLastError());
     }
     count_launches(ctx, 3);
@@ -555,8 +589,12 @@ ssi_status covariances_ws(ssi_ctx* ctx, Workspace& ws, const CovPlan& c, const f
     }
     {
       ProfScope ps(ctx, ST_LAG_REDUCE, stream);
-      k_reduce_partials<<<ctx->num_sms * 8, 256, 0, stream>>>(partial, c.n_split, split_stride, c.l,
-                                                              c.l_pad, c.max_lag, (int)c.N, R);
+      if (acc_sign == 0.0)
+        k_reduce_partials<<<ctx->num_sms * 8, 256, 0, stream>>>(partial, c.n_split, split_stride, c.l,
+                                                                c.l_pad, c.max_lag, (int)c.N, R);
+      else
+        k_accumulate_partials<<<red_grid, 256, 0, stream>>>(partial, c.n_split, split_stride, c.l,
+                                                            c.l_pad, acc_sign, R);
       SSI_CUDA(cudaGetLastError());
     }
     count_launches(ctx, 2);
