@@ -29,8 +29,9 @@
 //   k_features      one warp per slot: Stage I features of the candidates (two passes,
 //                   FP32 screening then FP64 among the screened neighbours)
 //   k_fcm           cooperative persistent kernel: candidate min/max, the C-means
-//                   iterations with a fixed-order reduction over fixed slot chunks (bit-
-//                   identical for any grid size), memberships, the ordered list of kept poles
+//                   iterations with a fixed-order reduction over fixed 128-slot chunks
+//                   (bit-identical for any grid size), memberships, the ordered list of
+//                   kept poles
 //   k_prelink       join each kept pole to its Stage I nearest neighbour when that one is
 //                   kept and within tau (an exact Stage II link found for free)
 //   k_compress      point every kept pole at its root
@@ -56,10 +57,12 @@ namespace {
 
 constexpr int CL_THREADS = 256;
 constexpr int CL_WARPS = CL_THREADS / 32;
-constexpr int FCM_CH = 512;            // slots per C-means chunk (fixes the reduction order)
+constexpr int FCM_THREADS = 128;       // C-means CTA: one slot of its chunk per thread
+constexpr int FCM_WARPS = FCM_THREADS / 32;
+constexpr int FCM_CH = 128;            // slots per C-means chunk (fixes the reduction order)
 constexpr int FCM_NV = 13;             // per chunk: sum w0 x (5), sum w0, sum w1 x (5), sum w1, max |du|
 constexpr int FCM_STRIDE = 16;
-constexpr int FCM_RED_PER = 16;        // threads per value of the cross-chunk reduction
+constexpr int FCM_RED_PER = 8;         // threads per value of the cross-chunk reduction
 constexpr uint64_t CL_BAR_NS = 2000000000ull;
 constexpr int UNION_LIMIT = 1 << 20;
 constexpr int SCAN_THREADS = 1024;
@@ -331,7 +334,7 @@ __device__ __forceinline__ double red_apply(int op, double a, double b) {
 
 // Block-wide reduction of NV values (op[k] per value) in a fixed order: a shuffle tree
 // within each warp, then the warps in order.  The result is in out[0..NV) (shared).
-template <int NV>
+template <int NV, int NW = CL_WARPS>
 __device__ void block_reduce(double (&v)[NV], const int (&op)[NV], double* sh, double* out) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
@@ -347,7 +350,7 @@ __device__ void block_reduce(double (&v)[NV], const int (&op)[NV], double* sh, d
   if (threadIdx.x < NV) {
     const int k = threadIdx.x;
     double a = sh[k];
-    for (int ww = 1; ww < CL_WARPS; ++ww) a = red_apply(op[k], a, sh[ww * NV + k]);
+    for (int ww = 1; ww < NW; ++ww) a = red_apply(op[k], a, sh[ww * NV + k]);
     out[k] = a;
   }
   __syncthreads();
@@ -355,14 +358,14 @@ __device__ void block_reduce(double (&v)[NV], const int (&op)[NV], double* sh, d
 
 __device__ __forceinline__ double fcm_pow(double r, double e) { return e == 2.0 ? r * r : pow(r, e); }
 
-__global__ void __launch_bounds__(CL_THREADS, 1) k_fcm(FcmParams p) {
-  __shared__ double sh[CL_WARPS * FCM_STRIDE];
+__global__ void __launch_bounds__(FCM_THREADS) k_fcm(FcmParams p) {
+  __shared__ double sh[FCM_WARPS * FCM_STRIDE];
   __shared__ double sred[FCM_NV * FCM_RED_PER];
   __shared__ double sres[FCM_STRIDE];
   __shared__ double sV[2][5];
   __shared__ double sdelta;
   __shared__ int sdone;
-  __shared__ int sw[CL_WARPS + 1];
+  __shared__ int sw[FCM_WARPS + 1];
   unsigned nbar = 0;
   const int tid = threadIdx.x;
   const int lane = tid & 31, wid = tid >> 5;
@@ -378,8 +381,8 @@ __global__ void __launch_bounds__(CL_THREADS, 1) k_fcm(FcmParams p) {
       v[5 + d] = -inf; op[5 + d] = RED_MAX;
     }
     v[10] = 0.0; op[10] = RED_SUM;
-    for (int r = 0; r < FCM_CH / CL_THREADS; ++r) {
-      const long long e = (long long)c * FCM_CH + r * CL_THREADS + tid;
+    for (int r = 0; r < FCM_CH / FCM_THREADS; ++r) {
+      const long long e = (long long)c * FCM_CH + r * FCM_THREADS + tid;
       if (e < p.n && p.cand[e]) {
         v[10] += 1.0;
 #pragma unroll
@@ -390,7 +393,7 @@ __global__ void __launch_bounds__(CL_THREADS, 1) k_fcm(FcmParams p) {
         }
       }
     }
-    block_reduce<11>(v, op, sh, sres);
+    block_reduce<11, FCM_WARPS>(v, op, sh, sres);
     if (tid < 11) p.mm[(size_t)c * FCM_STRIDE + tid] = sres[tid];
   }
   if (!fcm_grid_sync(p, nbar)) return;
@@ -415,7 +418,7 @@ __global__ void __launch_bounds__(CL_THREADS, 1) k_fcm(FcmParams p) {
       p.hdr->converged = 1;
       p.hdr->phys = 0;
     }
-    for (long long e = (long long)blockIdx.x * CL_THREADS + tid; e < p.n; e += (long long)gridDim.x * CL_THREADS) {
+    for (long long e = (long long)blockIdx.x * FCM_THREADS + tid; e < p.n; e += (long long)gridDim.x * FCM_THREADS) {
       if (p.membership) p.membership[e] = -1.0;
       if (p.label_out) p.label_out[e] = -1;
     }
@@ -433,8 +436,8 @@ __global__ void __launch_bounds__(CL_THREADS, 1) k_fcm(FcmParams p) {
 #pragma unroll
       for (int k = 0; k < FCM_NV; ++k) { v[k] = 0.0; op[k] = RED_SUM; }
       op[FCM_NV - 1] = RED_MAX;
-      for (int r = 0; r < FCM_CH / CL_THREADS; ++r) {
-        const long long e = (long long)c * FCM_CH + r * CL_THREADS + tid;
+      for (int r = 0; r < FCM_CH / FCM_THREADS; ++r) {
+        const long long e = (long long)c * FCM_CH + r * FCM_THREADS + tid;
         if (e >= p.n || !p.cand[e]) continue;
         double x[5];
 #pragma unroll
@@ -477,7 +480,7 @@ __global__ void __launch_bounds__(CL_THREADS, 1) k_fcm(FcmParams p) {
         v[5] += w0;
         v[11] += w1;
       }
-      block_reduce<FCM_NV>(v, op, sh, sres);
+      block_reduce<FCM_NV, FCM_WARPS>(v, op, sh, sres);
       if (tid < FCM_NV) part[(size_t)c * FCM_STRIDE + tid] = sres[tid];
     }
     if (!fcm_grid_sync(p, nbar)) return;
@@ -535,8 +538,8 @@ __global__ void __launch_bounds__(CL_THREADS, 1) k_fcm(FcmParams p) {
   // kept poles: per-chunk counts, then the ordered list
   for (int c = blockIdx.x; c < p.n_chunks; c += gridDim.x) {
     int cnt = 0;
-    for (int r = 0; r < FCM_CH / CL_THREADS; ++r) {
-      const long long e = (long long)c * FCM_CH + r * CL_THREADS + tid;
+    for (int r = 0; r < FCM_CH / FCM_THREADS; ++r) {
+      const long long e = (long long)c * FCM_CH + r * FCM_THREADS + tid;
       if (e < p.n && p.cand[e] && p.u[e * 2 + phys] >= 0.5) ++cnt;
     }
     for (int o = 16; o; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
@@ -544,7 +547,7 @@ __global__ void __launch_bounds__(CL_THREADS, 1) k_fcm(FcmParams p) {
     __syncthreads();
     if (tid == 0) {
       int s = 0;
-      for (int w = 0; w < CL_WARPS; ++w) s += sw[w];
+      for (int w = 0; w < FCM_WARPS; ++w) s += sw[w];
       p.kcount[c] = s;
     }
     __syncthreads();
@@ -553,20 +556,20 @@ __global__ void __launch_bounds__(CL_THREADS, 1) k_fcm(FcmParams p) {
   for (int c = blockIdx.x; c < p.n_chunks; c += gridDim.x) {
     // kept poles of the chunks before this one (integer sum: any order)
     int before = 0;
-    for (int cc = tid; cc < c; cc += CL_THREADS) before += p.kcount[cc];
+    for (int cc = tid; cc < c; cc += FCM_THREADS) before += p.kcount[cc];
     for (int o = 16; o; o >>= 1) before += __shfl_xor_sync(0xffffffffu, before, o);
     if (lane == 0) sw[wid] = before;
     __syncthreads();
     if (tid == 0) {
       int s = 0;
-      for (int w = 0; w < CL_WARPS; ++w) s += sw[w];
-      sw[CL_WARPS] = s;
+      for (int w = 0; w < FCM_WARPS; ++w) s += sw[w];
+      sw[FCM_WARPS] = s;
     }
     __syncthreads();
-    int base = sw[CL_WARPS];
+    int base = sw[FCM_WARPS];
     __syncthreads();
-    for (int r = 0; r < FCM_CH / CL_THREADS; ++r) {
-      const long long e = (long long)c * FCM_CH + r * CL_THREADS + tid;
+    for (int r = 0; r < FCM_CH / FCM_THREADS; ++r) {
+      const long long e = (long long)c * FCM_CH + r * FCM_THREADS + tid;
       const bool in = e < p.n;
       const bool is_c = in && p.cand[e];
       const double P = is_c ? p.u[e * 2 + phys] : -1.0;
@@ -580,7 +583,7 @@ __global__ void __launch_bounds__(CL_THREADS, 1) k_fcm(FcmParams p) {
       int off = base;
       for (int w = 0; w < wid; ++w) off += sw[w];
       int tot = 0;
-      for (int w = 0; w < CL_WARPS; ++w) tot += sw[w];
+      for (int w = 0; w < FCM_WARPS; ++w) tot += sw[w];
       if (keep) {
         const int pos = off + __popc(bal & ((1u << lane) - 1u));
         p.kept_slot[pos] = (int)e;
@@ -1166,11 +1169,16 @@ ssi_status cluster_run(ssi_ctx* ctx, int n_lags, int n_orders, const int* orders
     fp.bar = bar;
     fp.abort_flag = reinterpret_cast<int*>(bar + 8);
     fp.status = ctx->dev_status;
+    // every chunk its own CTA where they fit at once (the cooperative launch needs all CTAs
+    // resident); solves sharing the device get their share of it
+    int occ = 0;
+    SSI_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fcm, FCM_THREADS, 0));
     const int inflight = std::max(1, ctx->inflight.load());
-    const int grid = std::max(1, std::min(n_chunks, std::max(1, ctx->num_sms / inflight)));
+    const int resident = std::max(1, ctx->num_sms * std::max(1, occ) / inflight);
+    const int grid = std::max(1, std::min(n_chunks, resident));
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(CL_THREADS);
+    cfg.blockDim = dim3(FCM_THREADS);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = stream;
     cudaLaunchAttribute attr[1];
