@@ -42,8 +42,10 @@
 //   k_modes_scan    one CTA: components in index order, those with >= min_size poles
 //   k_mode_members  one CTA per mode: its members in index order, mean f and xi
 //   k_medoid_prep   one warp per member: FP64 reciprocals of f, xi and |phi|^2
-//   k_medoid_sums   one warp per member: sum of distances to its mode (double-float
-//                   cross products, FP64 finish of 32 partners side by side)
+//   k_medoid_tiles  each pair of a mode once, in 32 x 32 tiles: distances with double-
+//                   float cross products and an FP64 finish of 32 partners side by side,
+//                   row and column sums per tile
+//   k_medoid_finish one thread per member: its sum over the tiles, in order
 //   k_medoid_pick   one CTA per mode: first minimum
 #include "common.cuh"
 #include "blackwell.cuh"
@@ -951,57 +953,106 @@ __device__ __forceinline__ void df_warp_allsum(float& hi, float& lo) {
   }
 }
 
-// One warp per member: the sum of its distances to the other members of its mode.  The
-// cross products a^H b are accumulated in double-float (FP32 pairs, ~1e-13 relative),
-// 32 partners at a time with lanes over channels; lane j keeps partner j's products and
-// the 32 distances are then finished in FP64 side by side (1/max(a, b) = min(1/a, 1/b)
-// from the FP64 reciprocals) and added by a fixed butterfly.
-__global__ void __launch_bounds__(CL_THREADS) k_medoid_sums(MedoidParams p) {
-  const int lane = threadIdx.x & 31;
-  const long long warp0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-  for (long long qa = warp0; qa < p.n_members; qa += nwarps) {
-    const int md = p.member_mode[qa];
-    const int b0 = p.mode_off[md], b1 = p.mode_off[md + 1];
-    const int ea = p.kept_slot[p.members[qa]];
-    const float2* pa = p.phi + (size_t)ea * p.l;
-    double sum = 0.0;
-    for (int qb0 = b0; qb0 < b1; qb0 += 32) {
-      const int cnt = min(32, b1 - qb0);
-      float kr_h = 0.f, kr_l = 0.f, ki_h = 0.f, ki_l = 0.f;
-      for (int jj = 0; jj < cnt; ++jj) {
-        if (qb0 + jj == qa) continue;                     // warp-uniform
-        const float2* pb = p.phi + (size_t)p.kept_slot[p.members[qb0 + jj]] * p.l;
-        float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
-        for (int c = lane; c < p.l; c += 32) {
-          const float2 x = pa[c], y = pb[c];
-          df_fma(rh, rl, x.x, y.x);
-          df_fma(rh, rl, x.y, y.y);
-          df_fma(ih, il, x.x, y.y);
-          df_fma(ih, il, -x.y, y.x);
-        }
-        df_warp_allsum(rh, rl);
-        df_warp_allsum(ih, il);
-        if (lane == jj) {
-          kr_h = rh; kr_l = rl; ki_h = ih; ki_l = il;
-        }
-      }
+// Each pair of a mode once.  A work item is a tile pair (ti <= tj) of 32 x 32 members of
+// one mode; warp w takes rows 4w..4w+3 of the tile, and for each row the 32 partners'
+// cross products (double-float, lanes over channels; lane j keeps partner j's), then the
+// 32 distances in FP64 side by side.  A row's sum over the tile goes to P[a][tj], a
+// column's sum over the tile (from shared memory, rows in order) to P[b][ti]; on a
+// diagonal tile, pairs a < b only, and member x gets its row and column sums together in
+// P[x][ti].  Every (member, tile) entry of P is written once, so sum[a] = sum over t of
+// P[a][t] in t order is deterministic.
+struct MedoidTiles {
+  const int4* items;        // (mode, ti, tj, 0)
+  int n_items;
+  const long long* pbase;   // per mode: first entry of its P block (members x tiles)
+  double* P;
+};
+
+__global__ void __launch_bounds__(CL_THREADS) k_medoid_tiles(MedoidParams p, MedoidTiles mt) {
+  __shared__ double s_col[32][33];
+  __shared__ double s_row[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int item = blockIdx.x; item < mt.n_items; item += gridDim.x) {
+    const int4 it = mt.items[item];
+    const int md = it.x, ti = it.y, tj = it.z;
+    const int b0 = p.mode_off[md], sm = p.mode_off[md + 1] - b0;
+    const int nt = (sm + 31) / 32;
+    const bool diag = ti == tj;
+    double* P = mt.P + mt.pbase[md];
+    __syncthreads();
+    for (int rr = 0; rr < 4; ++rr) {
+      const int r = wid * 4 + rr;
+      const int ra = ti * 32 + r;                  // member index within the mode
       double d = 0.0;
-      const int qb = qb0 + lane;
-      if (lane < cnt && qb != qa) {
-        const ssi_pole pola = p.poles[ea];
-        const ssi_pole polb = p.poles[p.kept_slot[p.members[qb]]];
-        const double dr = (double)kr_h + (double)kr_l, di = (double)ki_h + (double)ki_l;
-        const double s = fabs((double)pola.f_hz - (double)polb.f_hz) * fmin(p.inv[qa * 3], p.inv[qb * 3]) +
-                         fabs((double)pola.xi - (double)polb.xi) * fmin(p.inv[qa * 3 + 1], p.inv[qb * 3 + 1]);
-        const double mac = (dr * dr + di * di) * p.inv[qa * 3 + 2] * p.inv[qb * 3 + 2];
-        d = s + (1.0 - mac);
+      if (ra < sm) {                               // warp-uniform
+        const int qa = b0 + ra;
+        const int ea = p.kept_slot[p.members[qa]];
+        const float2* pa = p.phi + (size_t)ea * p.l;
+        float kr_h = 0.f, kr_l = 0.f, ki_h = 0.f, ki_l = 0.f;
+        for (int jj = 0; jj < 32; ++jj) {
+          const int cb = tj * 32 + jj;
+          if (cb >= sm || (diag && cb <= ra)) continue;   // warp-uniform
+          const float2* pb = p.phi + (size_t)p.kept_slot[p.members[b0 + cb]] * p.l;
+          float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+          for (int c = lane; c < p.l; c += 32) {
+            const float2 x = pa[c], y = pb[c];
+            df_fma(rh, rl, x.x, y.x);
+            df_fma(rh, rl, x.y, y.y);
+            df_fma(ih, il, x.x, y.y);
+            df_fma(ih, il, -x.y, y.x);
+          }
+          df_warp_allsum(rh, rl);
+          df_warp_allsum(ih, il);
+          if (lane == jj) {
+            kr_h = rh; kr_l = rl; ki_h = ih; ki_l = il;
+          }
+        }
+        const int cb = tj * 32 + lane;
+        if (cb < sm && !(diag && cb <= ra)) {
+          const int qb = b0 + cb;
+          const ssi_pole pola = p.poles[ea];
+          const ssi_pole polb = p.poles[p.kept_slot[p.members[qb]]];
+          const double dr = (double)kr_h + (double)kr_l, di = (double)ki_h + (double)ki_l;
+          const double sdist =
+              fabs((double)pola.f_hz - (double)polb.f_hz) * fmin(p.inv[qa * 3], p.inv[qb * 3]) +
+              fabs((double)pola.xi - (double)polb.xi) * fmin(p.inv[qa * 3 + 1], p.inv[qb * 3 + 1]);
+          const double mac = (dr * dr + di * di) * p.inv[qa * 3 + 2] * p.inv[qb * 3 + 2];
+          d = sdist + (1.0 - mac);
+        }
       }
+      s_col[r][lane] = d;
+      double rs = d;
 #pragma unroll
-      for (int o = 16; o; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-      sum += d;
+      for (int o = 16; o; o >>= 1) rs += __shfl_xor_sync(0xffffffffu, rs, o);
+      if (lane == 0) {
+        if (diag) s_row[r] = rs;
+        else if (ra < sm) P[(long long)ra * nt + tj] = rs;
+      }
     }
-    if (lane == 0) p.sum[qa] = sum;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      const int c = threadIdx.x;
+      const int cb = tj * 32 + c;
+      if (cb < sm) {
+        double cs = 0.0;
+        for (int r = 0; r < 32; ++r) cs += s_col[r][c];
+        P[(long long)cb * nt + ti] = diag ? s_row[c] + cs : cs;
+      }
+    }
+  }
+}
+
+// One thread per member: its sum over the tiles of its mode, in tile order.
+__global__ void k_medoid_finish(MedoidParams p, MedoidTiles mt) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < p.n_members;
+       q += (long long)gridDim.x * blockDim.x) {
+    const int md = p.member_mode[q];
+    const int b0 = p.mode_off[md], sm = p.mode_off[md + 1] - b0;
+    const int nt = (sm + 31) / 32;
+    const double* P = mt.P + mt.pbase[md] + (long long)(q - b0) * nt;
+    double sum = 0.0;
+    for (int t = 0; t < nt; ++t) sum += P[t];
+    p.sum[q] = sum;
   }
 }
 
@@ -1260,8 +1311,48 @@ ssi_status cluster_run(ssi_ctx* ctx, int n_lags, int n_orders, const int* orders
       count_launches(ctx, 1);
       k_medoid_prep<<<std::max(mblocks, 1), CL_THREADS, 0, stream>>>(mp);
       SSI_CUDA(cudaGetLastError());
-      k_medoid_sums<<<std::max(mblocks, 1), CL_THREADS, 0, stream>>>(mp);
+      // tile pairs of every mode, and each mode's block of per-(member, tile) partials
+      std::vector<int4> items;
+      std::vector<long long> pbase(n_modes);
+      long long ptot = 0;
+      for (int md = 0; md < n_modes; ++md) {
+        const int sm = off[md + 1] - off[md];
+        const int nt = (sm + 31) / 32;
+        pbase[md] = ptot;
+        ptot += (long long)sm * nt;
+        for (int ti = 0; ti < nt; ++ti)
+          for (int tj = ti; tj < nt; ++tj) items.push_back(make_int4(md, ti, tj, 0));
+      }
+      WsPlan tp;
+      tp.add<int4>(items.size());
+      tp.add<long long>((size_t)n_modes);
+      tp.add<double>((size_t)ptot);
+      SSI_TRY(ws_reserve(ctx, ctx->ws_aux, tp.bytes, stream));
+      ctx->ws_aux.reset();
+      MedoidTiles mt{};
+      int4* d_items = ctx->ws_aux.take<int4>(items.size());
+      long long* d_pbase = ctx->ws_aux.take<long long>((size_t)n_modes);
+      mt.P = ctx->ws_aux.take<double>((size_t)ptot);
+      if (!d_items || !d_pbase || !mt.P) {
+        set_error("ssi_cluster: medoid workspace too small");
+        return SSI_E_NOMEM;
+      }
+      SSI_CUDA(cudaMemcpyAsync(d_items, items.data(), sizeof(int4) * items.size(),
+                               cudaMemcpyHostToDevice, stream));
+      SSI_CUDA(cudaMemcpyAsync(d_pbase, pbase.data(), sizeof(long long) * n_modes,
+                               cudaMemcpyHostToDevice, stream));
+      mt.items = d_items;
+      mt.n_items = (int)items.size();
+      mt.pbase = d_pbase;
+      const int tblocks = (int)std::min<long long>((long long)items.size(), (long long)ctx->num_sms * 8);
+      count_launches(ctx, 1);
+      k_medoid_tiles<<<std::max(tblocks, 1), CL_THREADS, 0, stream>>>(mp, mt);
       SSI_CUDA(cudaGetLastError());
+      k_medoid_finish<<<(int)std::min<long long>(ceil_div(mp.n_members, 256), (long long)ctx->num_sms * 4),
+                        256, 0, stream>>>(mp, mt);
+      SSI_CUDA(cudaGetLastError());
+      // the host vectors above must outlive the copies
+      SSI_CUDA(cudaStreamSynchronize(stream));
       k_medoid_pick<<<n_modes, CL_THREADS, 0, stream>>>(mp);
       SSI_CUDA(cudaGetLastError());
       med.resize(n_modes);

@@ -91,6 +91,7 @@ struct ssi_ctx {
   size_t in_use = 0;
   std::mutex mem_mu;
   ssi::Workspace ws;        // workspace of the direct (non-serving) calls
+  ssi::Workspace ws_aux;    // second workspace of the direct calls (clustering's medoid tiles)
   int* dev_status = nullptr;  // device status word of the direct calls
   ssi::Serving* serving = nullptr;
   ssi::JobBuffers* solve = nullptr;  // buffers of ssi_solve

@@ -186,6 +186,7 @@ void ssi_destroy(ssi_ctx* ctx) {
   cudaDeviceSynchronize();
   solve_buffers_destroy(ctx);
   if (ctx->ws.base) ctx_free(ctx, ctx->ws.base, ctx->ws.cap);
+  if (ctx->ws_aux.base) ctx_free(ctx, ctx->ws_aux.base, ctx->ws_aux.cap);
   ctx_free(ctx, ctx->dev_status, 256);
   delete ctx;
 }
