@@ -226,3 +226,28 @@ def test_cluster_identifies_bridge_modes(P, ctx, name):
                                    P.cluster_params(tau=TAU, min_size=min_size))
     rec_phi = phi.cpu().numpy().reshape(-1, w["l"], 2)
     assert _identified(modes, rec_phi, f_true, phi_true) == w["modes"] == len(modes), (info, modes)
+
+
+@pytest.mark.slow
+def test_cluster_identifies_frame10_modes_from_the_3d_diagram(P, ctx):
+    """The 10-DOF frame of Sec. 3.1 (fs 200 Hz, 10 % noise, N = 60000): 3D diagram over ten
+    lags from 170 to 255, RSVD k = 512 with p = q = 0 (Algorithm 1), orders 2..30, then the
+    clustering.  Every generating mode is one mode within 0.5 % in frequency, 40 % in
+    damping (a 300 s record), and MAC >= 0.99 between the medoid's shape and the model's."""
+    w = S.workload("frame10", seed=100)
+    Y, f_true, xi_true, phi_true = S.record(w, np.float32)
+    lags = [int(x) for x in np.linspace(170, 255, 10).round()]
+    orders = list(range(2, 31, 2))
+    desc = P.job_desc(torch.from_numpy(Y).cuda(), w["fs"], lags, orders, k=512, oversample=0, q=0,
+                      prec="split_bf16", seed=0)
+    poles, phi, _ = P.ssi_solve(ctx, desc, with_s=False)
+    modes, info, _ = P.ssi_cluster(ctx, len(lags), orders, Y.shape[0], poles, phi,
+                                   P.cluster_params(tau=TAU, min_size=len(lags) * len(orders) // 4))
+    ph = phi.cpu().numpy().reshape(-1, Y.shape[0], 2)
+    assert len(modes) == len(f_true), (info, modes)
+    for r, f0 in enumerate(f_true):
+        m = min(modes, key=lambda m: abs(m["f_hz"] - f0))
+        v = ph[m["medoid_slot"]]
+        assert abs(m["f_hz"] - f0) / f0 < 5e-3, (r, m, f0)
+        assert abs(m["xi"] - xi_true[r]) / xi_true[r] < 0.4, (r, m, xi_true[r])
+        assert O.mac(v[:, 0] + 1j * v[:, 1], phi_true[:, r]) >= 0.99, r
