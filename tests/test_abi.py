@@ -68,3 +68,18 @@ def test_cluster_abi_layout_and_argument_checks():
     st = L.lib.ssi_cluster(None, 1, 2, orders, 4, None, None, ctypes.byref(params), None, 0,
                            ctypes.byref(n_modes), None, None, None, None, None)
     assert st == 1
+
+
+def test_cov_stream_argument_checks_without_a_device():
+    import ctypes
+
+    import paper_2411_05510_gb300 as P
+    L = P._lib
+    out = ctypes.c_void_p(1)
+    # a null context is refused before any device work, and the handle is cleared
+    assert L.lib.ssi_cov_stream_create(None, 4, 3, 100, 10, 1, ctypes.byref(out)) == 1
+    assert not out.value
+    assert L.lib.ssi_cov_stream_push(None, None, 10, None) == 1
+    n = ctypes.c_int64()
+    assert L.lib.ssi_cov_stream_covariances(None, None, ctypes.byref(n), None) == 1
+    assert L.lib.ssi_cov_stream_destroy(None) == 0
