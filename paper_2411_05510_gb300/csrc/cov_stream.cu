@@ -86,8 +86,8 @@ extern "C" ssi_status ssi_cov_stream_create(ssi_ctx* ctx, int l, int max_lag, in
                                             int64_t max_block, ssi_precision prec,
                                             ssi_cov_stream** out) {
   using namespace ssi;
+  if (out) *out = nullptr;
   SSI_CHECK(ctx && out, "ssi_cov_stream_create: null pointer");
-  *out = nullptr;
   SSI_CHECK(l >= 1 && l <= 1024, "ssi_cov_stream_create: l=%d out of range [1, 1024]", l);
   SSI_CHECK(max_lag >= 1, "ssi_cov_stream_create: need max_lag >= 1");
   SSI_CHECK(max_block >= 1 && window >= (int64_t)max_lag + 1,
