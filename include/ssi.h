@@ -153,7 +153,7 @@ ssi_status ssi_covariances_noalloc(const float* Y, int l, int64_t N, int max_lag
                                    void* stream);
 
 /* ------------------------------------------------------------------------------
- * Gaussian test matrix Omega of Sec. 2.2 (Eq. Y = A Omega, Algorithm 1, line 1).
+ * Gaussian test matrix Omega of Sec. 2.2 (Eq. Y = A Omega, Algorithm 1).
  * omega   device, float32, rows x cols row-major.  Entry (r, c) comes from the
  *         Philox4x32-10 counter (r, c, 0, 0) with key (seed & 0xffffffff,
  *         seed >> 32): outputs x0, x1 -> u = (x + 0.5)/2^32,

@@ -1,4 +1,4 @@
-// Small SVD of the RSVD (Sec. 2.2: "P = U~ Sigma V^T", Algorithm 1 line 5).
+// Small SVD of the RSVD (Sec. 2.2: P = U~ Sigma V^T, Algorithm 1).
 //
 // With P^T = Q2 R2 (QR of the K x L_cols matrix's transpose), the left singular
 // vectors of P are the right singular vectors of R2.  One-sided (Hestenes) Jacobi
