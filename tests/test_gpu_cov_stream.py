@@ -111,3 +111,35 @@ def test_stream_rejects_bad_calls(P, ctx, rec):
         assert n == 100
     finally:
         st.close()
+
+
+def test_monitoring_chain_from_the_stream(P, ctx, rec):
+    """Continuous monitoring: the window's covariances from the stream feed the stage calls
+    (Toeplitz RSVD per lag, realisations, stability) and the clustering.  The reduced bridge
+    record has 6 generating modes in 4-20 Hz; after the window (40000 samples) has slid by
+    20000, every mode must come out of the 3D diagram of lags 14, 18, 22 within 1 %."""
+    import ssi_synth as S2
+    w = S2.workload("bridge186_3d", l=24, modes=6, f_lo=4.0, N=60000, lags=[14, 18, 22], k=32,
+                    oversample=16, orders=list(range(2, 33, 2)))
+    _, f_true, *_ = S2.record(w, np.float32)
+    Yd = torch.from_numpy(rec).cuda()
+    l, K = rec.shape[0], 2 * max(w["lags"]) - 1
+    st = P.CovStream(ctx, l, K, 40000, 5000)
+    try:
+        for j in range(12):
+            st.push(Yd[:, j * 5000:(j + 1) * 5000].contiguous())
+        R, n = st.covariances()
+    finally:
+        st.close()
+    assert n == 40000
+    Us = []
+    for i in w["lags"]:
+        U, _ = P.ssi_toeplitz_rsvd(ctx, R, l, i, w["k"], w["oversample"], w["q"], seed=5)
+        Us.append(U)
+    poles, phi = P.ssi_realize_batch(ctx, w["lags"], Us, l, w["k"], w["orders"], 1.0 / w["fs"])
+    P.ssi_stabilize(ctx, len(w["lags"]), w["orders"], l, poles, phi)
+    modes, info, _ = P.ssi_cluster(ctx, len(w["lags"]), w["orders"], l, poles, phi,
+                                   P.cluster_params(min_size=10))
+    P.check_sync(ctx)
+    for f0 in f_true:
+        assert any(abs(m["f_hz"] - f0) / f0 < 1e-2 for m in modes), (f0, modes, info)
