@@ -184,9 +184,16 @@ class CovStream:
         return R, n.value
 
     def close(self) -> None:
+        """Free the stream's device memory (before its context is closed)."""
         if self.ptr:
             check(lib.ssi_cov_stream_destroy(self.ptr), "ssi_cov_stream_destroy")
             self.ptr = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc) -> None:
+        self.close()
 
 
 def cluster_params(tau=0.05, min_size=10, fcm_max_iter=500, fcm_m=2.0,
