@@ -678,12 +678,14 @@ __device__ __forceinline__ void tile_rc(long long t, int nb, int& bi, int& bj) {
 __global__ void __launch_bounds__(CL_THREADS) k_link(LinkParams p) {
   __shared__ int s_slot[2][32];
   __shared__ float s_f[2][32], s_x[2][32];
+  __shared__ int s_tile[2];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int nk = *p.n_kept;
   for (long long t = blockIdx.x; t < p.n_tiles; t += gridDim.x) {
-    int bi, bj;
-    tile_rc(t, p.nb, bi, bj);
+    // one thread maps the tile index (an FP64 square root) for the block
+    if (threadIdx.x == 0) tile_rc(t, p.nb, s_tile[0], s_tile[1]);
     __syncthreads();
+    const int bi = s_tile[0], bj = s_tile[1];
     if (threadIdx.x < 64) {
       const int side = threadIdx.x >> 5, k = threadIdx.x & 31;
       const int idx = (side ? bj : bi) * 32 + k;

@@ -123,11 +123,12 @@ struct CovPlan {
   size_t ws_bytes;
 };
 CovPlan cov_plan(int l, int64_t N, int max_lag, ssi_precision prec, int num_sms);
-// acc_sign == 0: R = covariances of Y; otherwise R += acc_sign * the unnormalised lag sums
-// sum_t y_{t+k} y_t^T (accumulation over segments)
+// acc == nullptr: R = covariances of Y; otherwise acc (double-float hi/lo pairs, same
+// layout as R) += acc_sign * the unnormalised lag sums sum_t y_{t+k} y_t^T and R is unused
+// (accumulation over segments)
 ssi_status covariances_ws(ssi_ctx* ctx, Workspace& ws, const CovPlan& plan, const float* Y,
                           ssi_precision prec, double* R, int* dev_status, cudaStream_t stream,
-                          double acc_sign = 0.0);
+                          float acc_sign = 0.f, float2* acc = nullptr);
 
 struct RsvdPlan {
   int l, l_pad, i, k, K, Kp, q, L, L_pad;

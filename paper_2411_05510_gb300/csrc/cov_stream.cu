@@ -7,7 +7,8 @@
 //     S_k = sum over pairs (t, t+k) inside the window of y_{t+k} y_t^T
 // and updates them with the pairs that enter and leave, at O(l^2 (B + K) K) per block of
 // B samples.  Both updates are differences of two whole-segment lag sums, which the stage
-// (a) kernels add straight into S (their reduction's accumulate mode):
+// (a) kernels add straight into S (their reduction's accumulate mode; S is double-float,
+// hi + lo FP32 pairs, ~2^-48 relative, so the per-element update needs no FP64):
 //   entering pairs, t + k in [e, e+B):   F([e-T, e+B)) - F([e-T, e))
 //   leaving pairs,  t in [s, s+D):       F([s, s+D+T)) - F([s+D, s+D+T))
 // where F(seg) = sum over the pairs inside seg, e / s are the window's
@@ -27,7 +28,7 @@ struct ssi_cov_stream {
   ssi_precision prec = SSI_PREC_SPLIT_BF16;
   float* ring = nullptr;      // l x C
   float* seg = nullptr;       // l x (Bmax + K + 1)
-  double* S = nullptr;        // K x l x l
+  float2* S = nullptr;        // K x l x l lag sums, double-float (hi, lo)
   int64_t start = 0, n = 0;   // absolute index of the window's first sample; samples held
   size_t bytes_ring = 0, bytes_seg = 0, bytes_S = 0;
   ssi::Workspace ws;
@@ -36,13 +37,21 @@ struct ssi_cov_stream {
 namespace ssi {
 namespace {
 
-__global__ void k_stream_normalise(const double* __restrict__ S, long long per_lag, int K, long long n,
-                                   double* __restrict__ R) {
-  const long long total = per_lag * K;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const long long k = e / per_lag + 1;
-    R[e] = S[e] / (double)(n - k);
+// R_k = S_k / (n - k): one block per (lag k, eight channels a), the reciprocal once per
+// block (FP64 divisions are slow here).
+__global__ void __launch_bounds__(256) k_stream_normalise(const float2* __restrict__ S, int l, long long n,
+                                                          double* __restrict__ R) {
+  __shared__ double s_inv;
+  const int k = blockIdx.y + 1;
+  const int a = blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) s_inv = 1.0 / (double)(n - k);
+  __syncthreads();
+  if (a >= l) return;
+  const long long row = ((long long)(k - 1) * l + a) * l;
+  for (int b = lane; b < l; b += 32) {
+    const float2 v = S[row + b];
+    R[row + b] = ((double)v.x + (double)v.y) * s_inv;
   }
 }
 
@@ -68,7 +77,8 @@ ssi_status segment_acc(ssi_cov_stream* st, int64_t a, int64_t len, double sign, 
   CovPlan plan = cov_plan(st->l, len, st->K, st->prec, ctx->num_sms);
   SSI_TRY(ws_reserve(ctx, st->ws, plan.ws_bytes, s));
   st->ws.reset();
-  return covariances_ws(ctx, st->ws, plan, st->seg, st->prec, st->S, ctx->dev_status, s, sign);
+  return covariances_ws(ctx, st->ws, plan, st->seg, st->prec, nullptr, ctx->dev_status, s,
+                        (float)sign, st->S);
 }
 
 void stream_free(ssi_cov_stream* st) {
@@ -105,7 +115,7 @@ extern "C" ssi_status ssi_cov_stream_create(ssi_ctx* ctx, int l, int max_lag, in
   st->prec = prec;
   st->bytes_ring = sizeof(float) * (size_t)l * st->C;
   st->bytes_seg = sizeof(float) * (size_t)l * (max_block + max_lag + 1 + max_lag + 1);
-  st->bytes_S = sizeof(double) * (size_t)max_lag * l * l;
+  st->bytes_S = sizeof(float2) * (size_t)max_lag * l * l;
   ssi_status rc = ctx_alloc(ctx, reinterpret_cast<void**>(&st->ring), st->bytes_ring);
   if (rc == SSI_OK) rc = ctx_alloc(ctx, reinterpret_cast<void**>(&st->seg), st->bytes_seg);
   if (rc == SSI_OK) rc = ctx_alloc(ctx, reinterpret_cast<void**>(&st->S), st->bytes_S);
@@ -164,11 +174,9 @@ extern "C" ssi_status ssi_cov_stream_covariances(ssi_cov_stream* st, double* R, 
   SSI_CHECK(st && R, "ssi_cov_stream_covariances: null pointer");
   SSI_CHECK(st->n > st->K, "ssi_cov_stream_covariances: the window holds no more than max_lag samples");
   SSI_CUDA(cudaSetDevice(st->ctx->device));
-  const long long per_lag = (long long)st->l * st->l;
-  const int blocks = (int)std::min<long long>(ceil_div(per_lag * st->K, 256), (long long)st->ctx->num_sms * 8);
   count_launches(st->ctx, 1);
-  k_stream_normalise<<<blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(st->S, per_lag, st->K,
-                                                                            st->n, R);
+  k_stream_normalise<<<dim3((unsigned)ceil_div(st->l, 8), (unsigned)st->K), 256, 0,
+                       static_cast<cudaStream_t>(stream)>>>(st->S, st->l, st->n, R);
   SSI_CUDA(cudaGetLastError());
   if (n_samples) *n_samples = st->n;
   return SSI_OK;

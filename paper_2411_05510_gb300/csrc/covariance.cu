@@ -418,19 +418,21 @@ __global__ void k_reduce_partials(const float* __restrict__ partial, int n_split
   }
 }
 
-// Accumulating variant, R += acc_sign * (sum of the per-split partials), for callers that
-// add unnormalised lag sums over segments.  One block per (lag k, eight channels a), one
+// Accumulating variant, S += acc_sign * (sum of the per-split partials), for callers that
+// add unnormalised lag sums over segments.  S is kept in double-float (hi, lo FP32 pairs,
+// ~2^-48 relative), so the update runs on the FP32 pipes: the split sum (hi, lo) is added
+// with Knuth's two-sum and renormalised.  One block per (lag k, eight channels a), one
 // warp per a, lanes over b (no per-element index division); splits in the same order.
 __global__ void __launch_bounds__(256) k_accumulate_partials(const float* __restrict__ partial,
                                                              int n_split, long long split_stride,
-                                                             int l, int l_pad, double acc_sign,
-                                                             double* __restrict__ R) {
+                                                             int l, int l_pad, float acc_sign,
+                                                             float2* __restrict__ S) {
   const int k = blockIdx.y + 1;
   const int a = blockIdx.x * 8 + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (a >= l) return;
   const float* src = partial + ((long long)(k - 1) * l_pad + a) * l_pad;
-  double* dst = R + ((long long)(k - 1) * l + a) * l;
+  float2* dst = S + ((long long)(k - 1) * l + a) * l;
   for (int b = lane; b < l; b += 32) {
     float hi = 0.f, lo = 0.f;
     int sp = 0;
@@ -442,7 +444,17 @@ __global__ void __launch_bounds__(256) k_accumulate_partials(const float* __rest
       for (int u = 0; u < 8; ++u) two_sum_acc(hi, lo, x[u]);
     }
     for (; sp < n_split; ++sp) two_sum_acc(hi, lo, __ldcs(src + b + (long long)sp * split_stride));
-    dst[b] += acc_sign * ((double)hi + (double)lo);
+    if (acc_sign < 0.f) {
+      hi = -hi;
+      lo = -lo;
+    }
+    const float2 v = dst[b];
+    const float s = __fadd_rn(v.x, hi);
+    const float bb = __fsub_rn(s, v.x);
+    const float err = __fadd_rn(__fsub_rn(v.x, __fsub_rn(s, bb)), __fsub_rn(hi, bb));
+    const float t = __fadd_rn(__fadd_rn(v.y, lo), err);
+    const float h2 = __fadd_rn(s, t);
+    dst[b] = make_float2(h2, __fsub_rn(t, __fsub_rn(h2, s)));
   }
 }
 
@@ -514,7 +526,7 @@ CovPlan cov_plan(int l, int64_t N, int max_lag, ssi_precision prec, int num_sms)
 
 ssi_status covariances_ws(ssi_ctx* ctx, Workspace& ws, const CovPlan& c, const float* Y,
                           ssi_precision prec, double* R, int* dev_status, cudaStream_t stream,
-                          double acc_sign) {
+                          float acc_sign, float2* acc) {
   const dim3 red_grid((unsigned)ceil_div(c.l, 8), (unsigned)c.max_lag);
   ws.reset();
   const long long split_stride = (long long)c.max_lag * c.l_pad * c.l_pad;
@@ -567,12 +579,12 @@ ssi_status covariances_ws(ssi_ctx* ctx, Workspace& ws, const CovPlan& c, const f
     }
     {
       ProfScope ps(ctx, ST_LAG_REDUCE, stream);
-      if (acc_sign == 0.0)
+      if (!acc)
         k_reduce_partials<<<ctx->num_sms * 8, 256, 0, stream>>>(partial, c.n_split, split_stride, c.l,
                                                                 c.l_pad, c.max_lag, (int)c.N, R);
       else
         k_accumulate_partials<<<red_grid, 256, 0, stream>>>(partial, c.n_split, split_stride, c.l,
-                                                            c.l_pad, acc_sign, R);
+                                                            c.l_pad, acc_sign, acc);
       SSI_CUDA(cudaGetLastError());
     }
     count_launches(ctx, 3);
@@ -589,12 +601,12 @@ ssi_status covariances_ws(ssi_ctx* ctx, Workspace& ws, const CovPlan& c, const f
     }
     {
       ProfScope ps(ctx, ST_LAG_REDUCE, stream);
-      if (acc_sign == 0.0)
+      if (!acc)
         k_reduce_partials<<<ctx->num_sms * 8, 256, 0, stream>>>(partial, c.n_split, split_stride, c.l,
                                                                 c.l_pad, c.max_lag, (int)c.N, R);
       else
         k_accumulate_partials<<<red_grid, 256, 0, stream>>>(partial, c.n_split, split_stride, c.l,
-                                                            c.l_pad, acc_sign, R);
+                                                            c.l_pad, acc_sign, acc);
       SSI_CUDA(cudaGetLastError());
     }
     count_launches(ctx, 2);
