@@ -39,7 +39,9 @@ again in the design notes):
     nearest in d_f + d_xi + (1 - MAC), then 1 - MPC and MPD of the pole.
   * Fuzzy C-means with two clusters and fuzzifier 2, started from the feature-wise
     minimum and maximum.  The cluster whose centroid is nearer the origin is the
-    possibly physical one; poles with membership >= 0.5 in it are kept.
+    possibly physical one; poles with membership >= 0.5 in it are kept.  A cluster whose
+    memberships are all zero (every pole on the other centroid, e.g. a single pole)
+    keeps its centroid instead of the undefined 0/0 update.
   * Stage II: single linkage in d_f + d_xi + (1 - MAC), cut at a distance tau;
     clusters of at least min_size poles are modes (mean f and xi, medoid pole).
 """
@@ -490,7 +492,8 @@ def fuzzy_c_means(X, m: float = 2.0, tol: float = 1e-10, max_iter: int = 500):
         v_c  = sum_k u_ck^m x_k / sum_k u_ck^m,
     from v_1 = the feature-wise minimum and v_2 = the feature-wise maximum of X, until
     the largest change of a membership is below tol.  A point on a centroid belongs to it
-    alone.  Returns U (n, 2), V (2, d) and the number of iterations."""
+    alone; a cluster whose memberships are all zero keeps its centroid.  Returns U (n, 2),
+    V (2, d) and the number of iterations."""
     X = np.asarray(X, dtype=np.float64)
     n = X.shape[0]
     V = np.stack([X.min(axis=0), X.max(axis=0)])
@@ -508,7 +511,9 @@ def fuzzy_c_means(X, m: float = 2.0, tol: float = 1e-10, max_iter: int = 500):
                 for c in range(2):
                     Un[k, c] = 1.0 / sum((D[k, c] / D[k, j]) ** (2.0 / (m - 1.0)) for j in range(2))
         Wm = Un ** m
-        V = (Wm.T @ X) / Wm.sum(axis=0)[:, None]
+        W = Wm.sum(axis=0)
+        # a cluster whose memberships are all zero keeps its centroid (the update is 0/0)
+        V = np.where((W > 0)[:, None], (Wm.T @ X) / np.where(W > 0, W, 1.0)[:, None], V)
         delta = np.abs(Un - U).max() if n else 0.0
         U = Un
         if delta < tol:

@@ -511,8 +511,9 @@ __global__ void __launch_bounds__(FCM_THREADS) k_fcm(FcmParams p) {
       }
       __syncthreads();
       if (tid < 10) {
+        // a cluster whose memberships are all zero keeps its centroid (the update is 0/0)
         const int cc = tid / 5, d = tid % 5;
-        sV[cc][d] = sres[cc * 6 + d] / sres[cc * 6 + 5];
+        if (sres[cc * 6 + 5] > 0.0) sV[cc][d] = sres[cc * 6 + d] / sres[cc * 6 + 5];
       }
       if (tid == 0) {
         sdelta = sres[FCM_NV - 1];

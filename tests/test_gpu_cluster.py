@@ -258,3 +258,34 @@ def test_cluster_identifies_frame10_modes_from_the_3d_diagram(P, ctx):
         m = max(near, key=lambda m: mac_of(m, r))
         assert mac_of(m, r) >= 0.99, (r, m)
         assert abs(m["xi"] - xi_true[r]) / xi_true[r] < 0.4, (r, m, xi_true[r])
+
+
+def test_cluster_single_stable_pole(P, ctx, diag3):
+    """One stable pole in the whole diagram (the stability bits of all others cleared): it is
+    the only Stage I candidate, C-means puts it on the first centroid (the second cluster,
+    without weight, keeps its start centroid), it is kept, and with min_size 1 it is a mode
+    of its own and its own medoid; the oracle agrees."""
+    w, poles, phi, *_ = diag3
+    rec = P.poles_to_numpy(poles)
+    stable = np.nonzero((rec["flags"] & 48) != 0)[0]
+    one = int(stable[len(stable) // 2])
+    raw = poles.cpu().numpy().copy()
+    words = raw.view(np.uint32).reshape(len(raw), 10)    # flags are word 8 of a record
+    keep_bits = words[one, 8]
+    words[:, 8] &= ~np.uint32(48)
+    words[one, 8] = keep_bits
+    p1 = torch.from_numpy(raw).cuda()
+    modes, info, pp = P.ssi_cluster(ctx, len(w["lags"]), w["orders"], w["l"], p1, phi,
+                                    P.cluster_params(min_size=1), per_pole=True)
+    assert info["n_candidates"] == 1 and info["n_kept"] == 1 and info["n_modes"] == 1, info
+    assert info["fcm_converged"] == 1 and info["physical"] == 0
+    assert np.all(np.isfinite(info["centroids"]))
+    assert modes[0]["medoid_slot"] == one and modes[0]["size"] == 1
+    assert modes[0]["f_hz"] == float(rec["f_hz"][one])
+    memb = pp["membership"].cpu().numpy()
+    lab = pp["label"].cpu().numpy()
+    assert memb[one] == 1.0 and np.count_nonzero(memb >= 0) == 1
+    assert lab[one] == one and np.count_nonzero(lab >= 0) == 1
+    cells = _fp64_cells(P.poles_to_numpy(p1), phi.cpu().numpy(), w)
+    omodes, keep, _, idx = O.cluster_modes(cells, tau=TAU, min_size=1)
+    assert len(idx) == 1 and keep.all() and len(omodes) == 1

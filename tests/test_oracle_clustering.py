@@ -165,3 +165,20 @@ def test_pin_catches_a_wrong_fcm_exponent(monkeypatch):
     monkeypatch.setattr(O, "fuzzy_c_means", fcm_wrong)
     with pytest.raises(AssertionError):
         test_fcm_fixed_point_minimises_the_objective()
+
+
+def test_fcm_cluster_without_weight_keeps_its_centroid():
+    """Reading: a C-means cluster whose memberships are all zero keeps its centroid (the
+    update would be 0/0).  One pole, or two equal poles (their mean is exact), sit on the
+    first centroid: they belong to it alone, the second keeps the start value, and nothing
+    becomes NaN; the poles are kept (the physical cluster is the first of two equally near
+    centroids)."""
+    import warnings
+    for X in (np.array([[0.01, 0.02, 0.001, 0.05, 0.1]]),
+              np.repeat([[0.01, 0.02, 0.001, 0.05, 0.1]], 2, axis=0)):
+        with warnings.catch_warnings():
+            warnings.simplefilter("error")
+            U, V, it = O.fuzzy_c_means(X)
+            keep, P, V2, phys, _ = O.stage1(X)
+        assert np.all(U == [1.0, 0.0]) and np.all(V == X[0]) and it == 2
+        assert phys == 0 and np.all(keep) and np.all(P == 1.0)
