@@ -47,6 +47,7 @@
 //                   row and column sums per tile
 //   k_medoid_finish one thread per member: its sum over the tiles, in order
 //   k_medoid_pick   one CTA per mode: first minimum
+//   k_relabel       (per-slot labels asked for) the slot of each kept pole's component root
 #include "common.cuh"
 #include "blackwell.cuh"
 
