@@ -121,6 +121,9 @@ ssi_status ssi_covariances(ssi_ctx* ctx, const float* Y, int l, int64_t N, int m
  *          B > max_lag.  Asynchronous on `stream`; Y may be reused once the stream
  *          has passed the call.
  * covariances  R: device, max_lag x l x l; *n_samples (host, optional): n.
+ *          SSI_E_INVALID while the window holds no more than max_lag samples.
+ * destroy  synchronises the device, then frees the object's memory; call it before
+ *          ssi_destroy of its context.
  * Pushes and reads of one object must be ordered (one stream, or synchronised).
  * ---------------------------------------------------------------------------- */
 typedef struct ssi_cov_stream ssi_cov_stream;
