@@ -52,3 +52,28 @@ def test_medoid_tiles_cover_every_pair_once(s):
     P, writes = _tiled_sums(D)
     assert np.all(writes == 1)
     assert np.allclose(P.sum(axis=1), D.sum(axis=1), rtol=1e-13, atol=1e-13)
+
+
+def _tile_rc(t, nb):
+    """The pairwise-link kernel's map from a linear tile index to the tile pair (bi <= bj):
+    row bi holds tiles bi..nb-1 and starts at bi*nb - bi*(bi-1)/2; an FP64 square-root
+    estimate of the row, then corrected by whole steps."""
+    B = 2.0 * nb + 1.0
+    r = int((B - np.sqrt(max(B * B - 8.0 * t, 0.0))) * 0.5)
+    r = max(0, min(r, nb - 1))
+    start = lambda b: b * nb - b * (b - 1) // 2
+    while r > 0 and start(r) > t:
+        r -= 1
+    while r + 1 < nb and start(r + 1) <= t:
+        r += 1
+    return r, r + (t - start(r))
+
+
+@pytest.mark.parametrize("nb", [1, 2, 3, 7, 32, 101, 416, 2000])
+def test_link_tile_map_covers_each_pair_once(nb):
+    seen = set()
+    for t in range(nb * (nb + 1) // 2):
+        bi, bj = _tile_rc(t, nb)
+        assert 0 <= bi <= bj < nb
+        seen.add((bi, bj))
+    assert len(seen) == nb * (nb + 1) // 2
