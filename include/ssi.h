@@ -51,6 +51,16 @@ typedef enum {
                               hi*hi + hi*lo + lo*hi accumulated in FP32 */
 } ssi_precision;
 
+/* Arithmetic of the small dense problems of every lag: the K x K SVD of the range
+ * finder (Sec. 2.2), the least squares for A and eig(A) (Sec. 2.1).  The sketch and QR
+ * passes of the range finder are FP32 in both modes. */
+typedef enum {
+  SSI_SMALL_FP32 = 0,      /* FP32 with FP64 reductions (the fast mode) */
+  SSI_SMALL_FP64 = 1       /* FP64 throughout: FP64 one-sided Jacobi (stops at 1e-13
+                              relative off-orthogonality), U = Q U~ in FP64, FP64 Gram,
+                              Cholesky and A~_n, FP64 Hessenberg + double-shift QR */
+} ssi_small_precision;
+
 typedef struct ssi_ctx ssi_ctx;
 
 /* Context bound to CUDA device `device`.  hbm_budget_bytes caps the device memory
@@ -115,15 +125,24 @@ ssi_status ssi_covariances(ssi_ctx* ctx, const float* Y, int l, int64_t N, int m
  * ssi_cov_stream_covariances writes R_k = S_k / (n - k), k = 1..max_lag, for the n
  * samples in the window, in the layout of ssi_covariances.
  * create   window > max_lag, 1 <= max_block; l and precision as ssi_covariances.
- *          Allocates l x (window + max_block) floats of ring, the sums and a segment
- *          buffer from the context's budget.
+ *          Allocates l x (window + max_block) floats of ring, the sums, a segment
+ *          buffer and the stage (a) workspace from the context's budget.
  * push     Y: device, l x B channel-major, B <= max_block; the first push needs
  *          B > max_lag.  Asynchronous on `stream`; Y may be reused once the stream
  *          has passed the call.
  * covariances  R: device, max_lag x l x l; *n_samples (host, optional): n.
  *          SSI_E_INVALID while the window holds no more than max_lag samples.
+ * refresh  rebuilds the sums from the samples held in the ring (one whole-window
+ *          computation).  The updates add and subtract segment sums whose rounding does
+ *          not cancel; push rebuilds by itself after every `window` samples pushed, so
+ *          the error stays within that of a few whole-window computations however long
+ *          the stream runs.
  * destroy  synchronises the device, then frees the object's memory; call it before
  *          ssi_destroy of its context.
+ * The workspace of the largest segment and of a whole window is reserved at creation,
+ * so push and refresh never allocate.  A push or refresh that fails part way (a CUDA
+ * error) marks the object inconsistent: later calls other than destroy return
+ * SSI_E_INVALID.
  * Pushes and reads of one object must be ordered (one stream, or synchronised).
  * ---------------------------------------------------------------------------- */
 typedef struct ssi_cov_stream ssi_cov_stream;
@@ -132,6 +151,7 @@ ssi_status ssi_cov_stream_create(ssi_ctx* ctx, int l, int max_lag, int64_t windo
 ssi_status ssi_cov_stream_push(ssi_cov_stream* st, const float* Y, int64_t B, void* stream);
 ssi_status ssi_cov_stream_covariances(ssi_cov_stream* st, double* R, int64_t* n_samples,
                                       void* stream);
+ssi_status ssi_cov_stream_refresh(ssi_cov_stream* st, void* stream);
 ssi_status ssi_cov_stream_destroy(ssi_cov_stream* st);
 
 /* ------------------------------------------------------------------------------
@@ -147,8 +167,10 @@ ssi_status ssi_cov_stream_destroy(ssi_cov_stream* st);
  * process exits.
  * Limits: max_lag * roundup(l, 64)^2 <= 4 Mi floats (SSI_E_INVALID beyond, with a
  * message), plus the limits of ssi_covariances.
- * The first call on a device looks up the array's device address (a runtime query
- * that may not be captured), so make it before any stream capture on that device.
+ * Every call looks up the array's device address on the current device (a host-side
+ * runtime query; the address is not cached, so it stays valid across cudaDeviceReset).
+ * The first call on a device also loads the library's device code there, so make it
+ * before any stream capture on that device.
  * Every call shares the one array: calls whose work overlaps on the GPU (different
  * streams, or several host threads) race and must be serialised by the caller.
  * ---------------------------------------------------------------------------- */
@@ -175,13 +197,18 @@ ssi_status ssi_gaussian_omega(ssi_ctx* ctx, int rows, int cols, uint64_t seed, f
  *   (U~, S) = svd(P);                          U = Q U~[:, :k].
  * R       device, float64, (2i-1) x l x l as produced by ssi_covariances (more
  *         lags may be present; only R_1..R_{2i-1} are read).
- * U       device, float32, L x k row-major, L = l*i (left singular vectors).
- * S       device, float32, k singular values, descending.
- * Limits: i >= 2, 1 <= k, k + oversample <= min(L, 512), l <= 1024.
+ * small   arithmetic of the K x K SVD and of U = Q U~ (SSI_SMALL_FP32: FP32 Jacobi,
+ *         stopping at 1e-5 relative off-orthogonality; SSI_SMALL_FP64: FP64 Jacobi,
+ *         1e-13).  The Jacobi sweeps run on a cooperative grid (parallel block
+ *         ordering), so they take several SMs for as long as they run.
+ * U       device, float64, L x k row-major, L = l*i (left singular vectors).
+ * S       device, float64, k singular values, descending.
+ * Limits: i >= 2, 1 <= k, k + oversample <= min(L, 16384), l <= 1024.  (K = L with
+ *         q = 0 makes Q span the whole column space: U and S are then the SVD of T.)
  * ---------------------------------------------------------------------------- */
 ssi_status ssi_toeplitz_rsvd(ssi_ctx* ctx, const double* R, int l, int i, int k, int oversample,
-                             int q, uint64_t seed, ssi_precision prec, float* U, float* S,
-                             void* stream);
+                             int q, uint64_t seed, ssi_precision prec, ssi_small_precision small,
+                             double* U, double* S, void* stream);
 
 /* ------------------------------------------------------------------------------
  * Stage (c): realisation for every (lag, order) of a stabilization diagram,
@@ -193,11 +220,16 @@ ssi_status ssi_toeplitz_rsvd(ssi_ctx* ctx, const double* R, int l, int i, int k,
  * give no pole.
  *
  * lags     host, n_lags block counts i_t (each >= 2), n_lags <= 64.
- * U        host array of n_lags device pointers; U[t] is (l*lags[t]) x k float32.
+ * U        host array of n_lags device pointers; U[t] is (l*lags[t]) x k float64, row-
+ *          major (as written by ssi_toeplitz_rsvd).
+ * small    SSI_SMALL_FP32: U is rounded to FP32 and the Gram matrices, Cholesky factor,
+ *          A~_n and eig run in FP32 (FP64 chunk sums); SSI_SMALL_FP64: all of them in
+ *          FP64.  Pole records are written in FP32 either way (f, xi and mu are rounded
+ *          once, about 6e-8 relative).
  * orders   host, n_orders even model orders, ascending, 2 <= order <= min(k, 512),
- *          n_orders <= 512; k <= 512.  Orders up to 224 keep A in shared memory;
- *          larger ones run the same kernel with A in the realisation's global
- *          scratch (slower: every access goes to L2).
+ *          n_orders <= 512; k <= 512.  Orders up to 224 (FP32) or 160 (FP64) keep A
+ *          in shared memory; larger ones run the same kernel with A in the
+ *          realisation's global scratch (slower: every access goes to L2).
  * poles    device, ssi_pole_slots(n_orders, orders) * n_lags records.  Slot
  *          (t, m, j) = t*slots_per_lag + sum_{m'<m} orders[m']/2 + j; the poles of
  *          one realisation come first, ascending in frequency; unused slots have
@@ -230,9 +262,9 @@ typedef struct {
 /* Number of pole slots of one lag: sum over orders of order/2. */
 int64_t ssi_pole_slots(int n_orders, const int* orders);
 
-ssi_status ssi_realize_batch(ssi_ctx* ctx, int n_lags, const int* lags, const float* const* U,
+ssi_status ssi_realize_batch(ssi_ctx* ctx, int n_lags, const int* lags, const double* const* U,
                              int l, int k, const int* orders, int n_orders, double dt,
-                             ssi_pole* poles, float* phi, void* stream);
+                             ssi_small_precision small, ssi_pole* poles, float* phi, void* stream);
 
 /* ------------------------------------------------------------------------------
  * Stage (d): hard criteria and the soft criteria of Eq. (stabcriteria3D).
@@ -337,18 +369,21 @@ typedef struct {
   int32_t n_orders;
   const int32_t* orders;   /* host, ascending, even */
   int32_t k, oversample, q;
-  int32_t prec;            /* ssi_precision */
+  int32_t prec;            /* ssi_precision of the lag and sketch GEMMs */
   uint64_t seed;
   ssi_stab_params stab;
+  int32_t small;           /* ssi_small_precision of the K x K SVD, A and eig(A) */
+  int32_t reserved;
 } ssi_job_desc;
 
 /* Output sizes of a job: total pole slots and the matching phi length (floats). */
 ssi_status ssi_job_sizes(const ssi_job_desc* job, int64_t* n_slots, int64_t* phi_floats);
 
-/* poles/phi: device buffers of ssi_job_sizes() size.  S_out (optional, device):
- * n_lags x k singular values. */
+/* poles/phi: device buffers of ssi_job_sizes() size.  S_out (optional, device, float64):
+ * n_lags x k singular values.  Limits: k <= 512, k + oversample <= 16384, orders <= 512.
+ * A range finder wider than the orders need is k = max order, oversample = K - k. */
 ssi_status ssi_solve(ssi_ctx* ctx, const ssi_job_desc* job, ssi_pole* poles, float* phi,
-                     float* S_out, void* stream);
+                     double* S_out, void* stream);
 
 /* Synchronise `stream` and report device-side status raised by earlier asynchronous
  * calls of this context on it (SSI_E_TIMEOUT for a bounded wait that ran out,

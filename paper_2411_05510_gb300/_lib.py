@@ -16,6 +16,7 @@ SSI_OK, SSI_E_INVALID, SSI_E_NOMEM, SSI_E_CUDA, SSI_E_TIMEOUT, SSI_E_NOTCONVERGE
 STATUS_NAMES = ["SSI_OK", "SSI_E_INVALID", "SSI_E_NOMEM", "SSI_E_CUDA", "SSI_E_TIMEOUT",
                 "SSI_E_NOTCONVERGED", "SSI_E_BUSY", "SSI_E_NOTFOUND"]
 SSI_PREC_FP32, SSI_PREC_SPLIT_BF16 = 0, 1
+SSI_SMALL_FP32, SSI_SMALL_FP64 = 0, 1
 
 POLE_HC_XI, POLE_HC_MPC, POLE_HC_MPD, POLE_HC, POLE_ORDER, POLE_LAG, POLE_VALID, POLE_NOTCONV = \
     1, 2, 4, 8, 16, 32, 64, 128
@@ -64,7 +65,8 @@ class SsiJobDesc(ctypes.Structure):
                 ("lags", ctypes.POINTER(ctypes.c_int32)), ("n_orders", ctypes.c_int32),
                 ("orders", ctypes.POINTER(ctypes.c_int32)), ("k", ctypes.c_int32),
                 ("oversample", ctypes.c_int32), ("q", ctypes.c_int32), ("prec", ctypes.c_int32),
-                ("seed", ctypes.c_uint64), ("stab", SsiStabParams)]
+                ("seed", ctypes.c_uint64), ("stab", SsiStabParams), ("small", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 _c = ctypes
@@ -85,15 +87,16 @@ PROTOTYPES = {
                                          _c.POINTER(_P)]),
     "ssi_cov_stream_push": (_c.c_int, [_P, _P, _c.c_int64, _P]),
     "ssi_cov_stream_covariances": (_c.c_int, [_P, _P, _c.POINTER(_c.c_int64), _P]),
+    "ssi_cov_stream_refresh": (_c.c_int, [_P, _P]),
     "ssi_cov_stream_destroy": (_c.c_int, [_P]),
     "ssi_covariances_noalloc": (_c.c_int, [_P, _c.c_int, _c.c_int64, _c.c_int, _P, _P]),
     "ssi_gaussian_omega": (_c.c_int, [_P, _c.c_int, _c.c_int, _c.c_uint64, _P, _P]),
     "ssi_toeplitz_rsvd": (_c.c_int, [_P, _P, _c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.c_int,
-                                     _c.c_uint64, _c.c_int, _P, _P, _P]),
+                                     _c.c_uint64, _c.c_int, _c.c_int, _P, _P, _P]),
     "ssi_pole_slots": (_c.c_int64, [_c.c_int, _c.POINTER(_c.c_int)]),
     "ssi_realize_batch": (_c.c_int, [_P, _c.c_int, _c.POINTER(_c.c_int), _c.POINTER(_P), _c.c_int,
-                                     _c.c_int, _c.POINTER(_c.c_int), _c.c_int, _c.c_double, _P, _P,
-                                     _P]),
+                                     _c.c_int, _c.POINTER(_c.c_int), _c.c_int, _c.c_double, _c.c_int,
+                                     _P, _P, _P]),
     "ssi_stabilize": (_c.c_int, [_P, _c.c_int, _c.c_int, _c.POINTER(_c.c_int), _c.c_int, _P, _P,
                                  _c.POINTER(SsiStabParams), _P]),
     "ssi_cluster": (_c.c_int, [_P, _c.c_int, _c.c_int, _c.POINTER(_c.c_int), _c.c_int, _P, _P,

@@ -13,8 +13,8 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import (SSI_PREC_FP32, SSI_PREC_SPLIT_BF16, SsiClusterInfo, SsiClusterParams, SsiJobDesc,
-                   SsiMode, SsiStabParams, check, lib)
+from ._lib import (SSI_PREC_FP32, SSI_PREC_SPLIT_BF16, SSI_SMALL_FP32, SSI_SMALL_FP64, SsiClusterInfo,
+                   SsiClusterParams, SsiJobDesc, SsiMode, SsiStabParams, check, lib)
 
 __all__ = [
     "Context", "PREC", "ssi_covariances", "ssi_gaussian_omega", "ssi_toeplitz_rsvd",
@@ -25,10 +25,15 @@ __all__ = [
 ]
 
 PREC = {"fp32": SSI_PREC_FP32, "split_bf16": SSI_PREC_SPLIT_BF16}
+SMALL = {"fp32": SSI_SMALL_FP32, "fp64": SSI_SMALL_FP64}
 
 
 def _prec(p) -> int:
     return PREC[p] if isinstance(p, str) else int(p)
+
+
+def _small(p) -> int:
+    return SMALL[p] if isinstance(p, str) else int(p)
 
 
 def _stream(device=None) -> ctypes.c_void_p:
@@ -105,13 +110,14 @@ def ssi_gaussian_omega(ctx: Context, rows: int, cols: int, seed: int, device="cu
 
 
 def ssi_toeplitz_rsvd(ctx: Context, R: torch.Tensor, l: int, i: int, k: int, oversample: int = 0,
-                      q: int = 0, seed: int = 0, prec="split_bf16"):
-    """(U, S): U (l*i x k float32), S (k float32) of the block-Toeplitz T_{1|i} built from R."""
+                      q: int = 0, seed: int = 0, prec="split_bf16", small="fp32"):
+    """(U, S): U (l*i x k float64), S (k float64) of the block-Toeplitz T_{1|i} built from R;
+    `small` is the arithmetic of the K x K SVD ("fp32" or "fp64")."""
     _need(R, torch.float64, "R")
-    U = torch.empty((l * i, k), dtype=torch.float32, device=R.device)
-    S = torch.empty((k,), dtype=torch.float32, device=R.device)
+    U = torch.empty((l * i, k), dtype=torch.float64, device=R.device)
+    S = torch.empty((k,), dtype=torch.float64, device=R.device)
     check(lib.ssi_toeplitz_rsvd(ctx.ptr, ctypes.c_void_p(R.data_ptr()), l, i, k, oversample, q, seed,
-                                _prec(prec), ctypes.c_void_p(U.data_ptr()),
+                                _prec(prec), _small(small), ctypes.c_void_p(U.data_ptr()),
                                 ctypes.c_void_p(S.data_ptr()), _stream(R.device)),
           "ssi_toeplitz_rsvd")
     return U, S
@@ -127,17 +133,18 @@ def ssi_pole_slots(orders: Sequence[int]) -> int:
 
 
 def ssi_realize_batch(ctx: Context, lags: Sequence[int], Us: Sequence[torch.Tensor], l: int, k: int,
-                      orders: Sequence[int], dt: float):
-    """Pole records (uint8 tensor, n_lags*slots x 40 bytes) and phi (float32, slots x l x 2)."""
+                      orders: Sequence[int], dt: float, small="fp32"):
+    """Pole records (uint8 tensor, n_lags*slots x 40 bytes) and phi (float32, slots x l x 2)
+    from float64 U (l*i x k) per lag; `small` is the arithmetic of A and eig(A)."""
     slots = ssi_pole_slots(orders) * len(lags)
     dev = Us[0].device
     poles = torch.zeros((slots, _lib.POLE_BYTES), dtype=torch.uint8, device=dev)
     phi = torch.zeros((slots, l, 2), dtype=torch.float32, device=dev)
     for U in Us:
-        _need(U, torch.float32, "U")
+        _need(U, torch.float64, "U")
     uptrs = (ctypes.c_void_p * len(Us))(*[U.data_ptr() for U in Us])
     check(lib.ssi_realize_batch(ctx.ptr, len(lags), _int_array(lags), uptrs, l, k, _int_array(orders),
-                                len(orders), dt, ctypes.c_void_p(poles.data_ptr()),
+                                len(orders), dt, _small(small), ctypes.c_void_p(poles.data_ptr()),
                                 ctypes.c_void_p(phi.data_ptr()), _stream(dev)), "ssi_realize_batch")
     return poles, phi
 
@@ -182,6 +189,10 @@ class CovStream:
                                               ctypes.byref(n), _stream(R.device)),
               "ssi_cov_stream_covariances")
         return R, n.value
+
+    def refresh(self) -> None:
+        """Rebuild the window's lag sums from the samples held (ssi_cov_stream_refresh)."""
+        check(lib.ssi_cov_stream_refresh(self.ptr, _stream()), "ssi_cov_stream_refresh")
 
     def close(self) -> None:
         """Free the stream's device memory (before its context is closed)."""
@@ -232,7 +243,8 @@ def ssi_cluster(ctx: Context, n_lags: int, orders: Sequence[int], l: int, poles:
 
 
 def job_desc(Y, fs: float, lags: Sequence[int], orders: Sequence[int], k: int, oversample: int = 0,
-             q: int = 0, prec="split_bf16", seed: int = 0, stab: SsiStabParams | None = None):
+             q: int = 0, prec="split_bf16", seed: int = 0, stab: SsiStabParams | None = None,
+             small="fp32"):
     """An ssi_job_desc for a device tensor or a (pinned) host tensor / numpy array Y (l x N)."""
     keep = []
     if isinstance(Y, torch.Tensor):
@@ -248,7 +260,8 @@ def job_desc(Y, fs: float, lags: Sequence[int], orders: Sequence[int], k: int, o
     ord_arr = (ctypes.c_int32 * len(orders))(*orders)
     keep += [lag_arr, ord_arr]
     d = SsiJobDesc(ptr, on_host, l, N, fs, len(lags), lag_arr, len(orders), ord_arr, k, oversample,
-                   q, _prec(prec), seed, stab or stab_params(use_lag_axis=len(lags) > 1))
+                   q, _prec(prec), seed, stab or stab_params(use_lag_axis=len(lags) > 1),
+                   _small(small), 0)
     d._keep = keep
     return d
 
@@ -265,11 +278,11 @@ def ssi_job_sizes(desc: SsiJobDesc):
 
 
 def ssi_solve(ctx: Context, desc: SsiJobDesc, device="cuda", with_s: bool = True):
-    """Full solve; returns (poles uint8 tensor, phi float32 tensor, S float32 tensor or None)."""
+    """Full solve; returns (poles uint8 tensor, phi float32 tensor, S float64 tensor or None)."""
     n_slots, phi_floats = ssi_job_sizes(desc)
     poles = torch.zeros((n_slots, _lib.POLE_BYTES), dtype=torch.uint8, device=device)
     phi = torch.zeros((phi_floats,), dtype=torch.float32, device=device)
-    S = torch.zeros((desc.n_lags, desc.k), dtype=torch.float32, device=device) if with_s else None
+    S = torch.zeros((desc.n_lags, desc.k), dtype=torch.float64, device=device) if with_s else None
     check(lib.ssi_solve(ctx.ptr, ctypes.byref(desc), ctypes.c_void_p(poles.data_ptr()),
                         ctypes.c_void_p(phi.data_ptr()),
                         ctypes.c_void_p(S.data_ptr() if S is not None else 0),

@@ -119,10 +119,13 @@ ssi_status check_dev_status(int* dev_status, cudaStream_t stream);
 struct CovPlan {
   int l, l_pad, max_lag, n_nt, nb;    // channel padding, N tiles of the tensor-core kernel
   int64_t N, n_rows;
+  int64_t ldy;                        // floats between channels of Y (N unless a caller sets it)
   int rows_per_split, n_split;
   size_t ws_bytes;
 };
-CovPlan cov_plan(int l, int64_t N, int max_lag, ssi_precision prec, int num_sms);
+// max_ws: largest workspace the plan may need (the time split is coarsened to fit)
+CovPlan cov_plan(int l, int64_t N, int max_lag, ssi_precision prec, int num_sms,
+                 size_t max_ws = SIZE_MAX);
 // acc == nullptr: R = covariances of Y; otherwise acc (double-float hi/lo pairs, same
 // layout as R) += acc_sign * the unnormalised lag sums sum_t y_{t+k} y_t^T and R is unused
 // (accumulation over segments)
@@ -137,9 +140,13 @@ struct RsvdPlan {
 RsvdPlan rsvd_plan(int l, int i, int k, int oversample, int q, int num_sms);
 // shared_device: other work (another lag of the same solve) runs beside this one, so the
 // QR takes the half-device grid
+// small64: FP64 Jacobi and U = Q U~ in FP64 (U, S double); otherwise FP32, written as
+// double when out64 (U, S float otherwise)
 ssi_status toeplitz_rsvd_ws(ssi_ctx* ctx, Workspace& ws, const RsvdPlan& plan, const double* R,
-                            uint64_t seed, ssi_precision prec, float* U, float* S,
-                            int* dev_status, cudaStream_t stream, bool shared_device);
+                            uint64_t seed, ssi_precision prec, bool small64, void* U, void* S,
+                            bool out64, int* dev_status, cudaStream_t stream, bool shared_device);
+ssi_status convert_f2d(const float* x, long long n, double* y, cudaStream_t stream);
+ssi_status convert_d2f(const double* x, long long n, float* y, cudaStream_t stream);
 
 struct RealizePlan {
   int n_lags, l, k, n_orders, max_order;
@@ -151,6 +158,14 @@ RealizePlan realize_plan(int n_lags, const int* lags, int l, int k, const int* o
 ssi_status realize_ws(ssi_ctx* ctx, Workspace& ws, const RealizePlan& plan, const int* lags,
                       const float* const* U, const int* orders, double dt, ssi_pole* poles,
                       float* phi, int* dev_status, cudaStream_t stream);
+
+// FP64 small problems (csrc/eig64.cu): U per lag is (l*i) x k FP64
+size_t realize64_ws_bytes(int n_lags, const int* lags, int l, int k, const int* orders, int n_orders);
+ssi_status realize64_ws(ssi_ctx* ctx, Workspace& ws, int n_lags, const int* lags, int l, int k,
+                        const double* const* U, const int* orders, int n_orders, int64_t slots_per_lag,
+                        double dt, ssi_pole* poles, float* phi, int* dev_status, cudaStream_t stream);
+ssi_status lag_factor64_launch(const double* GH, int k, int n_lags, double* RM, double* Fs, int* status,
+                               cudaStream_t stream);
 
 ssi_status stabilize_ws(ssi_ctx* ctx, Workspace& ws, int n_lags, int n_orders, const int* orders,
                         int l, ssi_pole* poles, const float* phi, const ssi_stab_params* p,

@@ -15,8 +15,18 @@
 // end / start and T = K + 1 >= K (every pair with one end in the block has its other end
 // within K samples).  R_k of the window is S_k / (n - k).
 //
-// Samples live in a device ring of W + B_max columns per channel; segments are gathered
-// into a contiguous buffer by 2D copies.
+// Samples live in a device ring of W + B_max columns per channel.  A segment that lies in
+// one piece of the ring is read in place (the stage (a) kernels take a channel stride);
+// one that wraps is gathered into a contiguous buffer by 2D copies.
+//
+// Rounding: each update adds and subtracts segment sums whose rounding errors do not
+// cancel, so the error of S would grow with the number of updates.  Every W samples
+// pushed (and on ssi_cov_stream_refresh) S is therefore rebuilt from the window held in
+// the ring, which resets it to the error of one whole-window computation.
+//
+// The workspace is reserved at creation for the largest segment and for a whole window,
+// so a push or a rebuild never grows it; a push that fails part way (a CUDA error) leaves
+// the object marked inconsistent, and every later call but destroy is refused.
 #include "common.cuh"
 
 #include <algorithm>
@@ -27,9 +37,12 @@ struct ssi_cov_stream {
   int64_t W = 0, Bmax = 0, C = 0;
   ssi_precision prec = SSI_PREC_SPLIT_BF16;
   float* ring = nullptr;      // l x C
-  float* seg = nullptr;       // l x (Bmax + K + 1)
+  float* seg = nullptr;       // l x seg_cap, seg_cap = Bmax + 2 (K + 1)
   float2* S = nullptr;        // K x l x l lag sums, double-float (hi, lo)
   int64_t start = 0, n = 0;   // absolute index of the window's first sample; samples held
+  int64_t since_rebuild = 0;  // samples pushed since S was last rebuilt from the ring
+  int64_t seg_cap = 0;        // columns of the gather buffer
+  bool broken = false;        // a push or rebuild failed part way: S no longer matches the window
   size_t bytes_ring = 0, bytes_seg = 0, bytes_S = 0;
   ssi::Workspace ws;
 };
@@ -70,15 +83,55 @@ ssi_status ring_gather(ssi_cov_stream* st, int64_t a, int64_t len, float* dst, c
   return SSI_OK;
 }
 
-// S += sign * F(absolute samples [a, a + len)).
-ssi_status segment_acc(ssi_cov_stream* st, int64_t a, int64_t len, double sign, cudaStream_t s) {
-  SSI_TRY(ring_gather(st, a, len, st->seg, s));
+// S += sign * F(Y), Y an l x len record with channel stride ldy (len > max_lag).
+ssi_status lag_sums_acc(ssi_cov_stream* st, const float* Y, int64_t len, int64_t ldy, double sign,
+                        cudaStream_t s) {
   ssi_ctx* ctx = st->ctx;
-  CovPlan plan = cov_plan(st->l, len, st->K, st->prec, ctx->num_sms);
-  SSI_TRY(ws_reserve(ctx, st->ws, plan.ws_bytes, s));
+  CovPlan plan = cov_plan(st->l, len, st->K, st->prec, ctx->num_sms, st->ws.cap);
+  if (plan.ws_bytes > st->ws.cap) {
+    set_error("cov_stream: a segment of %lld samples needs more than the reserved workspace",
+              (long long)len);
+    return SSI_E_NOMEM;
+  }
+  plan.ldy = ldy;
   st->ws.reset();
-  return covariances_ws(ctx, st->ws, plan, st->seg, st->prec, nullptr, ctx->dev_status, s,
-                        (float)sign, st->S);
+  return covariances_ws(ctx, st->ws, plan, Y, st->prec, nullptr, ctx->dev_status, s, (float)sign,
+                        st->S);
+}
+
+// S += sign * F(absolute samples [a, a + len)): in place when the segment does not wrap,
+// else gathered (len <= seg_cap).
+ssi_status segment_acc(ssi_cov_stream* st, int64_t a, int64_t len, double sign, cudaStream_t s) {
+  const int64_t pos = a % st->C;
+  if (pos + len <= st->C) return lag_sums_acc(st, st->ring + pos, len, st->C, sign, s);
+  SSI_TRY(ring_gather(st, a, len, st->seg, s));
+  return lag_sums_acc(st, st->seg, len, len, sign, s);
+}
+
+// S = F(window), from the samples in the ring.  A window that wraps around the ring is
+// A (older, to the ring's end) followed by B (from column 0): F(A B) = F(A) + F(B) + the
+// pairs across the seam, which are F(a B') - F(a) - F(B') for a = the last T samples of A
+// and B' = the first T of B (every pair spans at most K < T samples); a piece shorter
+// than T is taken whole into the gathered seam segment instead.  Every segment is longer
+// than max_lag.
+ssi_status rebuild(ssi_cov_stream* st, cudaStream_t s) {
+  const int64_t T = (int64_t)st->K + 1;
+  const int64_t a0 = st->start, n = st->n, pos = a0 % st->C;
+  st->since_rebuild = 0;
+  SSI_CUDA(cudaMemsetAsync(st->S, 0, st->bytes_S, s));
+  if (pos + n <= st->C) return lag_sums_acc(st, st->ring + pos, n, st->C, 1.0, s);
+  if (n <= st->seg_cap) return segment_acc(st, a0, n, 1.0, s);
+  const int64_t lenA = st->C - pos, lenB = n - lenA;
+  const int64_t seam = a0 + lenA;   // absolute index of B's first sample
+  const int64_t ta = std::min(lenA, T), tb = std::min(lenB, T);
+  if (lenA >= T) SSI_TRY(segment_acc(st, a0, lenA, 1.0, s));
+  if (lenB >= T) SSI_TRY(segment_acc(st, seam, lenB, 1.0, s));
+  // the seam segment: (a or all of A) followed by (B' or all of B)
+  SSI_TRY(segment_acc(st, seam - ta, ta + tb, 1.0, s));
+  if (lenA >= T) SSI_TRY(segment_acc(st, seam - ta, ta, -1.0, s));
+  if (lenB >= T) SSI_TRY(segment_acc(st, seam, tb, -1.0, s));
+  st->since_rebuild = 0;
+  return SSI_OK;
 }
 
 void stream_free(ssi_cov_stream* st) {
@@ -114,11 +167,21 @@ extern "C" ssi_status ssi_cov_stream_create(ssi_ctx* ctx, int l, int max_lag, in
   st->C = window + max_block;
   st->prec = prec;
   st->bytes_ring = sizeof(float) * (size_t)l * st->C;
-  st->bytes_seg = sizeof(float) * (size_t)l * (max_block + max_lag + 1 + max_lag + 1);
+  st->seg_cap = max_block + 2 * ((int64_t)max_lag + 1);
+  st->bytes_seg = sizeof(float) * (size_t)l * st->seg_cap;
   st->bytes_S = sizeof(float2) * (size_t)max_lag * l * l;
   ssi_status rc = ctx_alloc(ctx, reinterpret_cast<void**>(&st->ring), st->bytes_ring);
   if (rc == SSI_OK) rc = ctx_alloc(ctx, reinterpret_cast<void**>(&st->seg), st->bytes_seg);
   if (rc == SSI_OK) rc = ctx_alloc(ctx, reinterpret_cast<void**>(&st->S), st->bytes_S);
+  if (rc == SSI_OK) {
+    // the workspace of the largest segment of a push and of a whole window, reserved now
+    // so that no push or rebuild has to grow it (segments in between fit by the planner)
+    const int64_t T = (int64_t)max_lag + 1;
+    size_t cap = 0;
+    for (int64_t len : {T, max_block + T, st->seg_cap, window})
+      cap = std::max(cap, cov_plan(l, len, max_lag, prec, ctx->num_sms).ws_bytes);
+    rc = ws_reserve(ctx, st->ws, cap, nullptr);
+  }
   if (rc != SSI_OK) {
     stream_free(st);
     return rc;
@@ -134,8 +197,10 @@ extern "C" ssi_status ssi_cov_stream_push(ssi_cov_stream* st, const float* Y, in
             (long long)st->Bmax);
   SSI_CHECK(st->n > 0 || B >= (int64_t)st->K + 1,
             "ssi_cov_stream_push: the first block needs more than max_lag samples");
+  SSI_CHECK(!st->broken, "ssi_cov_stream_push: the stream is inconsistent after a failed call");
   SSI_CUDA(cudaSetDevice(st->ctx->device));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  st->broken = true;   // until every step below has been enqueued
   const int64_t T = (int64_t)st->K + 1;
   const int64_t e = st->start + st->n;   // absolute index of the first new sample
   // the block into the ring (the window occupies at most W of the W + B_max columns)
@@ -165,6 +230,21 @@ extern "C" ssi_status ssi_cov_stream_push(ssi_cov_stream* st, const float* Y, in
     st->start += D;
     st->n = st->W;
   }
+  st->since_rebuild += B;
+  if (st->since_rebuild >= st->W) SSI_TRY(rebuild(st, s));
+  st->broken = false;
+  return SSI_OK;
+}
+
+extern "C" ssi_status ssi_cov_stream_refresh(ssi_cov_stream* st, void* stream) {
+  using namespace ssi;
+  SSI_CHECK(st, "ssi_cov_stream_refresh: null pointer");
+  SSI_CHECK(!st->broken, "ssi_cov_stream_refresh: the stream is inconsistent after a failed call");
+  SSI_CHECK(st->n > st->K, "ssi_cov_stream_refresh: the window holds no more than max_lag samples");
+  SSI_CUDA(cudaSetDevice(st->ctx->device));
+  st->broken = true;
+  SSI_TRY(rebuild(st, static_cast<cudaStream_t>(stream)));
+  st->broken = false;
   return SSI_OK;
 }
 
@@ -172,6 +252,7 @@ extern "C" ssi_status ssi_cov_stream_covariances(ssi_cov_stream* st, double* R, 
                                                  void* stream) {
   using namespace ssi;
   SSI_CHECK(st && R, "ssi_cov_stream_covariances: null pointer");
+  SSI_CHECK(!st->broken, "ssi_cov_stream_covariances: the stream is inconsistent after a failed call");
   SSI_CHECK(st->n > st->K, "ssi_cov_stream_covariances: the window holds no more than max_lag samples");
   SSI_CUDA(cudaSetDevice(st->ctx->device));
   count_launches(st->ctx, 1);

@@ -42,13 +42,14 @@ struct LagGemmParams {
 };
 
 // ------------------------------------------------------------------ split/transpose
-__global__ void k_split_transpose(const float* __restrict__ Y, int l, int N, int n_rows, int l_pad,
-                                  __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo) {
+__global__ void k_split_transpose(const float* __restrict__ Y, long long ldy, int l, int N, int n_rows,
+                                  int l_pad, __nv_bfloat16* __restrict__ hi,
+                                  __nv_bfloat16* __restrict__ lo) {
   __shared__ float tile[32][33];
   const int t0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
   for (int r = threadIdx.y; r < 32; r += blockDim.y) {
     const int c = c0 + r, t = t0 + threadIdx.x;
-    tile[r][threadIdx.x] = (c < l && t < N) ? Y[(size_t)c * N + t] : 0.f;
+    tile[r][threadIdx.x] = (c < l && t < N) ? Y[(size_t)c * ldy + t] : 0.f;
   }
   __syncthreads();
   for (int r = threadIdx.y; r < 32; r += blockDim.y) {
@@ -333,7 +334,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 // ------------------------------------------------------------------ CUDA-core lag GEMM
 // One CTA: one lag, a 64 x 64 block of (c, c'), one time split.  FP32 FMA.
 __global__ void __launch_bounds__(256)
-    k_lag_gemm_fp32(const float* __restrict__ Y, int l, int N, int l_pad, int max_lag,
+    k_lag_gemm_fp32(const float* __restrict__ Y, long long ldy, int l, int N, int l_pad, int max_lag,
                     int rows_per_split, long long split_stride, float* __restrict__ partial) {
   constexpr int TK = 32;
   __shared__ float As[TK][64 + 4];
@@ -354,8 +355,8 @@ __global__ void __launch_bounds__(256)
       const int r = e / TK, j = e % TK;
       const int tt = t + j;
       const bool in = tt < t_end;
-      As[j][r] = (in && c0 + r < l) ? Y[(size_t)(c0 + r) * N + tt + lag] : 0.f;
-      Bs[j][r] = (in && d0 + r < l) ? Y[(size_t)(d0 + r) * N + tt] : 0.f;
+      As[j][r] = (in && c0 + r < l) ? Y[(size_t)(c0 + r) * ldy + tt + lag] : 0.f;
+      Bs[j][r] = (in && d0 + r < l) ? Y[(size_t)(d0 + r) * ldy + tt] : 0.f;
     }
     __syncthreads();
 #pragma unroll 8
@@ -480,8 +481,9 @@ ssi_status launch_tc(const CUtensorMap& thi, const CUtensorMap& tlo, const LagGe
 
 }  // namespace
 
-CovPlan cov_plan(int l, int64_t N, int max_lag, ssi_precision prec, int num_sms) {
+CovPlan cov_plan(int l, int64_t N, int max_lag, ssi_precision prec, int num_sms, size_t max_ws) {
   CovPlan c{};
+  c.ldy = N;
   c.l = l;
   c.N = N;
   c.max_lag = max_lag;
@@ -497,12 +499,26 @@ CovPlan cov_plan(int l, int64_t N, int max_lag, ssi_precision prec, int num_sms)
   const int n_atoms = max_lag * c.l_pad / 64;
   const int n_mp = (int)ceil_div(n_atoms, A_ATOMS);
   const int64_t units_per_split = (int64_t)n_mp * c.n_nt;
+  // splits whose workspace exceeds max_ws are skipped (the fewest splits are kept if none
+  // fits; the caller then sees ws_bytes above its cap)
+  c.n_rows = std::max<int64_t>(N, 64);
+  auto ws_of = [&](int64_t n_sp) {
+    WsPlan w;
+    if (prec == SSI_PREC_SPLIT_BF16) {
+      w.add<__nv_bfloat16>((size_t)c.n_rows * c.l_pad);
+      w.add<__nv_bfloat16>((size_t)c.n_rows * c.l_pad);
+    }
+    w.add<float>((size_t)n_sp * max_lag * c.l_pad * c.l_pad);
+    if (prec == SSI_PREC_SPLIT_BF16) w.add<int>(64);   // the lag GEMM's unit counter
+    return w.bytes;
+  };
   int64_t best_rows = 0, best_cost = 0;
   const int64_t s_lo = std::max<int64_t>(1, ceil_div(N, 16384));
   const int64_t s_hi = std::max<int64_t>(s_lo, ceil_div(N, 512));
   for (int64_t sp = s_lo; sp <= s_hi; ++sp) {
     const int64_t rows = std::max<int64_t>(512, round_up(ceil_div(N, sp), BT));
     const int64_t n_sp = ceil_div(N, rows);
+    if (sp > s_lo && ws_of(n_sp) > max_ws) continue;
     const int64_t waves = ceil_div(units_per_split * n_sp, (int64_t)std::max(1, num_sms));
     const int64_t cost = waves * (rows + 512);
     if (best_rows == 0 || cost < best_cost || (cost == best_cost && rows > best_rows)) {
@@ -512,15 +528,7 @@ CovPlan cov_plan(int l, int64_t N, int max_lag, ssi_precision prec, int num_sms)
   }
   c.rows_per_split = (int)best_rows;
   c.n_split = (int)ceil_div(N, best_rows);
-  WsPlan w;
-  c.n_rows = std::max<int64_t>(N, 64);
-  if (prec == SSI_PREC_SPLIT_BF16) {
-    w.add<__nv_bfloat16>((size_t)c.n_rows * c.l_pad);
-    w.add<__nv_bfloat16>((size_t)c.n_rows * c.l_pad);
-  }
-  w.add<float>((size_t)c.n_split * max_lag * c.l_pad * c.l_pad);
-  if (prec == SSI_PREC_SPLIT_BF16) w.add<int>(64);   // the lag GEMM's unit counter
-  c.ws_bytes = w.bytes;
+  c.ws_bytes = ws_of(c.n_split);
   return c;
 }
 
@@ -542,7 +550,7 @@ ssi_status covariances_ws(ssi_ctx* ctx, Workspace& ws, const CovPlan& c, const f
     {
       ProfScope ps(ctx, ST_SPLIT, stream);
       dim3 blk(32, 8), grd((unsigned)ceil_div(c.n_rows, 32), c.l_pad / 32);
-      k_split_transpose<<<grd, blk, 0, stream>>>(Y, c.l, (int)c.N, (int)c.n_rows, c.l_pad, hi, lo);
+      k_split_transpose<<<grd, blk, 0, stream>>>(Y, c.ldy, c.l, (int)c.N, (int)c.n_rows, c.l_pad, hi, lo);
       SSI_CUDA(cudaGetLastError());
     }
     CUtensorMap thi, tlo;
@@ -595,7 +603,7 @@ ssi_status covariances_ws(ssi_ctx* ctx, Workspace& ws, const CovPlan& c, const f
     {
       ProfScope ps(ctx, ST_LAG_GEMM, stream);
       dim3 grd((unsigned)(c.max_lag * nb * nb), (unsigned)c.n_split);
-      k_lag_gemm_fp32<<<grd, 256, 0, stream>>>(Y, c.l, (int)c.N, c.l_pad, c.max_lag,
+      k_lag_gemm_fp32<<<grd, 256, 0, stream>>>(Y, c.ldy, c.l, (int)c.N, c.l_pad, c.max_lag,
                                                c.rows_per_split, split_stride, partial);
       SSI_CUDA(cudaGetLastError());
     }
@@ -650,24 +658,14 @@ namespace {
 constexpr size_t NOALLOC_SCRATCH_FLOATS = size_t(4) << 20;   // 16 MiB
 static __device__ __align__(256) float g_noalloc_scratch[NOALLOC_SCRATCH_FLOATS];
 
-constexpr int NOALLOC_MAX_DEVICES = 64;
-std::mutex g_noalloc_mu;
-float* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
-
 // Device address of the scratch array on the current device.  Host code cannot use the
-// array's name as an address; it asks the runtime once per device.
-ssi_status noalloc_scratch(int device, float** out) {
-  if (device < 0 || device >= NOALLOC_MAX_DEVICES) {
-    set_error("ssi_covariances_noalloc: device %d beyond %d", device, NOALLOC_MAX_DEVICES);
-    return SSI_E_INVALID;
-  }
-  std::lock_guard<std::mutex> g(g_noalloc_mu);
-  if (!g_noalloc_ptr[device]) {
-    void* p = nullptr;
-    SSI_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
-    g_noalloc_ptr[device] = static_cast<float*>(p);
-  }
-  *out = g_noalloc_ptr[device];
+// array's name as an address; it asks the runtime on every call (a host-side lookup), so
+// that the address stays right after the device's context has been torn down and
+// recreated, e.g. by cudaDeviceReset.
+ssi_status noalloc_scratch(float** out) {
+  void* p = nullptr;
+  SSI_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+  *out = static_cast<float*>(p);
   return SSI_OK;
 }
 
@@ -692,7 +690,7 @@ extern "C" ssi_status ssi_covariances_noalloc(const float* Y, int l, int64_t N, 
     return SSI_E_INVALID;
   }
   float* scratch = nullptr;
-  SSI_TRY(noalloc_scratch(device, &scratch));
+  SSI_TRY(noalloc_scratch(&scratch));
   // as many time chunks as fit the scratch, at most one per 512 samples and 64 in all
   int64_t n_split = (int64_t)(NOALLOC_SCRATCH_FLOATS / per_split);
   n_split = std::min<int64_t>(n_split, std::min<int64_t>(64, ceil_div(N, 512)));
@@ -705,7 +703,7 @@ extern "C" ssi_status ssi_covariances_noalloc(const float* Y, int l, int64_t N, 
   // every partial entry read by the reduction is written by the GEMM, so nothing needs
   // clearing between calls
   dim3 grd((unsigned)(max_lag * nb * nb), (unsigned)n_split);
-  k_lag_gemm_fp32<<<grd, 256, 0, s>>>(Y, l, (int)N, l_pad, max_lag, rows_per_split,
+  k_lag_gemm_fp32<<<grd, 256, 0, s>>>(Y, (long long)N, l, (int)N, l_pad, max_lag, rows_per_split,
                                       (long long)per_split, scratch);
   SSI_CUDA(cudaGetLastError());
   k_reduce_partials<<<num_sms * 4, 256, 0, s>>>(scratch, (int)n_split, (long long)per_split, l,

@@ -17,8 +17,11 @@ ssi_status validate_job(const ssi_job_desc* j) {
   SSI_CHECK(j->n_lags >= 1 && j->n_lags <= 64 && j->lags, "job: 1 <= n_lags <= 64");
   SSI_CHECK(j->n_orders >= 1 && j->n_orders <= 512 && j->orders, "job: 1 <= n_orders <= 512");
   SSI_CHECK(j->k >= 2 && j->oversample >= 0 && j->q >= 0, "job: bad k / oversample / q");
-  SSI_CHECK(j->k + j->oversample <= 512, "job: need k + oversample <= 512");
+  SSI_CHECK(j->k <= 512 && j->k + j->oversample <= 16384,
+            "job: need k <= 512 and k + oversample <= 16384");
   SSI_CHECK(j->prec == SSI_PREC_FP32 || j->prec == SSI_PREC_SPLIT_BF16, "job: bad precision");
+  SSI_CHECK(j->small == SSI_SMALL_FP32 || j->small == SSI_SMALL_FP64,
+            "job: bad small-problem precision");
   for (int t = 0; t < j->n_lags; ++t) {
     SSI_CHECK(j->lags[t] >= 2, "job: lag %d < 2", j->lags[t]);
     SSI_CHECK(t == 0 || j->lags[t] > j->lags[t - 1], "job: lags must ascend");
@@ -51,13 +54,16 @@ JobPlan plan_job(const ssi_job_desc* j, int num_sms) {
   ws = std::max(ws, rs_total);
   std::vector<int> lags(j->lags, j->lags + j->n_lags), orders(j->orders, j->orders + j->n_orders);
   p.rz = realize_plan(j->n_lags, lags.data(), j->l, j->k, orders.data(), j->n_orders);
+  if (j->small == SSI_SMALL_FP64)
+    p.rz.ws_bytes = realize64_ws_bytes(j->n_lags, lags.data(), j->l, j->k, orders.data(), j->n_orders);
   ws = std::max(ws, p.rz.ws_bytes);
   p.ws_bytes = ws;
   WsPlan b;
   b.add<int>(64);                                              // device status words
   b.add<double>((size_t)p.max_lag * j->l * j->l);             // R
-  for (int t = 0; t < j->n_lags; ++t) b.add<float>((size_t)j->l * j->lags[t] * j->k);  // U_t
-  b.add<float>((size_t)j->n_lags * j->k);                      // S
+  const size_t esz = j->small == SSI_SMALL_FP64 ? sizeof(double) : sizeof(float);
+  for (int t = 0; t < j->n_lags; ++t) b.add<char>(esz * j->l * j->lags[t] * j->k);   // U_t
+  b.add<char>(esz * j->n_lags * j->k);                                                 // S
   if (j->y_on_host) b.add<float>((size_t)j->l * j->N);        // device copy of Y
   p.buf_bytes = b.bytes;
   p.n_slots = p.rz.slots_per_lag * j->n_lags;
@@ -66,7 +72,7 @@ JobPlan plan_job(const ssi_job_desc* j, int num_sms) {
 }
 
 ssi_status run_job(ssi_ctx* ctx, const ssi_job_desc* j, const JobPlan& p, JobBuffers& B,
-                   ssi_pole* poles, float* phi, float* S_out, cudaStream_t stream) {
+                   ssi_pole* poles, float* phi, double* S_out, cudaStream_t stream) {
   // carve the job buffers
   Workspace carve;
   carve.base = static_cast<char*>(B.buf);
@@ -75,9 +81,11 @@ ssi_status run_job(ssi_ctx* ctx, const ssi_job_desc* j, const JobPlan& p, JobBuf
   // they are cleared only when the buffer is allocated and then reset by each read
   int* status = carve.take<int>(64);
   double* R = carve.take<double>((size_t)p.max_lag * j->l * j->l);
-  std::vector<float*> U(j->n_lags);
-  for (int t = 0; t < j->n_lags; ++t) U[t] = carve.take<float>((size_t)j->l * j->lags[t] * j->k);
-  float* S = carve.take<float>((size_t)j->n_lags * j->k);
+  const bool s64 = j->small == SSI_SMALL_FP64;
+  const size_t esz = s64 ? sizeof(double) : sizeof(float);
+  std::vector<void*> U(j->n_lags);
+  for (int t = 0; t < j->n_lags; ++t) U[t] = carve.take<char>(esz * j->l * j->lags[t] * j->k);
+  char* S = carve.take<char>(esz * j->n_lags * j->k);
   float* Ydev = j->y_on_host ? carve.take<float>((size_t)j->l * j->N) : nullptr;
   if (!R || !S || !status || (j->y_on_host && !Ydev)) {
     set_error("solve: job buffers too small");
@@ -96,8 +104,8 @@ ssi_status run_job(ssi_ctx* ctx, const ssi_job_desc* j, const JobPlan& p, JobBuf
   }
   SSI_TRY(covariances_ws(ctx, B.ws, p.cov, Y, (ssi_precision)j->prec, R, status, stream));
   if (j->n_lags == 1) {
-    SSI_TRY(toeplitz_rsvd_ws(ctx, B.ws, p.rs[0], R, j->seed, (ssi_precision)j->prec, U[0], S,
-                             status, stream, false));
+    SSI_TRY(toeplitz_rsvd_ws(ctx, B.ws, p.rs[0], R, j->seed, (ssi_precision)j->prec, s64, U[0], S,
+                             s64, status, stream, false));
   } else {
     // the lags' RSVDs are independent (Sec. 2.3): fork them over LAG_STREAMS streams, each
     // lag in its own scratch region, and join before the realisations
@@ -115,8 +123,8 @@ ssi_status run_job(ssi_ctx* ctx, const ssi_job_desc* j, const JobPlan& p, JobBuf
       Workspace sub;
       sub.base = B.ws.base + p.rs_off[t];
       sub.cap = p.rs[t].ws_bytes;
-      SSI_TRY(toeplitz_rsvd_ws(ctx, sub, p.rs[t], R, j->seed, (ssi_precision)j->prec, U[t],
-                               S + (size_t)t * j->k, status, B.lag_stream[t % n_str], true));
+      SSI_TRY(toeplitz_rsvd_ws(ctx, sub, p.rs[t], R, j->seed, (ssi_precision)j->prec, s64, U[t],
+                               S + esz * t * j->k, s64, status, B.lag_stream[t % n_str], true));
     }
     for (int a = 0; a < n_str; ++a) {
       SSI_CUDA(cudaEventRecord(B.join[a], B.lag_stream[a]));
@@ -124,14 +132,26 @@ ssi_status run_job(ssi_ctx* ctx, const ssi_job_desc* j, const JobPlan& p, JobBuf
     }
   }
   std::vector<int> lags(j->lags, j->lags + j->n_lags), orders(j->orders, j->orders + j->n_orders);
-  std::vector<const float*> Uc(U.begin(), U.end());
-  SSI_TRY(realize_ws(ctx, B.ws, p.rz, lags.data(), Uc.data(), orders.data(), 1.0 / j->fs, poles, phi,
-                     status, stream));
+  if (s64) {
+    std::vector<const double*> Ud(j->n_lags);
+    for (int t = 0; t < j->n_lags; ++t) Ud[t] = static_cast<const double*>(U[t]);
+    SSI_TRY(realize64_ws(ctx, B.ws, j->n_lags, lags.data(), j->l, j->k, Ud.data(), orders.data(),
+                         j->n_orders, p.rz.slots_per_lag, 1.0 / j->fs, poles, phi, status, stream));
+  } else {
+    std::vector<const float*> Uc(j->n_lags);
+    for (int t = 0; t < j->n_lags; ++t) Uc[t] = static_cast<const float*>(U[t]);
+    SSI_TRY(realize_ws(ctx, B.ws, p.rz, lags.data(), Uc.data(), orders.data(), 1.0 / j->fs, poles,
+                       phi, status, stream));
+  }
   SSI_TRY(stabilize_ws(ctx, B.ws, j->n_lags, j->n_orders, orders.data(), j->l, poles, phi, &j->stab,
                        stream));
-  if (S_out)
-    SSI_CUDA(cudaMemcpyAsync(S_out, S, sizeof(float) * (size_t)j->n_lags * j->k,
-                             cudaMemcpyDeviceToDevice, stream));
+  if (S_out) {
+    if (s64)
+      SSI_CUDA(cudaMemcpyAsync(S_out, S, sizeof(double) * (size_t)j->n_lags * j->k,
+                               cudaMemcpyDeviceToDevice, stream));
+    else
+      SSI_TRY(convert_f2d(reinterpret_cast<const float*>(S), (long long)j->n_lags * j->k, S_out, stream));
+  }
   return SSI_OK;
 }
 
@@ -193,7 +213,7 @@ extern "C" ssi_status ssi_job_sizes(const ssi_job_desc* job, int64_t* n_slots, i
 }
 
 extern "C" ssi_status ssi_solve(ssi_ctx* ctx, const ssi_job_desc* job, ssi_pole* poles, float* phi,
-                                float* S_out, void* stream) {
+                                double* S_out, void* stream) {
   SSI_CHECK(ctx && poles && phi, "ssi_solve: null pointer");
   SSI_TRY(validate_job(job));
   SSI_CUDA(cudaSetDevice(ctx->device));

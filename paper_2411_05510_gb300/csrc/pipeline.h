@@ -37,7 +37,7 @@ JobPlan plan_job(const ssi_job_desc* j, int num_sms);
 ssi_status buffers_reserve(ssi_ctx* ctx, JobBuffers& B, const JobPlan& p, cudaStream_t stream);
 void buffers_free(ssi_ctx* ctx, JobBuffers& B);
 ssi_status run_job(ssi_ctx* ctx, const ssi_job_desc* j, const JobPlan& p, JobBuffers& B,
-                   ssi_pole* poles, float* phi, float* S_out, cudaStream_t stream);
+                   ssi_pole* poles, float* phi, double* S_out, cudaStream_t stream);
 JobBuffers& ctx_solve_buffers(ssi_ctx* ctx);
 
 }  // namespace ssi

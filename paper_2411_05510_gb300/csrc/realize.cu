@@ -21,6 +21,7 @@
 //                 transformation through the logged reflectors, Phi = U[:l,:n] Psi~,
 //                 pole parameters, MPC and MPD.  Largest orders are scheduled first.
 #include <cfloat>
+#include <vector>
 
 #include "blackwell.cuh"
 #include "common.cuh"
@@ -121,59 +122,64 @@ constexpr int FACTOR_SMEM_K = 224;   // largest k whose factor fits shared memor
 //   2. R^{-1} in place, column by column (column j from the inverted leading block and
 //      a copy of R's column j);
 //   3. M = R^{-T} H = (R^{-1})^T H with 4 x 4 outputs per thread.
-// GLOBAL: k > FACTOR_SMEM_K, the same layout in the lag's global scratch (L2-resident);
-// a separate instantiation keeps shared-memory instructions for the common case.
-template <bool GLOBAL>
+// GLOBAL: k > FACTOR_SMEM_K (FP32) or FP64, the same layout in the lag's global scratch
+// (L2-resident); a separate instantiation keeps shared-memory instructions for the common
+// case.  T: float (the default small-problem arithmetic) or double.
+template <typename T> __device__ __forceinline__ T min_normal();
+template <> __device__ __forceinline__ float min_normal<float>() { return FLT_MIN; }
+template <> __device__ __forceinline__ double min_normal<double>() { return DBL_MIN; }
+
+template <bool GLOBAL, typename T>
 __global__ void __launch_bounds__(1024)
-    k_lag_factor(const float* __restrict__ GH, int k, float* __restrict__ RM, float* Rglobal,
-                 int* status) {
-  extern __shared__ float s_R[];  // k x (k+1), then a column buffer of k floats
-  float* sR = GLOBAL ? Rglobal + (size_t)blockIdx.x * ((size_t)k * (k + 1) + k) : s_R;
+    k_lag_factor(const T* __restrict__ GH, int k, T* __restrict__ RM, T* Rglobal, int* status) {
+  extern __shared__ __align__(16) unsigned char s_R_raw[];  // k x (k+1), then a column buffer of k
+  T* sR = GLOBAL ? Rglobal + (size_t)blockIdx.x * ((size_t)k * (k + 1) + k)
+                 : reinterpret_cast<T*>(s_R_raw);
   const int ldr = k + 1;
-  float* col = sR + (size_t)k * ldr;
+  T* col = sR + (size_t)k * ldr;
   const int t = blockIdx.x;
-  const float* G = GH + (size_t)t * 2 * k * k;
-  const float* H = G + (size_t)k * k;
-  float* Rinv = RM + (size_t)t * 2 * k * k;
-  float* M = Rinv + (size_t)k * k;
+  const T* G = GH + (size_t)t * 2 * k * k;
+  const T* H = G + (size_t)k * k;
+  T* Rinv = RM + (size_t)t * 2 * k * k;
+  T* M = Rinv + (size_t)k * k;
   const int tid = threadIdx.x, nth = blockDim.x, warp = tid >> 5, lane = tid & 31,
             nwarps = nth >> 5;
-  __shared__ float s_red[32];
-  float gmax = 0.f;
+  __shared__ T s_red[32];
+  T gmax = 0;
   for (int e = tid; e < k * k; e += nth) {
     const int r = e / k, c = e % k;
-    const float v = G[e];
+    const T v = G[e];
     sR[r * ldr + c] = v;
-    if (r == c) gmax = fmaxf(gmax, v);
+    if (r == c) gmax = fmax(gmax, v);
   }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) gmax = fmaxf(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
+  for (int o = 16; o > 0; o >>= 1) gmax = fmax(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
   if (lane == 0) s_red[warp] = gmax;
   __syncthreads();
   if (tid == 0) {
-    float g = 0.f;
-    for (int w2 = 0; w2 < nwarps; ++w2) g = fmaxf(g, s_red[w2]);
+    T g = 0;
+    for (int w2 = 0; w2 < nwarps; ++w2) g = fmax(g, s_red[w2]);
     s_red[0] = g;
   }
   __syncthreads();
-  const float floor_v = fmaxf(s_red[0] * 1e-10f, FLT_MIN);
+  const T floor_v = fmax(s_red[0] * (T)1e-10, min_normal<T>());
   // 1. Cholesky: row j of R
   for (int j = 0; j < k; ++j) {
     if (warp == 0) {
-      float d = sR[j * ldr + j];
+      T d = sR[j * ldr + j];
       if (!(d > floor_v)) {
         if (lane == 0) atomicOr(status, DEV_NOTCONVERGED);
         d = floor_v;
       }
-      d = sqrtf(d);
-      const float id = 1.f / d;
+      d = sqrt(d);
+      const T id = T(1) / d;
       for (int c = j + 1 + lane; c < k; c += 32) sR[j * ldr + c] *= id;
       if (lane == 0) sR[j * ldr + j] = d;
     }
     __syncthreads();
     // G[a][c] -= R[j][a] R[j][c], j < a <= c: warps along rows, lanes along columns
     for (int a = j + 1 + warp; a < k; a += nwarps) {
-      const float ra = sR[j * ldr + a];
+      const T ra = sR[j * ldr + a];
       for (int c = a + lane; c < k; c += 32) sR[a * ldr + c] -= ra * sR[j * ldr + c];
     }
     __syncthreads();
@@ -182,15 +188,15 @@ __global__ void __launch_bounds__(1024)
   for (int j = 0; j < k; ++j) {
     for (int i = tid; i < j; i += nth) col[i] = sR[i * ldr + j];
     __syncthreads();
-    const float inv = 1.f / sR[j * ldr + j];
+    const T inv = T(1) / sR[j * ldr + j];
     for (int i = tid; i < j; i += nth) {
-      float a0 = 0.f, a1 = 0.f;
+      T a0 = 0, a1 = 0;
       int m = i;
       for (; m + 1 < j; m += 2) {
-        a0 = fmaf(sR[i * ldr + m], col[m], a0);
-        a1 = fmaf(sR[i * ldr + m + 1], col[m + 1], a1);
+        a0 = fma(sR[i * ldr + m], col[m], a0);
+        a1 = fma(sR[i * ldr + m + 1], col[m + 1], a1);
       }
-      if (m < j) a0 = fmaf(sR[i * ldr + m], col[m], a0);
+      if (m < j) a0 = fma(sR[i * ldr + m], col[m], a0);
       sR[i * ldr + j] = -(a0 + a1) * inv;
     }
     __syncthreads();
@@ -199,25 +205,25 @@ __global__ void __launch_bounds__(1024)
   __syncthreads();
   for (int e = tid; e < k * k; e += nth) {
     const int r = e / k, c = e % k;
-    Rinv[e] = (c >= r) ? sR[r * ldr + c] : 0.f;
+    Rinv[e] = (c >= r) ? sR[r * ldr + c] : T(0);
   }
   // 3. M[j][c] = sum_{r <= j} Rinv[r][j] H[r][c]
   const int k4 = (k + 3) / 4;
   for (int task = tid; task < k4 * k4; task += nth) {
     const int j0 = 4 * (task / k4), c0 = 4 * (task % k4);
-    float acc[4][4] = {};
+    T acc[4][4] = {};
     const int rmax = min(j0 + 3, k - 1);
     for (int r = 0; r <= rmax; ++r) {
-      float ri[4], hv[4];
+      T ri[4], hv[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        ri[u] = (j0 + u < k && r <= j0 + u) ? sR[r * ldr + j0 + u] : 0.f;
-        hv[u] = (c0 + u < k) ? __ldg(H + (size_t)r * k + c0 + u) : 0.f;
+        ri[u] = (j0 + u < k && r <= j0 + u) ? sR[r * ldr + j0 + u] : T(0);
+        hv[u] = (c0 + u < k) ? __ldg(H + (size_t)r * k + c0 + u) : T(0);
       }
 #pragma unroll
       for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int u = 0; u < 4; ++u) acc[a][u] = fmaf(ri[a], hv[u], acc[a][u]);
+        for (int u = 0; u < 4; ++u) acc[a][u] = fma(ri[a], hv[u], acc[a][u]);
     }
 #pragma unroll
     for (int a = 0; a < 4; ++a)
@@ -1410,6 +1416,15 @@ __global__ void __launch_bounds__(VEC_THREADS)
 
 }  // namespace
 
+// The per-lag factorisation in FP64 (the FP64 realisation path, csrc/eig64.cu); R in the
+// lags' global scratch Fs (k (k + 1) + k doubles per lag).
+ssi_status lag_factor64_launch(const double* GH, int k, int n_lags, double* RM, double* Fs, int* status,
+                               cudaStream_t stream) {
+  k_lag_factor<true, double><<<n_lags, 1024, 0, stream>>>(GH, k, RM, Fs, status);
+  SSI_CUDA(cudaGetLastError());
+  return SSI_OK;
+}
+
 RealizePlan realize_plan(int n_lags, const int* lags, int l, int k, const int* orders, int n_orders) {
   RealizePlan r{};
   r.n_lags = n_lags;
@@ -1483,11 +1498,11 @@ ssi_status realize_ws(ssi_ctx* ctx, Workspace& ws, const RealizePlan& r, const i
   SSI_CUDA(cudaGetLastError());
   const size_t fsmem = Rg ? 0 : ((size_t)k * (k + 1) + k) * sizeof(float);
   if (Rg) {
-    k_lag_factor<true><<<r.n_lags, 1024, 0, stream>>>(GH, k, RM, Rg, dev_status);
+    k_lag_factor<true, float><<<r.n_lags, 1024, 0, stream>>>(GH, k, RM, Rg, dev_status);
   } else {
-    SSI_CUDA(cudaFuncSetAttribute(k_lag_factor<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)(220 * 1024)));
-    k_lag_factor<false><<<r.n_lags, 1024, fsmem, stream>>>(GH, k, RM, nullptr, dev_status);
+    SSI_CUDA(cudaFuncSetAttribute(k_lag_factor<false, float>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(220 * 1024)));
+    k_lag_factor<false, float><<<r.n_lags, 1024, fsmem, stream>>>(GH, k, RM, nullptr, dev_status);
   }
   SSI_CUDA(cudaGetLastError());
   }
@@ -1552,15 +1567,17 @@ ssi_status realize_ws(ssi_ctx* ctx, Workspace& ws, const RealizePlan& r, const i
 }  // namespace ssi
 
 extern "C" ssi_status ssi_realize_batch(ssi_ctx* ctx, int n_lags, const int* lags,
-                                        const float* const* U, int l, int k, const int* orders,
-                                        int n_orders, double dt, ssi_pole* poles, float* phi,
-                                        void* stream) {
+                                        const double* const* U, int l, int k, const int* orders,
+                                        int n_orders, double dt, ssi_small_precision small,
+                                        ssi_pole* poles, float* phi, void* stream) {
   using namespace ssi;
   SSI_CHECK(ctx && lags && U && orders && poles && phi, "ssi_realize_batch: null pointer");
   SSI_CHECK(n_lags >= 1 && n_lags <= MAX_LAGS, "ssi_realize_batch: 1 <= n_lags <= %d", MAX_LAGS);
   SSI_CHECK(n_orders >= 1 && n_orders <= 512, "ssi_realize_batch: 1 <= n_orders <= 512");
   SSI_CHECK(l >= 1 && k >= 2 && dt > 0, "ssi_realize_batch: bad l/k/dt");
   SSI_CHECK(k <= N_MAX, "ssi_realize_batch: k=%d > %d not supported", k, N_MAX);
+  SSI_CHECK(small == SSI_SMALL_FP32 || small == SSI_SMALL_FP64,
+            "ssi_realize_batch: bad small-problem precision");
   for (int t = 0; t < n_lags; ++t) {
     SSI_CHECK(lags[t] >= 2, "ssi_realize_batch: lag %d < 2", lags[t]);
     SSI_CHECK(U[t], "ssi_realize_batch: null U[%d]", t);
@@ -1576,7 +1593,25 @@ extern "C" ssi_status ssi_realize_batch(ssi_ctx* ctx, int n_lags, const int* lag
   SSI_CUDA(cudaSetDevice(ctx->device));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   RealizePlan plan = realize_plan(n_lags, lags, l, k, orders, n_orders);
+  if (small == SSI_SMALL_FP64) {
+    SSI_TRY(ws_reserve(ctx, ctx->ws, realize64_ws_bytes(n_lags, lags, l, k, orders, n_orders), s));
+    SSI_TRY(realize64_ws(ctx, ctx->ws, n_lags, lags, l, k, U, orders, n_orders, plan.slots_per_lag,
+                         dt, poles, phi, ctx->dev_status, s));
+    return check_dev_status(ctx->dev_status, s);
+  }
+  // FP32: U rounded once into the auxiliary workspace, then the FP32 path
+  size_t u_floats = 0;
+  for (int t = 0; t < n_lags; ++t) u_floats += (size_t)round_up((int64_t)l * lags[t] * k, 64);
+  SSI_TRY(ws_reserve(ctx, ctx->ws_aux, u_floats * sizeof(float), s));
+  std::vector<const float*> U32(n_lags);
+  size_t off = 0;
+  for (int t = 0; t < n_lags; ++t) {
+    float* dst = reinterpret_cast<float*>(ctx->ws_aux.base) + off;
+    SSI_TRY(convert_d2f(U[t], (long long)l * lags[t] * k, dst, s));
+    U32[t] = dst;
+    off += (size_t)round_up((int64_t)l * lags[t] * k, 64);
+  }
   SSI_TRY(ws_reserve(ctx, ctx->ws, plan.ws_bytes, s));
-  SSI_TRY(realize_ws(ctx, ctx->ws, plan, lags, U, orders, dt, poles, phi, ctx->dev_status, s));
+  SSI_TRY(realize_ws(ctx, ctx->ws, plan, lags, U32.data(), orders, dt, poles, phi, ctx->dev_status, s));
   return check_dev_status(ctx->dev_status, s);
 }

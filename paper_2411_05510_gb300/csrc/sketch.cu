@@ -24,9 +24,11 @@ namespace ssi {
 size_t qr_ws_bytes(int ncols, int num_sms);
 ssi_status qr_launch(ssi_ctx* ctx, Workspace& ws, float* A, int rows, int ncols, int ld,
                      float* Rout, int* status, cudaStream_t stream, bool shared_device);
-size_t jacobi_ws_bytes(int K);
+size_t jacobi_ws_bytes(int K, int num_sms, bool fp64);
+ssi_status jacobi_launch64(Workspace& ws, const float* R2, int K, double* Ut, double* S, int* status,
+                           int num_sms, cudaStream_t stream);
 ssi_status jacobi_launch(Workspace& ws, const float* R2, int K, float* Ut, float* S, int* status,
-                         cudaStream_t stream);
+                         int num_sms, cudaStream_t stream);
 
 namespace {
 
@@ -426,9 +428,10 @@ __global__ void __launch_bounds__(256)
         make_float4(acc[x][0], acc[x][1], acc[x][2], acc[x][3]);
 }
 
-// U[b*l + c][j] = sum_a Q[b*l_pad + c][a] Ut[a][j], j < k
-__global__ void k_form_u(const float* __restrict__ Q, int ldq, const float* __restrict__ Ut, int K,
-                         int k, int l, int l_pad, int i, float* __restrict__ U) {
+// U[b*l + c][j] = sum_a Q[b*l_pad + c][a] Ut[a][j], j < k; accumulated in Ut's precision
+template <typename TU, typename TO>
+__global__ void k_form_u(const float* __restrict__ Q, int ldq, const TU* __restrict__ Ut, int K,
+                         int k, int l, int l_pad, int i, TO* __restrict__ U) {
   const long long total = (long long)l * i * k;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
@@ -436,10 +439,17 @@ __global__ void k_form_u(const float* __restrict__ Q, int ldq, const float* __re
     const int rr = (int)(e / k);
     const int b = rr / l, c = rr % l;
     const float* q = Q + (size_t)(b * l_pad + c) * ldq;
-    float s = 0.f;
-    for (int a = 0; a < K; ++a) s = fmaf(q[a], Ut[(size_t)a * K + j], s);
-    U[e] = s;
+    TU s = 0;
+    for (int a = 0; a < K; ++a) s = fma((TU)q[a], Ut[(size_t)a * K + j], s);
+    U[e] = (TO)s;
   }
+}
+
+template <typename TI, typename TO>
+__global__ void k_convert(const TI* __restrict__ x, long long n, TO* __restrict__ y) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x)
+    y[e] = (TO)x[e];
 }
 
 template <int MODE, int NB>
@@ -502,6 +512,18 @@ int grid_1d(long long n, int threads, int num_sms) {
 
 }  // namespace
 
+ssi_status convert_f2d(const float* x, long long n, double* y, cudaStream_t stream) {
+  k_convert<float, double><<<grid_1d(n, 256, 152), 256, 0, stream>>>(x, n, y);
+  SSI_CUDA(cudaGetLastError());
+  return SSI_OK;
+}
+
+ssi_status convert_d2f(const double* x, long long n, float* y, cudaStream_t stream) {
+  k_convert<double, float><<<grid_1d(n, 256, 152), 256, 0, stream>>>(x, n, y);
+  SSI_CUDA(cudaGetLastError());
+  return SSI_OK;
+}
+
 ssi_status gaussian_omega_launch(int rows, int cols, int ld, uint64_t seed, float* out,
                                  __nv_bfloat16*, __nv_bfloat16*, cudaStream_t stream) {
   k_omega<<<grid_1d((long long)rows * ld, 256, 152), 256, 0, stream>>>(rows, cols, ld, seed, out, 1, 1,
@@ -541,14 +563,17 @@ RsvdPlan rsvd_plan(int l, int i, int k, int oversample, int q, int num_sms) {
   w.add<float>((size_t)r.K * r.K);  // R2
   w.add<float>((size_t)r.K * r.K);  // U~
   w.add<float>((size_t)r.K);        // sigma
-  w.bytes += qr_ws_bytes(r.K, num_sms) + jacobi_ws_bytes(r.K) + 4096;
+  w.add<double>((size_t)r.K * r.K); // U~ (FP64 small problems)
+  w.add<double>((size_t)r.K);       // sigma (FP64 small problems)
+  w.bytes += qr_ws_bytes(r.K, num_sms) +
+             std::max(jacobi_ws_bytes(r.K, num_sms, false), jacobi_ws_bytes(r.K, num_sms, true)) + 4096;
   r.ws_bytes = w.bytes;
   return r;
 }
 
 ssi_status toeplitz_rsvd_ws(ssi_ctx* ctx, Workspace& ws, const RsvdPlan& r, const double* R,
-                            uint64_t seed, ssi_precision prec, float* U, float* S,
-                            int* dev_status, cudaStream_t stream, bool shared_device) {
+                            uint64_t seed, ssi_precision prec, bool small64, void* U, void* S,
+                            bool out64, int* dev_status, cudaStream_t stream, bool shared_device) {
   ws.reset();
   const bool tc = prec == SSI_PREC_SPLIT_BF16;
   const int n_lag = 2 * r.i - 1;
@@ -581,7 +606,10 @@ ssi_status toeplitz_rsvd_ws(ssi_ctx* ctx, Workspace& ws, const RsvdPlan& r, cons
   float* R2 = ws.take<float>((size_t)r.K * r.K);
   float* Ut = ws.take<float>((size_t)r.K * r.K);
   float* sig = ws.take<float>((size_t)r.K);
-  if (!Rh || !Rl || !R32 || !Xh || !Xl || !Yb || !Qs || !part || !R2 || !Ut || !sig) {
+  double* Ut64 = ws.take<double>((size_t)r.K * r.K);
+  double* sig64 = ws.take<double>((size_t)r.K);
+  if (!Rh || !Rl || !R32 || !Xh || !Xl || !Yb || !Qs || !part || !R2 || !Ut || !sig || !Ut64 ||
+      !sig64) {
     set_error("toeplitz_rsvd: workspace too small");
     return SSI_E_NOMEM;
   }
@@ -665,13 +693,30 @@ ssi_status toeplitz_rsvd_ws(ssi_ctx* ctx, Workspace& ws, const RsvdPlan& r, cons
   ws.off = ws_mark;
   {
     ProfScope ps(ctx, ST_SMALL_SVD, stream);
-    SSI_TRY(jacobi_launch(ws, R2, r.K, Ut, sig, dev_status, stream));
+    if (small64)
+      SSI_TRY(jacobi_launch64(ws, R2, r.K, Ut64, sig64, dev_status, nsm, stream));
+    else
+      SSI_TRY(jacobi_launch(ws, R2, r.K, Ut, sig, dev_status, nsm, stream));
   }
   ProfScope ps_u(ctx, ST_OTHER, stream);
-  k_form_u<<<grid_1d((long long)r.L * r.k, 256, nsm), 256, 0, stream>>>(Qs, r.Kp, Ut, r.K, r.k, r.l,
-                                                                        r.l_pad, r.i, U);
+  const int gu = grid_1d((long long)r.L * r.k, 256, nsm), gs = grid_1d(r.k, 256, nsm);
+  if (small64) {
+    k_form_u<double, double><<<gu, 256, 0, stream>>>(Qs, r.Kp, Ut64, r.K, r.k, r.l, r.l_pad, r.i,
+                                                     static_cast<double*>(U));
+    SSI_CUDA(cudaGetLastError());
+    SSI_CUDA(cudaMemcpyAsync(S, sig64, sizeof(double) * r.k, cudaMemcpyDeviceToDevice, stream));
+  } else if (out64) {
+    k_form_u<float, double><<<gu, 256, 0, stream>>>(Qs, r.Kp, Ut, r.K, r.k, r.l, r.l_pad, r.i,
+                                                    static_cast<double*>(U));
+    SSI_CUDA(cudaGetLastError());
+    k_convert<float, double><<<gs, 256, 0, stream>>>(sig, r.k, static_cast<double*>(S));
+  } else {
+    k_form_u<float, float><<<gu, 256, 0, stream>>>(Qs, r.Kp, Ut, r.K, r.k, r.l, r.l_pad, r.i,
+                                                   static_cast<float*>(U));
+    SSI_CUDA(cudaGetLastError());
+    SSI_CUDA(cudaMemcpyAsync(S, sig, sizeof(float) * r.k, cudaMemcpyDeviceToDevice, stream));
+  }
   SSI_CUDA(cudaGetLastError());
-  SSI_CUDA(cudaMemcpyAsync(S, sig, sizeof(float) * r.k, cudaMemcpyDeviceToDevice, stream));
   return SSI_OK;
 }
 
@@ -689,19 +734,23 @@ extern "C" ssi_status ssi_gaussian_omega(ssi_ctx* ctx, int rows, int cols, uint6
 
 extern "C" ssi_status ssi_toeplitz_rsvd(ssi_ctx* ctx, const double* R, int l, int i, int k,
                                         int oversample, int q, uint64_t seed, ssi_precision prec,
-                                        float* U, float* S, void* stream) {
+                                        ssi_small_precision small, double* U, double* S,
+                                        void* stream) {
   using namespace ssi;
   SSI_CHECK(ctx && R && U && S, "ssi_toeplitz_rsvd: null pointer");
   SSI_CHECK(l >= 1 && l <= 1024, "ssi_toeplitz_rsvd: l=%d out of range", l);
   SSI_CHECK(i >= 2, "ssi_toeplitz_rsvd: need i >= 2");
   SSI_CHECK(k >= 1 && oversample >= 0 && q >= 0, "ssi_toeplitz_rsvd: bad k/oversample/q");
-  SSI_CHECK(k + oversample <= 512 && (int64_t)(k + oversample) <= (int64_t)l * i,
-            "ssi_toeplitz_rsvd: need k + oversample <= min(l*i, 512)");
+  SSI_CHECK(k + oversample <= 16384 && (int64_t)(k + oversample) <= (int64_t)l * i,
+            "ssi_toeplitz_rsvd: need k + oversample <= min(l*i, 16384)");
   SSI_CHECK(prec == SSI_PREC_FP32 || prec == SSI_PREC_SPLIT_BF16, "ssi_toeplitz_rsvd: bad precision");
+  SSI_CHECK(small == SSI_SMALL_FP32 || small == SSI_SMALL_FP64,
+            "ssi_toeplitz_rsvd: bad small-problem precision");
   SSI_CUDA(cudaSetDevice(ctx->device));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   RsvdPlan plan = rsvd_plan(l, i, k, oversample, q, ctx->num_sms);
   SSI_TRY(ws_reserve(ctx, ctx->ws, plan.ws_bytes, s));
-  SSI_TRY(toeplitz_rsvd_ws(ctx, ctx->ws, plan, R, seed, prec, U, S, ctx->dev_status, s, false));
+  SSI_TRY(toeplitz_rsvd_ws(ctx, ctx->ws, plan, R, seed, prec, small == SSI_SMALL_FP64, U, S, true,
+                           ctx->dev_status, s, false));
   return check_dev_status(ctx->dev_status, s);
 }

@@ -5,176 +5,332 @@
 // on B = R2^T: rotating the columns of B until they are mutually orthogonal gives
 // B V = W Sigma, hence R2 = V Sigma W^T and U~ = W (the normalised columns of B),
 // Sigma = their norms; V itself is never needed.
-// One CTA of 512 threads; B is held column by column in shared memory when it fits,
-// else in global memory.  Pairs follow the circle (round-robin) ordering, four pairs
-// per warp (eight lanes each).  The column stride is = 8 (mod 32) floats, so the four
-// groups of a warp, which hold consecutive pair indices, read distinct banks.  Sweeps stop when every pair satisfies
-// |b_p^T b_q| <= tol ||b_p|| ||b_q|| or after max_sweeps (status bit set).
+//
+// Parallel block ordering on a cooperative grid of C CTAs.  The K columns are cut into
+// 2C blocks of bw columns; in each outer round every CTA holds two blocks and rotates
+// every column of the one against every column of the other (bw inner rounds of bw
+// disjoint pairs, one warp per pair), and in the first outer round of a sweep also the
+// pairs inside each of its two blocks.  The blocks move between CTAs by the circle
+// (round-robin) schedule of 2C players, so one sweep (2C - 1 outer rounds) meets every
+// column pair once.  The blocks of a round are staged in shared memory when they fit;
+// the global copy of B is the exchange medium, and a bounded grid barrier separates the
+// rounds.  Sweeps stop when no pair of a sweep had |b_p^T b_q| > tol ||b_p|| ||b_q||, or
+// after max_sweeps (status bit set).  Every reduction runs in a fixed order, so the
+// result does not depend on timing.
+//
+// The scalar type is FP32 (the default small-problem arithmetic) or FP64.
+#include <algorithm>
+#include <cmath>
+
+#include "blackwell.cuh"
 #include "common.cuh"
 
 namespace ssi {
 
 namespace {
 
-constexpr int JT = 512;
+constexpr int BJ_THREADS = 512;
+constexpr int BJ_WARPS = BJ_THREADS / 32;
+constexpr uint64_t BJ_BAR_NS = 2000000000ull;
+constexpr size_t BJ_SMEM_MAX = 200 * 1024;
 
-__host__ __device__ inline int col_stride(int K) { return ((K + 23) / 32) * 32 + 8; }
+template <typename T>
+struct BjParams {
+  const float* R2;      // K x K row-major: column c of B = R2^T is row c of R2
+  int K, ldb;           // B in global memory, column c at B + c * ldb
+  T* B;
+  int n_blk, bw;        // 2C blocks of bw columns (the last ones may be short or empty)
+  T tol;
+  int max_sweeps;
+  int* flags;           // [max_sweeps] "some pair was rotated", zeroed before the launch
+  unsigned* bar;        // [0] grid barrier counter, [8] abort flag; zeroed before the launch
+  T* norms;             // K column norms
+  T* Ut;                // K x K row-major: column j = singular vector of rank j
+  T* S;                 // K singular values, descending
+  int* status;
+  int ldk;              // leading dimension of a staged column (0: blocks stay in global)
+};
 
-__device__ __forceinline__ float warp_sum(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// B: column c of B at B + c*ldb (length K).  Output: Ut (K x K row-major, column j =
-// singular vector of rank j), S (K, descending).
-template <int RJ8>   // K <= 8 * RJ8
-__global__ void __launch_bounds__(JT, 1)
-    k_jacobi_svd(const float* __restrict__ R2, int K, float* __restrict__ Bglobal, float tol,
-                 int max_sweeps, float* __restrict__ Ut, float* __restrict__ Sout, int* status) {
-  extern __shared__ float smem_f[];
-  const bool in_smem = Bglobal == nullptr;
-  float* B = in_smem ? smem_f : Bglobal;
-  __shared__ float s_norm[512];
-  __shared__ int s_rank[512];
-  __shared__ int s_rot;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = JT / 32;
-  // B = R2^T: column c of B is row c of R2
-  const int KS = col_stride(K);
-  for (int e = tid; e < K * K; e += JT) B[(e / K) * KS + e % K] = R2[e];
+// Grid barrier on a monotonic arrival counter: barrier j of the launch passes once the
+// counter reaches j x gridDim.x.  The wait is bounded; on timeout the status word gets
+// DEV_TIMEOUT and every CTA leaves through the abort flag.
+template <typename T>
+__device__ bool bj_grid_sync(const BjParams<T>& p, unsigned& n_bar) {
   __syncthreads();
-  const int n_pad = K + (K & 1);
-  const int half = n_pad / 2;
-  int sweep = 0;
-  for (; sweep < max_sweeps; ++sweep) {
-    if (tid == 0) s_rot = 0;
-    __syncthreads();
-    for (int rnd = 0; rnd < n_pad - 1; ++rnd) {
-      // circle method: position 0 fixed, others rotate by rnd.  Eight lanes per pair
-      // (four pairs per warp): short reductions, many pairs in flight per warp.
-      const int g = lane >> 3, gl = lane & 7;
-      const unsigned gmask = 0xFFu << (8 * g);
-      // the loop bound depends on the warp only, so all 32 lanes run the same iterations
-      // (the group reductions below shuffle across the whole warp)
-      for (int base = warp * 4; base < half; base += nw * 4) {
-        const int pi = base + g;
-        const bool live = pi < half;
-        int p = 0, q = 0;
-        if (live) {
-          // (x - 1 + rnd) mod (n_pad - 1) with both terms below the modulus: one subtraction
-          const int a = pi, b = n_pad - 1 - pi, m1 = n_pad - 1;
-          int va = a - 1 + rnd, vb = b - 1 + rnd;
-          if (va >= m1) va -= m1;
-          if (vb >= m1) vb -= m1;
-          p = (a == 0) ? 0 : 1 + va;
-          q = (b == 0) ? 0 : 1 + vb;
-          if (p > q) { const int t = p; p = q; q = t; }
-        }
-        const bool act = live && p < K && q < K;
-        float* bp = B + (size_t)p * KS;
-        float* bq = B + (size_t)q * KS;
-        float xv[RJ8], yv[RJ8];
-        float al = 0.f, be = 0.f, ga = 0.f;
-#pragma unroll
-        for (int t = 0; t < RJ8; ++t) {
-          const int r = gl + 8 * t;
-          xv[t] = (act && r < K) ? bp[r] : 0.f;
-          yv[t] = (act && r < K) ? bq[r] : 0.f;
-          al = fmaf(xv[t], xv[t], al);
-          be = fmaf(yv[t], yv[t], be);
-          ga = fmaf(xv[t], yv[t], ga);
-        }
-#pragma unroll
-        for (int o = 4; o > 0; o >>= 1) {
-          al += __shfl_xor_sync(0xffffffffu, al, o);
-          be += __shfl_xor_sync(0xffffffffu, be, o);
-          ga += __shfl_xor_sync(0xffffffffu, ga, o);
-        }
-        (void)gmask;
-        if (act && fabsf(ga) > tol * sqrtf(al * be) && al > 0.f && be > 0.f) {
-          const float zeta = (be - al) / (2.f * ga);
-          const float t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
-          const float c = rsqrtf(1.f + t * t);
-          const float s = c * t;
-#pragma unroll
-          for (int u = 0; u < RJ8; ++u) {
-            const int r = gl + 8 * u;
-            if (r < K) {
-              bp[r] = c * xv[u] - s * yv[u];
-              bq[r] = s * xv[u] + c * yv[u];
-            }
-          }
-          if (gl == 0) s_rot = 1;
+  __shared__ int ok_s;
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    n_bar += 1;
+    const unsigned target = n_bar * gridDim.x;
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(p.bar + 8);
+    __threadfence();
+    const unsigned arrived = atomicAdd(&p.bar[0], 1u) + 1u;
+    if (arrived < target) {
+      const uint64_t t0 = bw::global_ns();
+      while (*(volatile unsigned*)&p.bar[0] < target) {
+        if (*abort_flag) { ok = 0; break; }
+        if (bw::global_ns() - t0 > BJ_BAR_NS) {
+          atomicOr(p.status, DEV_TIMEOUT);
+          atomicExch(reinterpret_cast<int*>(p.bar + 8), 1);
+          ok = 0;
+          break;
         }
       }
-      __syncthreads();
     }
-    if (s_rot == 0) break;
-    __syncthreads();
-  }
-  if (sweep == max_sweeps && tid == 0) atomicOr(status, DEV_NOTCONVERGED);
-  // norms and ranks
-  for (int c = warp; c < K; c += nw) {
-    float s = 0.f;
-    for (int r = lane; r < K; r += 32) s = fmaf(B[(size_t)c * KS + r], B[(size_t)c * KS + r], s);
-    s = warp_sum(s);
-    if (lane == 0) s_norm[c] = sqrtf(s);
+    __threadfence();
+    ok_s = ok;
   }
   __syncthreads();
-  for (int c = tid; c < K; c += JT) {
+  return ok_s != 0;
+}
+
+__device__ __forceinline__ float bj_sqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double bj_sqrt(double x) { return sqrt(x); }
+
+// One Jacobi rotation of columns x and y (length K) by one warp; returns whether it
+// rotated (the same in every lane).
+template <typename T>
+__device__ __forceinline__ bool rotate_pair(T* x, T* y, int K, T tol, int lane) {
+  T a = 0, b = 0, g = 0;
+  for (int r = lane; r < K; r += 32) {
+    const T xv = x[r], yv = y[r];
+    a = fma(xv, xv, a);
+    b = fma(yv, yv, b);
+    g = fma(xv, yv, g);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+    g += __shfl_xor_sync(0xffffffffu, g, o);
+  }
+  if (!(a > T(0) && b > T(0)) || !(fabs(g) > tol * bj_sqrt(a * b))) return false;
+  const T zeta = (b - a) / (T(2) * g);
+  const T t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + bj_sqrt(T(1) + zeta * zeta));
+  const T c = T(1) / bj_sqrt(T(1) + t * t);
+  const T s = c * t;
+  for (int r = lane; r < K; r += 32) {
+    const T xv = x[r], yv = y[r];
+    x[r] = c * xv - s * yv;
+    y[r] = s * xv + c * yv;
+  }
+  return true;
+}
+
+// player at position pos of round r of the circle schedule of np players (np even)
+__device__ __forceinline__ int circle_player(int pos, int r, int np) {
+  if (pos == 0) return 0;
+  int v = pos - 1 + r;
+  v %= (np - 1);
+  return 1 + v;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(BJ_THREADS, 1) k_block_jacobi(BjParams<T> p) {
+  extern __shared__ __align__(16) unsigned char bj_smem_raw[];
+  T* smem = reinterpret_cast<T*>(bj_smem_raw);
+  __shared__ int s_rot;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int K = p.K, bw = p.bw, np = p.n_blk;
+  unsigned n_bar = 0;
+  // B = R2^T in T precision: column c of B is row c of R2
+  for (long long e = (long long)blockIdx.x * BJ_THREADS + tid; e < (long long)K * K;
+       e += (long long)gridDim.x * BJ_THREADS) {
+    const int c = (int)(e / K), r = (int)(e % K);
+    p.B[(size_t)c * p.ldb + r] = (T)p.R2[e];
+  }
+  if (!bj_grid_sync(p, n_bar)) return;
+  const bool staged = p.ldk > 0;
+  T* sA = smem;
+  T* sB = smem + (size_t)bw * p.ldk;
+  int sweep = 0;
+  bool converged = false;
+  for (; sweep < p.max_sweeps && !converged; ++sweep) {
+    if (tid == 0) s_rot = 0;
+    bool rot = false;
+    for (int rnd = 0; rnd < np - 1; ++rnd) {
+      const int pa = circle_player(blockIdx.x, rnd, np);
+      const int pb = circle_player(np - 1 - blockIdx.x, rnd, np);
+      const int a0 = pa * bw, b0 = pb * bw;
+      const int na = max(0, min(bw, K - a0)), nb = max(0, min(bw, K - b0));
+      T* A = staged ? sA : p.B + (size_t)a0 * p.ldb;
+      T* Bk = staged ? sB : p.B + (size_t)b0 * p.ldb;
+      const int ld = staged ? p.ldk : p.ldb;
+      if (staged) {
+        for (int e = tid; e < na * K; e += BJ_THREADS)
+          sA[(size_t)(e / K) * ld + e % K] = p.B[(size_t)(a0 + e / K) * p.ldb + e % K];
+        for (int e = tid; e < nb * K; e += BJ_THREADS)
+          sB[(size_t)(e / K) * ld + e % K] = p.B[(size_t)(b0 + e / K) * p.ldb + e % K];
+      }
+      __syncthreads();
+      if (rnd == 0) {
+        // pairs inside each of the two blocks: circle schedule of bw (even) players, both
+        // blocks at once (pairs 0..half-1 in A, half..2 half-1 in B)
+        const int bwe = bw + (bw & 1), half = bwe / 2;
+        for (int ir = 0; ir < bwe - 1; ++ir) {
+          for (int q = warp; q < 2 * half; q += BJ_WARPS) {
+            const int which = q / half, j = q % half;
+            int u = circle_player(j, ir, bwe), v = circle_player(bwe - 1 - j, ir, bwe);
+            const int ncol = which ? nb : na;
+            if (u < ncol && v < ncol) {
+              T* base = which ? Bk : A;
+              rot |= rotate_pair(base + (size_t)u * ld, base + (size_t)v * ld, K, p.tol, lane);
+            }
+          }
+          __syncthreads();
+        }
+      }
+      // every column of block A against every column of block B: bw inner rounds of bw
+      // disjoint pairs (j, (j + ir) mod bw)
+      for (int ir = 0; ir < bw; ++ir) {
+        for (int j = warp; j < bw; j += BJ_WARPS) {
+          const int v = (j + ir) % bw;
+          if (j < na && v < nb)
+            rot |= rotate_pair(A + (size_t)j * ld, Bk + (size_t)v * ld, K, p.tol, lane);
+        }
+        __syncthreads();
+      }
+      if (staged) {
+        for (int e = tid; e < na * K; e += BJ_THREADS)
+          p.B[(size_t)(a0 + e / K) * p.ldb + e % K] = sA[(size_t)(e / K) * ld + e % K];
+        for (int e = tid; e < nb * K; e += BJ_THREADS)
+          p.B[(size_t)(b0 + e / K) * p.ldb + e % K] = sB[(size_t)(e / K) * ld + e % K];
+      }
+      if (rnd == np - 2) {
+        if (rot && lane == 0) s_rot = 1;
+        __syncthreads();
+        if (tid == 0 && s_rot) atomicOr(&p.flags[sweep], 1);
+      }
+      if (!bj_grid_sync(p, n_bar)) return;
+    }
+    converged = *(volatile int*)&p.flags[sweep] == 0;
+  }
+  if (!converged && blockIdx.x == 0 && tid == 0) atomicOr(p.status, DEV_NOTCONVERGED);
+  // column norms, then each column's rank among them, S and the normalised columns
+  for (int c = blockIdx.x * BJ_WARPS + warp; c < K; c += gridDim.x * BJ_WARPS) {
+    T s = 0;
+    for (int r = lane; r < K; r += 32) {
+      const T v = p.B[(size_t)c * p.ldb + r];
+      s = fma(v, v, s);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) p.norms[c] = bj_sqrt(s);
+  }
+  if (!bj_grid_sync(p, n_bar)) return;
+  for (int c = blockIdx.x * BJ_WARPS + warp; c < K; c += gridDim.x * BJ_WARPS) {
+    const T v = p.norms[c];
     int rank = 0;
-    const float v = s_norm[c];
-    for (int d = 0; d < K; ++d) {
-      const float u = s_norm[d];
+    for (int d = lane; d < K; d += 32) {
+      const T u = p.norms[d];
       rank += (u > v) || (u == v && d < c);
     }
-    s_rank[c] = rank;
-    Sout[rank] = v;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) rank += __shfl_xor_sync(0xffffffffu, rank, o);
+    if (lane == 0) p.S[rank] = v;
+    const T inv = v > T(0) ? T(1) / v : T(0);
+    for (int r = lane; r < K; r += 32) p.Ut[(size_t)r * K + rank] = p.B[(size_t)c * p.ldb + r] * inv;
   }
-  __syncthreads();
-  for (int e = tid; e < K * K; e += JT) {
-    const int c = e / K, r = e % K;
-    const float nv = s_norm[c];
-    Ut[(size_t)r * K + s_rank[c]] = nv > 0.f ? B[(size_t)c * KS + r] / nv : 0.f;
+}
+
+// Grid of the block ordering: C CTAs, 2C blocks of bw columns.  FP32 rounds are short
+// and latency-bound, so fewer, wider blocks (about 14 columns) keep the barrier count
+// low; FP64 work is bound by the FP64 pipes (two FMA per clock per SM), so it spreads
+// over more SMs with narrow blocks.
+struct BjGrid {
+  int C, bw;
+};
+
+BjGrid bj_grid(int K, bool fp64, int num_sms) {
+  const int target_bw = fp64 ? 2 : 14;
+  int C = std::max(1, (int)ceil_div(K, 2 * target_bw));
+  C = std::min(C, num_sms);
+  int bw = (int)ceil_div(K, 2 * C);
+  return {C, bw};
+}
+
+template <typename T>
+size_t bj_smem(int K, int bw) {
+  const int ldk = (int)round_up(K, 2);
+  return (size_t)2 * bw * ldk * sizeof(T);
+}
+
+template <typename T>
+size_t bj_ws_bytes_t(int K, int num_sms) {
+  const BjGrid g = bj_grid(K, sizeof(T) == 8, num_sms);
+  WsPlan w;
+  w.add<T>((size_t)K * round_up(K, 4));   // B
+  w.add<T>((size_t)K);                     // norms
+  w.add<int>(256);                         // sweep flags
+  w.add<unsigned>(64);                     // barrier
+  (void)g;
+  return w.bytes;
+}
+
+template <typename T>
+ssi_status bj_launch(Workspace& ws, const float* R2, int K, T* Ut, T* S, int* status, int num_sms,
+                     T tol, int max_sweeps, cudaStream_t stream) {
+  const BjGrid g = bj_grid(K, sizeof(T) == 8, num_sms);
+  BjParams<T> p{};
+  p.R2 = R2;
+  p.K = K;
+  p.ldb = (int)round_up(K, 4);
+  p.B = ws.take<T>((size_t)K * p.ldb);
+  p.norms = ws.take<T>((size_t)K);
+  p.flags = ws.take<int>(256);
+  p.bar = ws.take<unsigned>(64);
+  if (!p.B || !p.norms || !p.flags || !p.bar) {
+    set_error("jacobi: workspace too small");
+    return SSI_E_NOMEM;
   }
+  p.n_blk = 2 * g.C;
+  p.bw = g.bw;
+  p.tol = tol;
+  p.max_sweeps = std::min(max_sweeps, 256);
+  p.Ut = Ut;
+  p.S = S;
+  p.status = status;
+  size_t smem = bj_smem<T>(K, g.bw);
+  if (smem > BJ_SMEM_MAX) {
+    smem = 0;
+    p.ldk = 0;   // the blocks stay in global memory (L2-resident)
+  } else {
+    p.ldk = (int)round_up(K, 2);
+  }
+  SSI_CUDA(cudaMemsetAsync(p.flags, 0, 256 * sizeof(int), stream));
+  SSI_CUDA(cudaMemsetAsync(p.bar, 0, 64 * sizeof(unsigned), stream));
+  SSI_CUDA(cudaFuncSetAttribute(k_block_jacobi<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)BJ_SMEM_MAX));
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(g.C);
+  cfg.blockDim = dim3(BJ_THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  SSI_CUDA(cudaLaunchKernelEx(&cfg, k_block_jacobi<T>, p));
+  return SSI_OK;
 }
 
 }  // namespace
 
-constexpr size_t JACOBI_SMEM_MAX = 216 * 1024;
-
-size_t jacobi_ws_bytes(int K) {
-  WsPlan w;
-  if ((size_t)K * col_stride(K) * sizeof(float) > JACOBI_SMEM_MAX) w.add<float>((size_t)K * col_stride(K));
-  return w.bytes;
+size_t jacobi_ws_bytes(int K, int num_sms, bool fp64) {
+  return fp64 ? bj_ws_bytes_t<double>(K, num_sms) : bj_ws_bytes_t<float>(K, num_sms);
 }
 
+// FP32: stop at |b_p^T b_q| <= 1e-5 ||b_p|| ||b_q|| (30 sweeps at most); FP64: 1e-13
+// (the rounding of an FP64 dot product of length K is about sqrt(K) 1e-16).
 ssi_status jacobi_launch(Workspace& ws, const float* R2, int K, float* Ut, float* S, int* status,
-                         cudaStream_t stream) {
-  if (K > 512) {
-    set_error("jacobi: K=%d > 512", K);
-    return SSI_E_INVALID;
-  }
-  const size_t bytes = (size_t)K * col_stride(K) * sizeof(float);
-  float* Bg = nullptr;
-  size_t smem = 0;
-  if (bytes > JACOBI_SMEM_MAX) {
-    Bg = ws.take<float>((size_t)K * col_stride(K));
-    if (!Bg) {
-      set_error("jacobi: workspace too small");
-      return SSI_E_NOMEM;
-    }
-  } else {
-    smem = bytes;
-    SSI_CUDA(cudaFuncSetAttribute(k_jacobi_svd<29>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)JACOBI_SMEM_MAX));
-  }
-  if (K <= 232)
-    k_jacobi_svd<29><<<1, JT, smem, stream>>>(R2, K, Bg, 1e-5f, 30, Ut, S, status);
-  else
-    k_jacobi_svd<64><<<1, JT, smem, stream>>>(R2, K, Bg, 1e-5f, 30, Ut, S, status);
-  SSI_CUDA(cudaGetLastError());
-  return SSI_OK;
+                         int num_sms, cudaStream_t stream) {
+  return bj_launch<float>(ws, R2, K, Ut, S, status, num_sms, 1e-5f, 30, stream);
+}
+
+ssi_status jacobi_launch64(Workspace& ws, const float* R2, int K, double* Ut, double* S, int* status,
+                           int num_sms, cudaStream_t stream) {
+  return bj_launch<double>(ws, R2, K, Ut, S, status, num_sms, 1e-13, 40, stream);
 }
 
 }  // namespace ssi

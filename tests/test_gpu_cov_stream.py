@@ -83,7 +83,8 @@ def test_stream_matches_whole_window_after_every_push(P, ctx, rec, prec):
 
 def test_stream_smallest_window_and_long_drift(P, ctx, rec):
     """Window of max_lag + 1 samples slid by whole windows; then 300 pushes of 150 samples
-    through a 3000-sample window (the sums are updated 300 times and never recomputed)."""
+    through a 3000-sample window (the sums are updated 300 times and rebuilt from the ring
+    after every 3000 samples pushed)."""
     K = 39
     _, _, n, worst, _ = _run(P, ctx, rec, K, K + 1, K + 1, [K + 1] * 30, "split_bf16")
     assert n == K + 1 and worst < TOL, worst
@@ -91,6 +92,37 @@ def test_stream_smallest_window_and_long_drift(P, ctx, rec):
                                   every=50)
     assert pushes == 300 and n == 3000 and worst < TOL, worst
     Ro = O.covariances(rec[:, t - n:t].astype(np.float64), K)
+    assert _err(R, Ro) < TOL
+
+
+def test_stream_thousands_of_pushes_with_rebuilds(P, ctx):
+    """3000 pushes of 50 samples through a 4000-sample window (75 windows; the ring of
+    4050 columns wraps at almost every push).  The sums are rebuilt from the ring every
+    4000 samples and, in between, whenever ssi_cov_stream_refresh is called; after each
+    refresh and every 250 pushes R must equal ssi_covariances of the window, and the final
+    window the FP64 oracle's covariances, within the stage (a) bound."""
+    w = S.workload("bridge186_3d", l=24, modes=6, f_lo=4.0, N=150000 + 64, seed=11)
+    Y, *_ = S.record(w, np.float32)
+    Yd = torch.from_numpy(np.ascontiguousarray(Y)).cuda()
+    K, W, B = 39, 4000, 50
+    st = P.CovStream(ctx, 24, K, W, B, "split_bf16")
+    worst, t = 0.0, 0
+    try:
+        for j in range(3000):
+            st.push(Yd[:, t:t + B].contiguous())
+            t += B
+            if j % 37 == 36:
+                st.refresh()
+            if j % 37 == 36 or j % 250 == 249:
+                R, n = st.covariances()
+                ref = P.ssi_covariances(ctx, Yd[:, t - n:t].contiguous(), K, "split_bf16")
+                worst = max(worst, _err(R.cpu().numpy(), ref.cpu().numpy()))
+        R, n = st.covariances()
+        R = R.cpu().numpy()
+    finally:
+        st.close()
+    assert n == W and worst < TOL, worst
+    Ro = O.covariances(Y[:, t - n:t].astype(np.float64), K)
     assert _err(R, Ro) < TOL
 
 

@@ -40,11 +40,11 @@ def test_omega_matches_oracle_philox(P, ctx):
         assert np.abs(g - o).max() < 2e-5
 
 
-def _rsvd_case(P, ctx, R, l, i, k, p, q, seed, prec):
+def _rsvd_case(P, ctx, R, l, i, k, p, q, seed, prec, small="fp32"):
     Rd = torch.from_numpy(np.ascontiguousarray(R)).cuda()
-    U, Sv = P.ssi_toeplitz_rsvd(ctx, Rd, l, i, k, p, q, seed, prec)
-    torch.cuda.synchronize()
-    return U.cpu().numpy().astype(np.float64), Sv.cpu().numpy().astype(np.float64)
+    U, Sv = P.ssi_toeplitz_rsvd(ctx, Rd, l, i, k, p, q, seed, prec, small)
+    P.check_sync(ctx)
+    return U.cpu().numpy(), Sv.cpu().numpy()
 
 
 @pytest.mark.parametrize("prec", ["split_bf16", "fp32"])
@@ -67,48 +67,77 @@ def _oracle_rsvd_case(l, i, k, p, q):
     return R, s_ref
 
 
-@pytest.mark.parametrize("prec", ["split_bf16", "fp32"])
+@pytest.mark.parametrize("prec,small", [("split_bf16", "fp32"), ("fp32", "fp32"),
+                                        ("split_bf16", "fp64")])
 @pytest.mark.parametrize("l,i,k,p,q", [(24, 10, 40, 10, 2), (70, 7, 60, 20, 1), (9, 30, 30, 6, 3),
                                        (64, 10, 300, 20, 1)])
-def test_rsvd_matches_oracle_rsvd(P, ctx, prec, l, i, k, p, q):
-    """Same Omega (Philox) on both sides: leading singular values agree to 1e-4.  The
-    K = 320 case runs the Jacobi SVD of the small matrix from global memory."""
+def test_rsvd_matches_oracle_rsvd(P, ctx, prec, small, l, i, k, p, q):
+    """Same Omega (Philox) on both sides: leading singular values agree to 1e-4, in both
+    small-problem precisions (the K x K Jacobi SVD in FP32 or FP64)."""
     R, s_ref = _oracle_rsvd_case(l, i, k, p, q)
-    U, s = _rsvd_case(P, ctx, R, l, i, k, p, q, 5, prec)
+    U, s = _rsvd_case(P, ctx, R, l, i, k, p, q, 5, prec, small)
     lead = 16
     assert np.allclose(s[:lead], s_ref[:lead], rtol=1e-4), np.abs(s[:lead] / s_ref[:lead] - 1).max()
     G = U.T @ U
     assert np.abs(G - np.eye(k)).max() < 2e-4
 
 
-def _realize(P, ctx, Us, lags, l, k, orders, dt):
-    Ud = [torch.from_numpy(np.ascontiguousarray(U, dtype=np.float32)).cuda() for U in Us]
-    poles, phi = P.ssi_realize_batch(ctx, lags, Ud, l, k, orders, dt)
-    torch.cuda.synchronize()
+@functools.lru_cache(maxsize=None)
+def _wide_case(l, i):
+    rec = S.bridge_record(l, 10, 1.0, 12.0, 50.0, 60000, 0.05, seed=3 * l + i)
+    R = O.covariances(rec.Y, 2 * i - 1)
+    # leading singular values of T by the oracle's RSVD with three power iterations
+    _, s_ref = O.rsvd(O.block_toeplitz(R, i), 48, 16, 3, seed=9)
+    return R, s_ref
+
+
+@pytest.mark.parametrize("l,i,small", [(32, 32, "fp32"), (64, 32, "fp32"), (32, 32, "fp64")])
+def test_rsvd_full_width_above_512(P, ctx, l, i, small):
+    """The range finder at full width K = L = 1024 and 2048 (no sketching error): the
+    K x K Jacobi runs on the cooperative grid with 74 (FP32, 1024), 147 (FP32, 2048) or
+    152 (FP64) CTAs.  The leading 16 singular values match the oracle's converged RSVD of
+    the same T to 1e-4 and U has orthonormal columns."""
+    R, s_ref = _wide_case(l, i)
+    L = l * i
+    U, s = _rsvd_case(P, ctx, R, l, i, L, 0, 0, 7, "split_bf16", small)
+    assert np.allclose(s[:16], s_ref[:16], rtol=1e-4), np.abs(s[:16] / s_ref[:16] - 1).max()
+    assert np.all(np.diff(s) <= 0)
+    G = U[:, :64].T @ U[:, :64]
+    assert np.abs(G - np.eye(64)).max() < 2e-4
+
+
+def _realize(P, ctx, Us, lags, l, k, orders, dt, small="fp32"):
+    Ud = [torch.from_numpy(np.ascontiguousarray(U, dtype=np.float64)).cuda() for U in Us]
+    poles, phi = P.ssi_realize_batch(ctx, lags, Ud, l, k, orders, dt, small)
+    P.check_sync(ctx)
     return P.poles_to_numpy(poles), phi.cpu().numpy()
 
 
-def test_realize_recovers_exact_modes_from_model_covariances(P, ctx):
+@pytest.mark.parametrize("small", ["fp32", "fp64"])
+def test_realize_recovers_exact_modes_from_model_covariances(P, ctx, small):
     model = S.chain_model(S.workload("chain4_tiny"))
     T = O.block_toeplitz(S.model_covariances(model, 39)[1:], 20)
     U, s = O.full_svd(T)
-    rec, phi = _realize(P, ctx, [U[:, :8]], [20], 4, 8, [2, 4, 6, 8], model.dt)
+    rec, phi = _realize(P, ctx, [U[:, :8]], [20], 4, 8, [2, 4, 6, 8], model.dt, small)
     cells = gpu_cells(rec, phi, [20], [2, 4, 6, 8], 4)
     c8 = cells[0][3]
     assert len(c8["f"]) == 4
-    assert np.allclose(c8["f"], model.f_true, rtol=2e-5)
-    assert np.allclose(c8["xi"], model.xi_true, atol=2e-4)
+    # FP64: the modes of the model to the precision of the output records (FP32)
+    rtol, atol = (2e-5, 2e-4) if small == "fp32" else (1e-6, 1e-6)
+    assert np.allclose(c8["f"], model.f_true, rtol=rtol)
+    assert np.allclose(c8["xi"], model.xi_true, atol=atol)
     for j in range(4):
         assert O.mac(c8["Phi"][:, j], model.phi_true[:, j]) > 0.9999
 
 
-def test_realize_matches_oracle_on_noisy_chain(P, ctx):
+@pytest.mark.parametrize("small", ["fp32", "fp64"])
+def test_realize_matches_oracle_on_noisy_chain(P, ctx, small):
     w = S.workload("chain4_tiny")
     Y, f_true, _, phi_true = S.record(w)
     T = O.block_toeplitz(O.covariances(Y, 39), 20)
     U, s = O.full_svd(T)
     orders = list(range(2, 41, 2))
-    rec, phi = _realize(P, ctx, [U[:, :40]], [20], 4, 40, orders, 0.01)
+    rec, phi = _realize(P, ctx, [U[:, :40]], [20], 4, 40, orders, 0.01, small)
     gpu = gpu_cells(rec, phi, [20], orders, 4)
     ora = [[]]
     for n in orders:
@@ -180,14 +209,15 @@ def test_stabilize_flags_match_oracle_on_shared_poles(P, ctx):
     assert n_checked > 50
 
 
-@pytest.mark.parametrize("prec", ["split_bf16", "fp32"])
-def test_full_solve_chain_matches_oracle(P, ctx, prec):
+@pytest.mark.parametrize("prec,small", [("split_bf16", "fp32"), ("fp32", "fp32"),
+                                        ("split_bf16", "fp64")])
+def test_full_solve_chain_matches_oracle(P, ctx, prec, small):
     """Complete solve of the 4-channel chain record (i = 20, full width k = 80, orders 2..40)."""
     w = S.workload("chain4_tiny")
     Y, f_true, _, phi_true = S.record(w, np.float32)
     orders = w["orders"]
     desc = P.job_desc(torch.from_numpy(Y).cuda(), w["fs"], w["lags"], orders, k=40, oversample=40,
-                      q=0, prec=prec, seed=1)
+                      q=0, prec=prec, seed=1, small=small)
     poles, phi, Sg = P.ssi_solve(ctx, desc)
     P.check_sync(ctx)
     rec = P.poles_to_numpy(poles)
@@ -259,7 +289,8 @@ def test_3d_diagram_matches_oracle(P, ctx):
     assert n_flag >= 24
 
 
-def test_realize_orders_above_shared_memory_recover_model_modes(P, ctx):
+@pytest.mark.parametrize("small", ["fp32", "fp64"])
+def test_realize_orders_above_shared_memory_recover_model_modes(P, ctx, small):
     """Orders above 224 run with A in global scratch, and k = 240 factors each lag in
     global scratch too.  From the exact covariances of a 240-state model (120-storey shear
     chain, 2 % modal damping, white forces at every storey, accelerations of every storey)
@@ -273,7 +304,7 @@ def test_realize_orders_above_shared_memory_recover_model_modes(P, ctx):
     U, s = O.full_svd(T)
     assert s[239] > 1e-9 * s[0] and s[240] < 1e-9 * s[0]   # rank 240 = 2 x 120 modes
     orders = [200, 230, 240]
-    rec, phi = _realize(P, ctx, [U[:, :240]], [i], 120, 240, orders, model.dt)
+    rec, phi = _realize(P, ctx, [U[:, :240]], [i], 120, 240, orders, model.dt, small)
     cells = gpu_cells(rec, phi, [i], orders, 120)
     c240 = cells[0][2]
     assert len(c240["f"]) == 120
@@ -284,6 +315,8 @@ def test_realize_orders_above_shared_memory_recover_model_modes(P, ctx):
     lam = -model.xi_true * w_true + 1j * w_true * np.sqrt(1 - model.xi_true ** 2)
     mu_true = np.exp(lam * model.dt)
     assert np.abs(mu_gpu - mu_true).max() < 1e-4, np.abs(mu_gpu - mu_true).max()
+    if small == "fp64":   # FP64 eigenvalues, rounded once to the FP32 records
+        assert np.abs(mu_gpu - mu_true).max() < 2e-7, np.abs(mu_gpu - mu_true).max()
     # f and xi amplify d mu by 1 / (omega dt): the lowest modes (mu within 0.01 of 1) get
     # looser gates, the modes above 1 Hz the parity gates
     hi = model.f_true >= 1.0
