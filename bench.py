@@ -79,6 +79,9 @@ def parse():
     ap.add_argument("--no-fp64-small", action="store_true")
     ap.add_argument("--no-3d", action="store_true")
     ap.add_argument("--no-mix", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--rank-jb-max", type=int, default=1000,
+                    help="largest time-lag step of --workload rank_study")
     ap.add_argument("--inflight", type=int, default=4,
                     help="solves in flight at once, each on its own stream and context")
     return ap.parse_args()
@@ -615,6 +618,55 @@ def run_frame10_table2(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def run_rank_study(args, world, rank):
+    """The parametric analysis of Sec. 3.1 on the 10-DOF frame: for SNR 10, 15, 20 and
+    25 dB (5-minute records at 200 Hz) and j_b = 100, 200, ..., --rank-jb-max (T = 10 j_b),
+    the minimum rank kbar (percent of T, on a 2.5 % grid) at which the RSVD identification
+    (q = 0, orders 10..100) matches the SVD's (paper_2411_05510_gb300/rank_study.py).
+    Beside the points: Eq. (empirical_formula) and the least-squares line through them,
+    as the paper fits its line before shifting its intercept to 30 %.  Rank 0 only."""
+    import torch
+    import paper_2411_05510_gb300 as P
+    from paper_2411_05510_gb300 import rank_study as RS
+    if rank != 0:
+        return
+    ctx = P.Context(0)
+    orders = list(range(10, 101, 2))
+    grid = RS.rank_grid(2.5, 60.0, 2.5)
+    jbs = list(range(100, args.rank_jb_max + 1, 100))
+    points, t0 = [], time.perf_counter()
+    for snr in (10, 15, 20, 25):
+        w = S.workload("frame10", noise=10 ** (-snr / 20), seed=200 + snr)
+        Y, *_ = S.record(w, np.float32)
+        Yd = torch.from_numpy(Y).cuda()
+        for jb in jbs:
+            T = Y.shape[0] * jb
+            ts = time.perf_counter()
+            kbar, ref, trace = RS.minimum_rank(ctx, Yd, w["fs"], jb, orders, grid, seed=1)
+            points.append({"snr_db": snr, "jb": jb, "T": T, "kbar_pct": kbar,
+                           "modes_svd": len(ref), "trace": trace,
+                           "seconds": round(time.perf_counter() - ts, 2)})
+    ctx.close()
+    xs = np.array([p["T"] for p in points if p["kbar_pct"] is not None], float)
+    ys = np.array([p["kbar_pct"] for p in points if p["kbar_pct"] is not None], float)
+    fit = None
+    if len(xs) >= 2:
+        b, a = np.polyfit(xs, ys, 1)
+        fit = {"intercept_pct": float(a), "slope_pct_per_T": float(b)}
+    line = {"metric": "minimum RSVD rank kbar (percent of T), 10-DOF frame (Sec. 3.1)",
+            "unit": "percent", "workload": "rank_study",
+            "config": {"fs": 200.0, "N": 60000, "snr_db": [10, 15, 20, 25], "jb": jbs,
+                       "orders": "10..100 step 2", "grid_pct": [grid[0], grid[-1], 2.5],
+                       "q": 0, "oversample": 0, "match_tol": [0.01, 0.01, 0.02],
+                       "sc": [0.02, 0.02, 0.05], "hc": [0.10, 0.6, 0.5],
+                       "svd": "range finder at full width (K = T)"},
+            "points": points, "least_squares_line": fit,
+            "eq_empirical_formula": {str(p["T"]): max(30 - 0.00156 * p["T"], 25.0)
+                                     for p in points},
+            "total_s": round(time.perf_counter() - t0, 1)}
+    print(json.dumps(line), flush=True)
+
+
 def l2_note(w):
     mb = w.get("l", w.get("n_dof", 0)) * w["N"] * 4 / 1e6
     if mb > 129:
@@ -651,6 +703,9 @@ def main():
         return
     if args.workload == "frame10_table2":
         run_frame10_table2(args, world, rank)
+        return
+    if args.workload == "rank_study":
+        run_rank_study(args, world, rank)
         return
 
     import torch
@@ -733,7 +788,17 @@ def main():
             P.check_sync(ln["ctx"], dev)
         return e0.elapsed_time(e1), [a.elapsed_time(b2) for a, b2 in st]
 
+    def autotune(ls):
+        """The library's autotuner on lane 0, its choices copied to the other lanes."""
+        if args.no_autotune:
+            return None
+        t = P.ssi_autotune(ls[0]["ctx"], ls[0]["desc"])
+        for ln in ls[1:]:
+            P.ssi_tuning_set(ln["ctx"], ln["desc"], t)
+        return t
+
     lanes = make_lanes(args.prec)
+    tuning = autotune(lanes)
     warm(lanes)
     for ln in lanes:
         ln["ctx"].profile_read()   # drop warm-up records
@@ -810,6 +875,7 @@ def main():
                          "traffic_note": tnote},
             "stages_ms_per_step": {k: v / n_ser for k, v in stage_ms.items()},
             "gpu_launches": launches,
+            "autotune": tuning,
             "modes_found": f"{found}/{len(f_true)}",
         }
         if not args.no_clocks:
@@ -926,6 +992,7 @@ def main():
     def measure(prec, small="fp32", wl=None, n_solves=None, Ydev=None, stages=True):
         """solves/s with J in flight, p50/p99 latency, the serial latency and its stages."""
         ls = make_lanes(prec, small, wl, Ydev)
+        tv = autotune(ls)
         saved_warmup = args.warmup
         args.warmup = 1
         warm(ls)
@@ -947,6 +1014,8 @@ def main():
                "serial_latency_ms": pct(mss, 50)}
         if stages:
             res["stages_ms_per_step"] = {k: v / 3 for k, v in st_ms.items() if v > 0}
+        if tv is not None:
+            res["autotune"] = tv
         for ln in ls:
             ln["ctx"].close()
         return res

@@ -385,6 +385,31 @@ ssi_status ssi_job_sizes(const ssi_job_desc* job, int64_t* n_slots, int64_t* phi
 ssi_status ssi_solve(ssi_ctx* ctx, const ssi_job_desc* job, ssi_pole* poles, float* phi,
                      double* S_out, void* stream);
 
+/* ------------------------------------------------------------------------------
+ * Autotuner of a job shape's plan choices (the batching pattern: tile and split shapes
+ * picked from timed candidates; the paper has no counterpart).  Three choices are made
+ * by cost models otherwise: the lag GEMM's samples per time split, the Toeplitz GEMMs'
+ * reduction splits and the K x K Jacobi's columns per block.  ssi_autotune runs solves of
+ * `job` (its record included) on an internal stream, one choice at a time, each
+ * candidate once untimed and twice timed by the stage profiler, keeps the fastest, and
+ * stores the three values in the context under the job's shape (l, N, lags, k,
+ * oversample, precisions); later ssi_solve calls and serving jobs of that shape use them.
+ * The results change only by rounding (the split and block structure orders the sums).
+ * Synchronous; call it before serving starts.  ssi_tuning_get returns the stored values
+ * (SSI_E_NOTFOUND if the shape was never tuned); ssi_tuning_set stores values, e.g. those
+ * tuned on another context (0 = the model's choice).
+ * ---------------------------------------------------------------------------- */
+typedef struct {
+  int32_t cov_rows_per_split;   /* lag GEMM: samples per FP32 partial sum */
+  int32_t sketch_splits;        /* Toeplitz GEMMs: reduction splits */
+  int32_t jacobi_block;         /* K x K Jacobi: columns per block */
+  int32_t reserved;
+  double stage_ms[3];           /* ms per solve of each stage with the chosen value */
+} ssi_tuning;
+ssi_status ssi_autotune(ssi_ctx* ctx, const ssi_job_desc* job, ssi_tuning* out);
+ssi_status ssi_tuning_get(ssi_ctx* ctx, const ssi_job_desc* job, ssi_tuning* out);
+ssi_status ssi_tuning_set(ssi_ctx* ctx, const ssi_job_desc* job, const ssi_tuning* in);
+
 /* Synchronise `stream` and report device-side status raised by earlier asynchronous
  * calls of this context on it (SSI_E_TIMEOUT for a bounded wait that ran out,
  * SSI_E_NOTCONVERGED for an iteration cap).  Clears the status. */

@@ -69,6 +69,12 @@ class SsiJobDesc(ctypes.Structure):
                 ("reserved", ctypes.c_int32)]
 
 
+class SsiTuning(ctypes.Structure):
+    _fields_ = [("cov_rows_per_split", ctypes.c_int32), ("sketch_splits", ctypes.c_int32),
+                ("jacobi_block", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("stage_ms", ctypes.c_double * 3)]
+
+
 _c = ctypes
 _P = ctypes.c_void_p
 # name -> (restype, argtypes): the full exported surface of include/ssi.h
@@ -106,6 +112,9 @@ PROTOTYPES = {
                                  _c.POINTER(_c.c_int64)]),
     "ssi_solve": (_c.c_int, [_P, _c.POINTER(SsiJobDesc), _P, _P, _P, _P]),
     "ssi_sync_status": (_c.c_int, [_P, _P]),
+    "ssi_autotune": (_c.c_int, [_P, _c.POINTER(SsiJobDesc), _c.POINTER(SsiTuning)]),
+    "ssi_tuning_get": (_c.c_int, [_P, _c.POINTER(SsiJobDesc), _c.POINTER(SsiTuning)]),
+    "ssi_tuning_set": (_c.c_int, [_P, _c.POINTER(SsiJobDesc), _c.POINTER(SsiTuning)]),
     "ssi_serve_config": (_c.c_int, [_P, _c.c_int, _c.c_int]),
     "ssi_submit": (_c.c_int, [_P, _c.POINTER(SsiJobDesc), _c.POINTER(_c.c_uint64)]),
     "ssi_poll": (_c.c_int, [_P, _c.c_uint64, _c.c_int, _c.POINTER(_P), _c.POINTER(_P),

@@ -14,14 +14,15 @@ import torch
 
 from . import _lib
 from ._lib import (SSI_PREC_FP32, SSI_PREC_SPLIT_BF16, SSI_SMALL_FP32, SSI_SMALL_FP64, SsiClusterInfo,
-                   SsiClusterParams, SsiJobDesc, SsiMode, SsiStabParams, check, lib)
+                   SsiClusterParams, SsiJobDesc, SsiMode, SsiStabParams, SsiTuning, check, lib)
 
 __all__ = [
     "Context", "PREC", "ssi_covariances", "ssi_gaussian_omega", "ssi_toeplitz_rsvd",
     "ssi_realize_batch", "ssi_stabilize", "ssi_solve", "ssi_pole_slots", "poles_to_numpy",
     "stab_params", "job_desc", "ssi_rank_rule", "ssi_lag_rule", "ssi_time_lag", "check_sync",
     "ssi_job_sizes", "ssi_serve_config", "ssi_submit", "ssi_poll", "ssi_release",
-    "cluster_params", "ssi_cluster", "CovStream",
+    "cluster_params", "ssi_cluster", "CovStream", "ssi_autotune", "ssi_tuning_get",
+    "ssi_tuning_set",
 ]
 
 PREC = {"fp32": SSI_PREC_FP32, "split_bf16": SSI_PREC_SPLIT_BF16}
@@ -288,6 +289,30 @@ def ssi_solve(ctx: Context, desc: SsiJobDesc, device="cuda", with_s: bool = True
                         ctypes.c_void_p(S.data_ptr() if S is not None else 0),
                         _stream(torch.device(device))), "ssi_solve")
     return poles, phi, S
+
+
+def _tuning_dict(t: SsiTuning) -> dict:
+    return {"cov_rows_per_split": t.cov_rows_per_split, "sketch_splits": t.sketch_splits,
+            "jacobi_block": t.jacobi_block, "stage_ms": [t.stage_ms[i] for i in range(3)]}
+
+
+def ssi_autotune(ctx: Context, desc: SsiJobDesc) -> dict:
+    """Time candidate plan choices on solves of the job and store the fastest in ctx."""
+    t = SsiTuning()
+    check(lib.ssi_autotune(ctx.ptr, ctypes.byref(desc), ctypes.byref(t)), "ssi_autotune")
+    return _tuning_dict(t)
+
+
+def ssi_tuning_get(ctx: Context, desc: SsiJobDesc) -> dict:
+    t = SsiTuning()
+    check(lib.ssi_tuning_get(ctx.ptr, ctypes.byref(desc), ctypes.byref(t)), "ssi_tuning_get")
+    return _tuning_dict(t)
+
+
+def ssi_tuning_set(ctx: Context, desc: SsiJobDesc, tuning: dict) -> None:
+    t = SsiTuning(int(tuning.get("cov_rows_per_split", 0)), int(tuning.get("sketch_splits", 0)),
+                  int(tuning.get("jacobi_block", 0)), 0)
+    check(lib.ssi_tuning_set(ctx.ptr, ctypes.byref(desc), ctypes.byref(t)), "ssi_tuning_set")
 
 
 def ssi_serve_config(ctx: Context, max_slots: int = 2, max_queue: int = 64) -> None:

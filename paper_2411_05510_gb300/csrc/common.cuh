@@ -11,6 +11,8 @@
 #include <mutex>
 #include <tuple>
 #include <vector>
+#include <map>
+#include <array>
 
 #include "../../include/ssi.h"
 
@@ -100,6 +102,10 @@ struct ssi_ctx {
   bool prof_on = false;               // per-stage CUDA-event timers
   std::mutex prof_mu;
   std::vector<std::tuple<int, cudaEvent_t, cudaEvent_t>> prof_recs;
+  // autotuned plan choices per job shape (ssi_autotune): lag-GEMM samples per split,
+  // Toeplitz GEMM splits, Jacobi columns per block (0 = the model's choice)
+  std::mutex tune_mu;
+  std::map<std::string, std::array<int, 3>> tuned;
 };
 
 namespace ssi {
@@ -123,9 +129,10 @@ struct CovPlan {
   int rows_per_split, n_split;
   size_t ws_bytes;
 };
-// max_ws: largest workspace the plan may need (the time split is coarsened to fit)
+// max_ws: largest workspace the plan may need (the time split is coarsened to fit);
+// rows > 0: samples per time split chosen by the caller (the autotuner) instead of the model
 CovPlan cov_plan(int l, int64_t N, int max_lag, ssi_precision prec, int num_sms,
-                 size_t max_ws = SIZE_MAX);
+                 size_t max_ws = SIZE_MAX, int64_t rows = 0);
 // acc == nullptr: R = covariances of Y; otherwise acc (double-float hi/lo pairs, same
 // layout as R) += acc_sign * the unnormalised lag sums sum_t y_{t+k} y_t^T and R is unused
 // (accumulation over segments)
@@ -135,9 +142,13 @@ ssi_status covariances_ws(ssi_ctx* ctx, Workspace& ws, const CovPlan& plan, cons
 
 struct RsvdPlan {
   int l, l_pad, i, k, K, Kp, q, L, L_pad;
+  int tg_splits;        // reduction splits of the Toeplitz GEMMs
+  int jacobi_block;     // columns per block of the K x K Jacobi (0: the model's choice)
   size_t ws_bytes;
 };
-RsvdPlan rsvd_plan(int l, int i, int k, int oversample, int q, int num_sms);
+// splits > 0 / jacobi_block > 0: values chosen by the caller (the autotuner)
+RsvdPlan rsvd_plan(int l, int i, int k, int oversample, int q, int num_sms, int splits = 0,
+                   int jacobi_block = 0);
 // shared_device: other work (another lag of the same solve) runs beside this one, so the
 // QR takes the half-device grid
 // small64: FP64 Jacobi and U = Q U~ in FP64 (U, S double); otherwise FP32, written as

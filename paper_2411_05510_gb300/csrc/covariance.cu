@@ -481,7 +481,8 @@ ssi_status launch_tc(const CUtensorMap& thi, const CUtensorMap& tlo, const LagGe
 
 }  // namespace
 
-CovPlan cov_plan(int l, int64_t N, int max_lag, ssi_precision prec, int num_sms, size_t max_ws) {
+CovPlan cov_plan(int l, int64_t N, int max_lag, ssi_precision prec, int num_sms, size_t max_ws,
+                 int64_t rows_req) {
   CovPlan c{};
   c.ldy = N;
   c.l = l;
@@ -515,7 +516,13 @@ CovPlan cov_plan(int l, int64_t N, int max_lag, ssi_precision prec, int num_sms,
   int64_t best_rows = 0, best_cost = 0;
   const int64_t s_lo = std::max<int64_t>(1, ceil_div(N, 16384));
   const int64_t s_hi = std::max<int64_t>(s_lo, ceil_div(N, 512));
-  for (int64_t sp = s_lo; sp <= s_hi; ++sp) {
+  if (rows_req > 0) {
+    // the caller's split length, kept within the FP32 partial-sum bound of 16384 samples
+    const int64_t rows = std::min<int64_t>(16384, std::max<int64_t>(512, round_up(rows_req, BT)));
+    if (ws_of(ceil_div(N, rows)) <= max_ws) best_rows = rows;
+  }
+  const bool fixed = best_rows > 0;
+  for (int64_t sp = s_lo; sp <= s_hi && !fixed; ++sp) {
     const int64_t rows = std::max<int64_t>(512, round_up(ceil_div(N, sp), BT));
     const int64_t n_sp = ceil_div(N, rows);
     if (sp > s_lo && ws_of(n_sp) > max_ws) continue;

@@ -2,6 +2,7 @@
 // planning of its device memory.  Used directly by ssi_solve and by the serving
 // scheduler (serving.cpp).
 #include <algorithm>
+#include <string>
 #include <vector>
 
 #include "common.cuh"
@@ -39,15 +40,32 @@ ssi_status validate_job(const ssi_job_desc* j) {
   return SSI_OK;
 }
 
-JobPlan plan_job(const ssi_job_desc* j, int num_sms) {
+std::string job_shape_key(const ssi_job_desc* j) {
+  std::string key = std::to_string(j->l) + ":" + std::to_string(j->N) + ":" + std::to_string(j->k) +
+                    ":" + std::to_string(j->oversample) + ":" + std::to_string(j->prec) + ":" +
+                    std::to_string(j->small) + ":";
+  for (int t = 0; t < j->n_lags; ++t) key += std::to_string(j->lags[t]) + ",";
+  return key;
+}
+
+JobPlan plan_job(const ssi_job_desc* j, ssi_ctx* ctx, const std::array<int, 3>* tune) {
+  const int num_sms = ctx->num_sms;
+  std::array<int, 3> tv{0, 0, 0};
+  if (tune) {
+    tv = *tune;
+  } else {
+    std::lock_guard<std::mutex> g(ctx->tune_mu);
+    auto it = ctx->tuned.find(job_shape_key(j));
+    if (it != ctx->tuned.end()) tv = it->second;
+  }
   JobPlan p{};
   p.max_lag = 2 * j->lags[j->n_lags - 1] - 1;
-  p.cov = cov_plan(j->l, j->N, p.max_lag, (ssi_precision)j->prec, num_sms);
+  p.cov = cov_plan(j->l, j->N, p.max_lag, (ssi_precision)j->prec, num_sms, SIZE_MAX, tv[0]);
   size_t ws = p.cov.ws_bytes;
   // the RSVDs of several lags run at once, each in its own region of the scratch
   size_t rs_total = 0;
   for (int t = 0; t < j->n_lags; ++t) {
-    p.rs.push_back(rsvd_plan(j->l, j->lags[t], j->k, j->oversample, j->q, num_sms));
+    p.rs.push_back(rsvd_plan(j->l, j->lags[t], j->k, j->oversample, j->q, num_sms, tv[1], tv[2]));
     p.rs_off.push_back(rs_total);
     rs_total += (p.rs.back().ws_bytes + 255) & ~size_t(255);
   }
@@ -218,7 +236,7 @@ extern "C" ssi_status ssi_solve(ssi_ctx* ctx, const ssi_job_desc* job, ssi_pole*
   SSI_TRY(validate_job(job));
   SSI_CUDA(cudaSetDevice(ctx->device));
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  JobPlan p = plan_job(job, ctx->num_sms);
+  JobPlan p = plan_job(job, ctx);
   JobBuffers& B = ctx_solve_buffers(ctx);
   SSI_TRY(buffers_reserve(ctx, B, p, s));
   return run_job(ctx, job, p, B, poles, phi, S_out, s);

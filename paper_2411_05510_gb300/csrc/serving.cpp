@@ -294,7 +294,7 @@ extern "C" ssi_status ssi_submit(ssi_ctx* ctx, const ssi_job_desc* job, uint64_t
   j->orders.assign(job->orders, job->orders + job->n_orders);
   j->desc.lags = j->lags.data();
   j->desc.orders = j->orders.data();
-  j->plan = plan_job(&j->desc, ctx->num_sms);
+  j->plan = plan_job(&j->desc, ctx);
   j->t_submit = Clock::now();
   std::lock_guard<std::mutex> g(sv->mu);
   if ((int)sv->queue.size() >= sv->max_queue) {

@@ -26,9 +26,9 @@ ssi_status qr_launch(ssi_ctx* ctx, Workspace& ws, float* A, int rows, int ncols,
                      float* Rout, int* status, cudaStream_t stream, bool shared_device);
 size_t jacobi_ws_bytes(int K, int num_sms, bool fp64);
 ssi_status jacobi_launch64(Workspace& ws, const float* R2, int K, double* Ut, double* S, int* status,
-                           int num_sms, cudaStream_t stream);
+                           int num_sms, int block, cudaStream_t stream);
 ssi_status jacobi_launch(Workspace& ws, const float* R2, int K, float* Ut, float* S, int* status,
-                         int num_sms, cudaStream_t stream);
+                         int num_sms, int block, cudaStream_t stream);
 
 namespace {
 
@@ -532,7 +532,8 @@ ssi_status gaussian_omega_launch(int rows, int cols, int ld, uint64_t seed, floa
   return SSI_OK;
 }
 
-RsvdPlan rsvd_plan(int l, int i, int k, int oversample, int q, int num_sms) {
+RsvdPlan rsvd_plan(int l, int i, int k, int oversample, int q, int num_sms, int splits_req,
+                   int jacobi_block) {
   RsvdPlan r{};
   r.l = l;
   r.i = i;
@@ -545,9 +546,11 @@ RsvdPlan rsvd_plan(int l, int i, int k, int oversample, int q, int num_sms) {
   const int n_nt = (int)ceil_div(round_up(r.K, 64), 256);
   r.Kp = (int)round_up(r.K, 64 * n_nt);
   const int n_mt = r.L_pad / 128 + (r.L_pad % 128 ? 1 : 0);
-  int S = toeplitz_splits(r.L_pad, n_mt * n_nt, num_sms);
+  int S = splits_req > 0 ? std::min(splits_req, 64) : toeplitz_splits(r.L_pad, n_mt * n_nt, num_sms);
   const int krows = (int)round_up(ceil_div(r.L_pad, S), SBK);
   S = (int)ceil_div(r.L_pad, krows);
+  r.tg_splits = S;
+  r.jacobi_block = jacobi_block;
   const int n_lag = 2 * i - 1;
   const size_t rblk = (size_t)n_lag * r.l_pad * r.l_pad;
   const size_t xsz = (size_t)r.L_pad * r.Kp;
@@ -587,11 +590,8 @@ ssi_status toeplitz_rsvd_ws(ssi_ctx* ctx, Workspace& ws, const RsvdPlan& r, cons
   p.L_pad = r.L_pad;
   p.n_mt = (int)ceil_div(r.L_pad, 128);
   p.n_nt = n_nt;
-  {
-    const int Sg = toeplitz_splits(r.L_pad, p.n_mt * n_nt, ctx->num_sms);
-    p.krows = (int)round_up(ceil_div(r.L_pad, Sg), SBK);
-    p.n_split = (int)ceil_div(r.L_pad, p.krows);
-  }
+  p.krows = (int)round_up(ceil_div(r.L_pad, r.tg_splits), SBK);
+  p.n_split = (int)ceil_div(r.L_pad, p.krows);
   p.ld = r.Kp;
   p.split_stride = (long long)xsz;
 
@@ -694,9 +694,9 @@ ssi_status toeplitz_rsvd_ws(ssi_ctx* ctx, Workspace& ws, const RsvdPlan& r, cons
   {
     ProfScope ps(ctx, ST_SMALL_SVD, stream);
     if (small64)
-      SSI_TRY(jacobi_launch64(ws, R2, r.K, Ut64, sig64, dev_status, nsm, stream));
+      SSI_TRY(jacobi_launch64(ws, R2, r.K, Ut64, sig64, dev_status, nsm, r.jacobi_block, stream));
     else
-      SSI_TRY(jacobi_launch(ws, R2, r.K, Ut, sig, dev_status, nsm, stream));
+      SSI_TRY(jacobi_launch(ws, R2, r.K, Ut, sig, dev_status, nsm, r.jacobi_block, stream));
   }
   ProfScope ps_u(ctx, ST_OTHER, stream);
   const int gu = grid_1d((long long)r.L * r.k, 256, nsm), gs = grid_1d(r.k, 256, nsm);

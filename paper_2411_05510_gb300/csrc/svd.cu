@@ -241,8 +241,8 @@ struct BjGrid {
   int C, bw;
 };
 
-BjGrid bj_grid(int K, bool fp64, int num_sms) {
-  const int target_bw = fp64 ? 2 : 14;
+BjGrid bj_grid(int K, bool fp64, int num_sms, int block = 0) {
+  const int target_bw = block > 0 ? block : (fp64 ? 2 : 14);
   int C = std::max(1, (int)ceil_div(K, 2 * target_bw));
   C = std::min(C, num_sms);
   int bw = (int)ceil_div(K, 2 * C);
@@ -269,8 +269,8 @@ size_t bj_ws_bytes_t(int K, int num_sms) {
 
 template <typename T>
 ssi_status bj_launch(Workspace& ws, const float* R2, int K, T* Ut, T* S, int* status, int num_sms,
-                     T tol, int max_sweeps, cudaStream_t stream) {
-  const BjGrid g = bj_grid(K, sizeof(T) == 8, num_sms);
+                     int block, T tol, int max_sweeps, cudaStream_t stream) {
+  const BjGrid g = bj_grid(K, sizeof(T) == 8, num_sms, block);
   BjParams<T> p{};
   p.R2 = R2;
   p.K = K;
@@ -324,13 +324,13 @@ size_t jacobi_ws_bytes(int K, int num_sms, bool fp64) {
 // FP32: stop at |b_p^T b_q| <= 1e-5 ||b_p|| ||b_q|| (30 sweeps at most); FP64: 1e-13
 // (the rounding of an FP64 dot product of length K is about sqrt(K) 1e-16).
 ssi_status jacobi_launch(Workspace& ws, const float* R2, int K, float* Ut, float* S, int* status,
-                         int num_sms, cudaStream_t stream) {
-  return bj_launch<float>(ws, R2, K, Ut, S, status, num_sms, 1e-5f, 30, stream);
+                         int num_sms, int block, cudaStream_t stream) {
+  return bj_launch<float>(ws, R2, K, Ut, S, status, num_sms, block, 1e-5f, 30, stream);
 }
 
 ssi_status jacobi_launch64(Workspace& ws, const float* R2, int K, double* Ut, double* S, int* status,
-                           int num_sms, cudaStream_t stream) {
-  return bj_launch<double>(ws, R2, K, Ut, S, status, num_sms, 1e-13, 40, stream);
+                           int num_sms, int block, cudaStream_t stream) {
+  return bj_launch<double>(ws, R2, K, Ut, S, status, num_sms, block, 1e-13, 40, stream);
 }
 
 }  // namespace ssi

@@ -1,0 +1,110 @@
+"""The rank calibration of Sec. 3.1 (parametric analysis behind Eq. empirical_formula) on
+the GPU path against the same search run by the oracle.
+
+Record: the 10-DOF frame of Sec. 3.1 (Rayleigh 1 % at modes 1 and 4, white forces at
+every floor, 10 floor accelerations, fs = 200 Hz, 5 min), SNR 20 dB.  Orders 10..100 step
+2; HC xi <= 10 %, MPC > 60 %, MPD < 50 %; SC between orders 2 %, 2 %, 5 %; the stable
+poles clustered into modes (tau 0.05); RSVD modes match the SVD's when every SVD mode
+has an RSVD mode within 1 % in frequency, 1 % in damping and 2 % in 1 - MAC.
+
+For j_b = 100 and 120 (T = 1000 and 1200):
+  * the SVD of T: the GPU's full-width range finder against the oracle's Jacobi SVD,
+    leading 2 m = 20 singular values to 1e-4, and the same number of identified modes,
+    each within 1e-3 in frequency;
+  * the minimum rank kbar on the grid 2.5 %, 5 %, ...: the GPU's search and the oracle's
+    agree to one grid step (a mode whose match criterion sits at its threshold may tip
+    either way between two FP arithmetics).
+The oracle leg (two Jacobi SVDs of 1000-1200 columns and the candidate RSVDs) takes
+several minutes of host time.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import ssi_synth as S
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+ORDERS = list(range(10, 101, 2))
+TOL = (0.01, 0.01, 0.02)
+SEED = 1
+JBS = (100, 120)
+
+
+def _record():
+    w = S.workload("frame10", noise=10 ** (-20 / 20), seed=220)
+    Y, *_ = S.record(w, np.float32)
+    return w, Y
+
+
+def _oracle_identify(R, jb, l, dt, K):
+    T = O.block_toeplitz(R, jb)
+    if K >= T.shape[0]:
+        U, s = O.full_svd(T)
+    else:
+        U, s = O.rsvd(T, K, 0, 0, SEED)
+    diag = [[]]
+    for n in ORDERS:
+        mu, f, xi, Phi, _ = O.realize(U, s, l, jb, n, dt)
+        diag[0].append(dict(mu=mu, f=f, xi=xi, Phi=Phi))
+    O.stability(diag, a_f=0.02, a_xi=0.02, a_mac=0.05, use_lag_axis=False)
+    modes, _, _, _ = O.cluster_modes(diag, tau=0.05, min_size=len(ORDERS) // 5)
+    out = []
+    for md in modes:
+        t, m, i = md["medoid"]
+        out.append(dict(f_hz=md["f"], xi=md["xi"], size=md["size"], phi=diag[t][m]["Phi"][:, i]))
+    return out, s
+
+
+@pytest.fixture(scope="module")
+def study():
+    from paper_2411_05510_gb300 import rank_study as RS
+    w, Y = _record()
+    l, dt = Y.shape[0], 1.0 / w["fs"]
+    R = O.covariances(Y.astype(np.float64), 2 * max(JBS) - 1)
+    grid = RS.rank_grid(2.5, 50.0, 2.5)
+    res = {}
+    for jb in JBS:
+        T = l * jb
+        ref, s_ref = _oracle_identify(R, jb, l, dt, T)
+        kbar, trace = None, []
+        for pct in grid:
+            K = max(max(ORDERS), int(math.ceil(pct * T / 100.0 - 1e-9)))
+            cand, _ = _oracle_identify(R, jb, l, dt, K)
+            ok = RS.modes_match(ref, cand, TOL)
+            trace.append((pct, K, ok, len(cand)))
+            if ok:
+                kbar = pct
+                break
+        res[jb] = dict(ref=ref, s=s_ref, kbar=kbar, trace=trace)
+    return dict(w=w, Y=Y, R=R, grid=grid, ora=res)
+
+
+@pytest.mark.parametrize("jb", JBS)
+def test_minimum_rank_matches_oracle_search(study, jb):
+    import paper_2411_05510_gb300 as P
+    from paper_2411_05510_gb300 import rank_study as RS
+    w, Y = study["w"], study["Y"]
+    l = Y.shape[0]
+    ctx = P.Context(0)
+    # the SVD of T: the full-width range finder against the oracle's Jacobi SVD
+    Rd = torch.from_numpy(np.ascontiguousarray(study["R"][:2 * jb - 1])).cuda()
+    _, sg = P.ssi_toeplitz_rsvd(ctx, Rd, l, jb, l * jb, 0, 0, SEED, "split_bf16")
+    P.check_sync(ctx)
+    s_ref = study["ora"][jb]["s"]
+    rel = np.abs(sg.cpu().numpy()[:20] / s_ref[:20] - 1)
+    assert rel.max() <= 1e-4, rel.max()
+    Yd = torch.from_numpy(Y).cuda()
+    kbar, ref, trace = RS.minimum_rank(ctx, Yd, w["fs"], jb, ORDERS, study["grid"], TOL, seed=SEED)
+    ctx.close()
+    ora = study["ora"][jb]
+    print(f"jb={jb}: GPU kbar {kbar} trace {trace}; oracle kbar {ora['kbar']} trace {ora['trace']}")
+    assert len(ref) == len(ora["ref"]) >= 8, (len(ref), len(ora["ref"]))
+    for a in ref:
+        assert min(abs(a["f_hz"] - b["f_hz"]) / b["f_hz"] for b in ora["ref"]) <= 1e-3, a["f_hz"]
+    assert kbar is not None and ora["kbar"] is not None
+    g = study["grid"]
+    assert abs(g.index(kbar) - g.index(ora["kbar"])) <= 1, (kbar, ora["kbar"])
