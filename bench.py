@@ -70,6 +70,8 @@ def parse():
     ap.add_argument("--n-samples", type=int, default=0,
                     help="record length override (smaller cases for profiler captures)")
     ap.add_argument("--prec", default="split_bf16", choices=["split_bf16", "fp32"])
+    ap.add_argument("--small", default="fp32", choices=["fp32", "fp64"],
+                    help="arithmetic of the K x K SVD, A and eig(A) of the timed solves")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32", action="store_true")
@@ -564,8 +566,11 @@ def run_frame10_table2(args, world, rank):
         Yd = torch.from_numpy(Y).cuda()
         for key, lags, min_size in (("rsvd_2d", [189], 5),
                                     ("rsvd_3d", lags3, len(lags3) * len(orders) // 4)):
-            desc = P.job_desc(Yd, w["fs"], lags, orders, k=512, oversample=0, q=0,
-                              prec="split_bf16", seed=seed)
+            # Eq. (empirical_formula) at the largest Toeplitz size of the diagram: K columns
+            # of the range finder (Algorithm 1, p = q = 0), the first 30 kept for the orders
+            _, K = P.ssi_rank_rule(Y.shape[0] * max(lags))
+            desc = P.job_desc(Yd, w["fs"], lags, orders, k=max(orders), oversample=K - max(orders),
+                              q=0, prec="split_bf16", seed=seed)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             poles, phi, _ = P.ssi_solve(ctx, desc, with_s=False)
@@ -610,7 +615,8 @@ def run_frame10_table2(args, world, rank):
             "reference": "generating model (exact ZOH modal values); the SVD arm of Table 2 "
                          "is the paper's comparison system and is not built",
             "config": {"fs": 200.0, "N": 60000, "noise": 0.1, "orders": "2..30",
-                       "lags_2d": [189], "lags_3d": lags3, "k": 512, "oversample": 0, "q": 0,
+                       "lags_2d": [189], "lags_3d": lags3,
+                       "K": "Eq. (empirical_formula) at the largest T: 512 (2D), 664 (3D)", "q": 0,
                        "tau": 0.05, "min_size_2d": 5,
                        "min_size_3d": len(lags3) * len(orders) // 4},
             "rsvd_2d": table(res["rsvd_2d"]), "rsvd_3d": table(res["rsvd_3d"]),
@@ -637,12 +643,13 @@ def run_rank_study(args, world, rank):
     points, t0 = [], time.perf_counter()
     for snr in (10, 15, 20, 25):
         w = S.workload("frame10", noise=10 ** (-snr / 20), seed=200 + snr)
-        Y, *_ = S.record(w, np.float32)
+        Y, f_true, *_ = S.record(w, np.float32)
         Yd = torch.from_numpy(Y).cuda()
         for jb in jbs:
             T = Y.shape[0] * jb
             ts = time.perf_counter()
-            kbar, ref, trace = RS.minimum_rank(ctx, Yd, w["fs"], jb, orders, grid, seed=1)
+            kbar, ref, trace = RS.minimum_rank(ctx, Yd, w["fs"], jb, orders, grid, f_names=f_true,
+                                               seed=1)
             points.append({"snr_db": snr, "jb": jb, "T": T, "kbar_pct": kbar,
                            "modes_svd": len(ref), "trace": trace,
                            "seconds": round(time.perf_counter() - ts, 2)})
@@ -659,6 +666,7 @@ def run_rank_study(args, world, rank):
                        "orders": "10..100 step 2", "grid_pct": [grid[0], grid[-1], 2.5],
                        "q": 0, "oversample": 0, "match_tol": [0.01, 0.01, 0.02],
                        "sc": [0.02, 0.02, 0.05], "hc": [0.10, 0.6, 0.5],
+                       "modes_compared": "the SVD modes nearest the 10 generating frequencies",
                        "svd": "range finder at full width (K = T)"},
             "points": points, "least_squares_line": fit,
             "eq_empirical_formula": {str(p["T"]): max(30 - 0.00156 * p["T"], 25.0)
@@ -797,7 +805,7 @@ def main():
             P.ssi_tuning_set(ln["ctx"], ln["desc"], t)
         return t
 
-    lanes = make_lanes(args.prec)
+    lanes = make_lanes(args.prec, args.small)
     tuning = autotune(lanes)
     warm(lanes)
     for ln in lanes:
@@ -852,6 +860,7 @@ def main():
         traffic, tnote = stored_traffic(args.workload)
         cfg = config_of(w, args.prec)
         cfg["inflight"] = J
+        cfg["small"] = args.small
         out = {
             "metric": "SSI solves/s", "value": value, "unit": "solves/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
@@ -1031,7 +1040,7 @@ def main():
             out["fp32_path"] = r32
 
     # the same pipeline with the K x K SVD, A and eig(A) in FP64
-    if not args.no_fp64_small:
+    if not args.no_fp64_small and args.small == "fp32":
         for ln in lanes[1:]:
             ln["ctx"].close()
         lanes = lanes[:1]

@@ -13,9 +13,14 @@ module runs that search on the GPU path for one record and one j_b:
     increasing grid, until the first one whose modes match the reference's;
   * identification: the 2D stabilization diagram of the orders (hard and soft criteria),
     then the two-stage clustering of its stable poles into modes (ssi_cluster);
-  * match: the two mode lists have the same length and every reference mode has a mode
-    within the matching tolerances (relative frequency, relative damping, 1 - MAC of the
-    medoids' shapes; Sec. 3.1 uses 1 %, 1 % and 2 %).
+  * match: every reference mode of interest has a candidate mode within the matching
+    tolerances (relative frequency, relative damping, 1 - MAC of the medoids' shapes;
+    Sec. 3.1 uses 1 %, 1 % and 2 %).  The modes of interest are the reference modes nearest
+    (within 5 %) to the frequencies the caller names -- the structure's modes, e.g. the
+    generating model's in a synthetic study -- or, when none are named, every reference
+    mode (the lists must then also have the same length).  Spurious clusters of the SVD's
+    diagram come from its noise subspace, which no rank-k approximation reproduces, so a
+    study over the structure's modes names them.
 
 Every step runs in libssi's kernels; this module only chooses the calls and compares the
 mode tables it gets back (a few numbers per mode).
@@ -30,7 +35,7 @@ import torch
 
 from . import api as A
 
-__all__ = ["identify", "modes_match", "minimum_rank", "rank_grid"]
+__all__ = ["identify", "modes_match", "modes_of_interest", "minimum_rank", "rank_grid"]
 
 
 def rank_grid(lo: float = 2.5, hi: float = 50.0, step: float = 2.5):
@@ -65,10 +70,30 @@ def _mac(a, b) -> float:
     return float(abs(np.vdot(a, b)) ** 2 / den) if den > 0 else 0.0
 
 
-def modes_match(ref, cand, tol=(0.01, 0.01, 0.02)) -> bool:
-    """Same number of modes, and every reference mode has a candidate mode within the
-    tolerances: |df| / f, |dxi| / xi (denominators the larger value) and 1 - MAC."""
-    if len(ref) != len(cand) or not ref:
+def modes_of_interest(ref, f_names):
+    """The reference modes nearest (within 5 %) to each named frequency, once each."""
+    out = []
+    for f0 in f_names:
+        best = None
+        for r in ref:
+            d = abs(r["f_hz"] - f0) / f0
+            if d < 0.05 and (best is None or d < best[0]):
+                best = (d, r)
+        if best is not None and all(best[1] is not o for o in out):
+            out.append(best[1])
+    return out
+
+
+def modes_match(ref, cand, tol=(0.01, 0.01, 0.02), f_names=None) -> bool:
+    """Every reference mode of interest (all of them, with equal counts, when f_names is
+    None) has a candidate mode within the tolerances: |df| / f, |dxi| / xi (denominators
+    the larger value) and 1 - MAC."""
+    if f_names is None:
+        if len(ref) != len(cand):
+            return False
+    else:
+        ref = modes_of_interest(ref, f_names)
+    if not ref:
         return False
     for r in ref:
         ok = False
@@ -84,9 +109,10 @@ def modes_match(ref, cand, tol=(0.01, 0.01, 0.02)) -> bool:
 
 
 def minimum_rank(ctx: A.Context, Y: torch.Tensor, fs: float, jb: int, orders: Sequence[int],
-                 grid: Sequence[float] | None = None, tol=(0.01, 0.01, 0.02), **kw):
-    """Smallest percentage of T on `grid` whose RSVD identification matches the SVD's.
-    Returns (kbar_pct or None, reference modes, trace of (pct, K, matched, n_modes))."""
+                 grid: Sequence[float] | None = None, tol=(0.01, 0.01, 0.02), f_names=None, **kw):
+    """Smallest percentage of T on `grid` whose RSVD identification matches the SVD's on
+    the modes of interest (f_names, see modes_match).  Returns (kbar_pct or None,
+    reference modes, trace of (pct, K, matched, n_modes))."""
     l = Y.shape[0]
     T = l * jb
     grid = list(grid or rank_grid())
@@ -98,7 +124,7 @@ def minimum_rank(ctx: A.Context, Y: torch.Tensor, fs: float, jb: int, orders: Se
             trace.append((pct, T, True, len(ref)))
             return pct, ref, trace
         cand = identify(ctx, Y, fs, jb, orders, K, **kw)
-        ok = modes_match(ref, cand, tol)
+        ok = modes_match(ref, cand, tol, f_names)
         trace.append((pct, K, ok, len(cand)))
         if ok:
             return pct, ref, trace

@@ -4,8 +4,9 @@ the GPU path against the same search run by the oracle.
 Record: the 10-DOF frame of Sec. 3.1 (Rayleigh 1 % at modes 1 and 4, white forces at
 every floor, 10 floor accelerations, fs = 200 Hz, 5 min), SNR 20 dB.  Orders 10..100 step
 2; HC xi <= 10 %, MPC > 60 %, MPD < 50 %; SC between orders 2 %, 2 %, 5 %; the stable
-poles clustered into modes (tau 0.05); RSVD modes match the SVD's when every SVD mode
-has an RSVD mode within 1 % in frequency, 1 % in damping and 2 % in 1 - MAC.
+poles clustered into modes (tau 0.05); the RSVD's modes match the SVD's when each SVD mode
+nearest to one of the frame's ten generating frequencies has an RSVD mode within 1 % in
+frequency, 1 % in damping and 2 % in 1 - MAC.
 
 For j_b = 100 and 120 (T = 1000 and 1200):
   * the SVD of T: the GPU's full-width range finder against the oracle's Jacobi SVD,
@@ -36,8 +37,8 @@ JBS = (100, 120)
 
 def _record():
     w = S.workload("frame10", noise=10 ** (-20 / 20), seed=220)
-    Y, *_ = S.record(w, np.float32)
-    return w, Y
+    Y, f_true, *_ = S.record(w, np.float32)
+    return w, Y, f_true
 
 
 def _oracle_identify(R, jb, l, dt, K):
@@ -62,7 +63,7 @@ def _oracle_identify(R, jb, l, dt, K):
 @pytest.fixture(scope="module")
 def study():
     from paper_2411_05510_gb300 import rank_study as RS
-    w, Y = _record()
+    w, Y, f_true = _record()
     l, dt = Y.shape[0], 1.0 / w["fs"]
     R = O.covariances(Y.astype(np.float64), 2 * max(JBS) - 1)
     grid = RS.rank_grid(2.5, 50.0, 2.5)
@@ -74,13 +75,13 @@ def study():
         for pct in grid:
             K = max(max(ORDERS), int(math.ceil(pct * T / 100.0 - 1e-9)))
             cand, _ = _oracle_identify(R, jb, l, dt, K)
-            ok = RS.modes_match(ref, cand, TOL)
+            ok = RS.modes_match(ref, cand, TOL, f_true)
             trace.append((pct, K, ok, len(cand)))
             if ok:
                 kbar = pct
                 break
         res[jb] = dict(ref=ref, s=s_ref, kbar=kbar, trace=trace)
-    return dict(w=w, Y=Y, R=R, grid=grid, ora=res)
+    return dict(w=w, Y=Y, R=R, grid=grid, ora=res, f_true=f_true)
 
 
 @pytest.mark.parametrize("jb", JBS)
@@ -98,7 +99,8 @@ def test_minimum_rank_matches_oracle_search(study, jb):
     rel = np.abs(sg.cpu().numpy()[:20] / s_ref[:20] - 1)
     assert rel.max() <= 1e-4, rel.max()
     Yd = torch.from_numpy(Y).cuda()
-    kbar, ref, trace = RS.minimum_rank(ctx, Yd, w["fs"], jb, ORDERS, study["grid"], TOL, seed=SEED)
+    kbar, ref, trace = RS.minimum_rank(ctx, Yd, w["fs"], jb, ORDERS, study["grid"], TOL,
+                                       f_names=study["f_true"], seed=SEED)
     ctx.close()
     ora = study["ora"][jb]
     print(f"jb={jb}: GPU kbar {kbar} trace {trace}; oracle kbar {ora['kbar']} trace {ora['trace']}")
