@@ -82,7 +82,7 @@ def parse():
     ap.add_argument("--no-3d", action="store_true")
     ap.add_argument("--no-mix", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
-    ap.add_argument("--rank-jb-max", type=int, default=1000,
+    ap.add_argument("--rank-jb-max", type=int, default=500,
                     help="largest time-lag step of --workload rank_study")
     ap.add_argument("--inflight", type=int, default=4,
                     help="solves in flight at once, each on its own stream and context")
@@ -628,7 +628,7 @@ def run_rank_study(args, world, rank):
     """The parametric analysis of Sec. 3.1 on the 10-DOF frame: for SNR 10, 15, 20 and
     25 dB (5-minute records at 200 Hz) and j_b = 100, 200, ..., --rank-jb-max (T = 10 j_b),
     the minimum rank kbar (percent of T, on a 2.5 % grid) at which the RSVD identification
-    (q = 0, orders 10..100) matches the SVD's (paper_2411_05510_gb300/rank_study.py).
+    (q = 1, orders 10..100) matches the SVD's (paper_2411_05510_gb300/rank_study.py).
     Beside the points: Eq. (empirical_formula) and the least-squares line through them,
     as the paper fits its line before shifting its intercept to 30 %.  Rank 0 only."""
     import torch
@@ -648,8 +648,8 @@ def run_rank_study(args, world, rank):
         for jb in jbs:
             T = Y.shape[0] * jb
             ts = time.perf_counter()
-            kbar, ref, trace = RS.minimum_rank(ctx, Yd, w["fs"], jb, orders, grid, f_names=f_true,
-                                               seed=1)
+            kbar, ref, trace = RS.minimum_rank(ctx, Yd, w["fs"], jb, orders, grid,
+                                               f_names=f_true, seed=1, q=1)
             points.append({"snr_db": snr, "jb": jb, "T": T, "kbar_pct": kbar,
                            "modes_svd": len(ref), "trace": trace,
                            "seconds": round(time.perf_counter() - ts, 2)})
@@ -664,7 +664,8 @@ def run_rank_study(args, world, rank):
             "unit": "percent", "workload": "rank_study",
             "config": {"fs": 200.0, "N": 60000, "snr_db": [10, 15, 20, 25], "jb": jbs,
                        "orders": "10..100 step 2", "grid_pct": [grid[0], grid[-1], 2.5],
-                       "q": 0, "oversample": 0, "match_tol": [0.01, 0.01, 0.02],
+                       "q": 1, "oversample": "K - 100 (k = 100, the largest order)",
+                       "match_tol": [0.01, 0.01, 0.02],
                        "sc": [0.02, 0.02, 0.05], "hc": [0.10, 0.6, 0.5],
                        "modes_compared": "the SVD modes nearest the 10 generating frequencies",
                        "svd": "range finder at full width (K = T)"},

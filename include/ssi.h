@@ -387,14 +387,16 @@ ssi_status ssi_solve(ssi_ctx* ctx, const ssi_job_desc* job, ssi_pole* poles, flo
 
 /* ------------------------------------------------------------------------------
  * Autotuner of a job shape's plan choices (the batching pattern: tile and split shapes
- * picked from timed candidates; the paper has no counterpart).  Three choices are made
+ * picked from timed candidates; the paper has no counterpart).  Four choices are made
  * by cost models otherwise: the lag GEMM's samples per time split, the Toeplitz GEMMs'
- * reduction splits and the K x K Jacobi's columns per block.  ssi_autotune runs solves of
- * `job` (its record included) on an internal stream, one choice at a time, each
- * candidate once untimed and twice timed by the stage profiler, keeps the fastest, and
- * stores the three values in the context under the job's shape (l, N, lags, k,
- * oversample, precisions); later ssi_solve calls and serving jobs of that shape use them.
- * The results change only by rounding (the split and block structure orders the sums).
+ * reduction splits, the K x K Jacobi's columns per block and the sketch QR's row chunks
+ * per CTA.  ssi_autotune runs solves of `job` (its record included) on an internal
+ * stream, one choice at a time, each candidate once untimed and twice timed by the stage
+ * profiler, keeps the fastest (for the QR grid, when the context expects several solves
+ * at once, the smallest time x CTAs), and stores the four values in the context under
+ * the job's shape (l, N, lags, k, oversample, precisions); later ssi_solve calls and
+ * serving jobs of that shape use them.  The results change only by rounding (the split
+ * and block structure orders the sums; the QR grid changes none of its sums).
  * Synchronous; call it before serving starts.  ssi_tuning_get returns the stored values
  * (SSI_E_NOTFOUND if the shape was never tuned); ssi_tuning_set stores values, e.g. those
  * tuned on another context (0 = the model's choice).
@@ -403,8 +405,8 @@ typedef struct {
   int32_t cov_rows_per_split;   /* lag GEMM: samples per FP32 partial sum */
   int32_t sketch_splits;        /* Toeplitz GEMMs: reduction splits */
   int32_t jacobi_block;         /* K x K Jacobi: columns per block */
-  int32_t reserved;
-  double stage_ms[3];           /* ms per solve of each stage with the chosen value */
+  int32_t qr_chunks_per_cta;    /* sketch QR: row chunks (one per SM) per CTA of its grid */
+  double stage_ms[4];           /* ms per solve of each stage with the chosen value */
 } ssi_tuning;
 ssi_status ssi_autotune(ssi_ctx* ctx, const ssi_job_desc* job, ssi_tuning* out);
 ssi_status ssi_tuning_get(ssi_ctx* ctx, const ssi_job_desc* job, ssi_tuning* out);

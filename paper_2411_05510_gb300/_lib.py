@@ -71,8 +71,8 @@ class SsiJobDesc(ctypes.Structure):
 
 class SsiTuning(ctypes.Structure):
     _fields_ = [("cov_rows_per_split", ctypes.c_int32), ("sketch_splits", ctypes.c_int32),
-                ("jacobi_block", ctypes.c_int32), ("reserved", ctypes.c_int32),
-                ("stage_ms", ctypes.c_double * 3)]
+                ("jacobi_block", ctypes.c_int32), ("qr_chunks_per_cta", ctypes.c_int32),
+                ("stage_ms", ctypes.c_double * 4)]
 
 
 _c = ctypes

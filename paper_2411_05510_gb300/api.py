@@ -293,7 +293,8 @@ def ssi_solve(ctx: Context, desc: SsiJobDesc, device="cuda", with_s: bool = True
 
 def _tuning_dict(t: SsiTuning) -> dict:
     return {"cov_rows_per_split": t.cov_rows_per_split, "sketch_splits": t.sketch_splits,
-            "jacobi_block": t.jacobi_block, "stage_ms": [t.stage_ms[i] for i in range(3)]}
+            "jacobi_block": t.jacobi_block, "qr_chunks_per_cta": t.qr_chunks_per_cta,
+            "stage_ms": [t.stage_ms[i] for i in range(4)]}
 
 
 def ssi_autotune(ctx: Context, desc: SsiJobDesc) -> dict:
@@ -311,7 +312,7 @@ def ssi_tuning_get(ctx: Context, desc: SsiJobDesc) -> dict:
 
 def ssi_tuning_set(ctx: Context, desc: SsiJobDesc, tuning: dict) -> None:
     t = SsiTuning(int(tuning.get("cov_rows_per_split", 0)), int(tuning.get("sketch_splits", 0)),
-                  int(tuning.get("jacobi_block", 0)), 0)
+                  int(tuning.get("jacobi_block", 0)), int(tuning.get("qr_chunks_per_cta", 0)))
     check(lib.ssi_tuning_set(ctx.ptr, ctypes.byref(desc), ctypes.byref(t)), "ssi_tuning_set")
 
 

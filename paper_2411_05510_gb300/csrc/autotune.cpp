@@ -1,16 +1,19 @@
 // Autotuner of the plan choices of one job shape (the batching pattern's tile shapes).
 //
-// Three choices of a solve are made by cost models when nothing else is known: the lag
+// Four choices of a solve are made by cost models when nothing else is known: the lag
 // GEMM's time split (samples per FP32 partial sum; the model minimises whole waves of
-// work units), the Toeplitz GEMMs' reduction splits (the model maximises wave efficiency)
-// and the K x K Jacobi's block width (columns per block of the parallel ordering, which
-// trades grid barriers against the work of one outer round).  ssi_autotune times real
-// solves of the job on the calling thread: for each choice in turn (coordinate descent),
-// every candidate runs one untimed and two timed solves with the context's stage
-// profiler on, and the candidate with the smallest time of its own stage is kept.  The
-// three values are stored in the context under the job's shape (channels, samples, lags,
-// k, oversampling, precisions) and every later plan of that shape, by ssi_solve or the
-// serving loop, uses them.
+// work units), the Toeplitz GEMMs' reduction splits (the model maximises wave efficiency),
+// the K x K Jacobi's block width (columns per block of the parallel ordering, which
+// trades grid barriers against the work of one outer round) and the sketch QR's grid (row
+// chunks per CTA: the rows are cut into one chunk per SM, and fewer CTAs meet at cheaper
+// barriers but each does more work).  ssi_autotune times real solves of the job on the
+// calling thread: for each choice in turn (coordinate descent), every candidate runs one
+// untimed and two timed solves with the context's stage profiler on, and the candidate
+// with the smallest time of its own stage is kept -- for the QR grid, when the context
+// expects several solves at once (ssi_set_concurrency), the smallest time x CTAs, the
+// share of the device a QR holds.  The four values are stored in the context under the
+// job's shape (channels, samples, lags, k, oversampling, precisions) and every later plan
+// of that shape, by ssi_solve or the serving loop, uses them.
 #include <algorithm>
 #include <array>
 #include <cmath>
@@ -53,6 +56,15 @@ std::vector<int> block_candidates(const ssi_job_desc* j) {
   return {6, 8, 10, 14, 20, 28};
 }
 
+std::vector<int> qr_candidates() { return {1, 2, 4, 8}; }
+
+// CTAs of the QR grid with `cpc` chunks per CTA (as qr_launch forms it)
+int qr_ctas(const ssi_job_desc* j, int num_sms, int cpc) {
+  const int rows = (int)round_up(j->l, 64) * j->lags[0];
+  const int C = std::max(1, std::min<int>(num_sms, (int)ceil_div(rows, 32)));
+  return (int)ceil_div(C, std::min(cpc, C));
+}
+
 }  // namespace
 }  // namespace ssi
 
@@ -75,10 +87,10 @@ extern "C" ssi_status ssi_autotune(ssi_ctx* ctx, const ssi_job_desc* job, ssi_tu
     if (e != cudaSuccess) st = cuda_fail(e, "cudaStreamCreate", __FILE__, __LINE__);
   }
   const bool prof_was = ctx->prof_on;
-  std::array<int, 3> best{0, 0, 0};
-  double best_ms[3] = {0, 0, 0};
+  std::array<int, 4> best{0, 0, 0, 0};
+  double best_ms[4] = {0, 0, 0, 0};
   // stage time per solve of a candidate: one untimed solve, then two profiled ones
-  auto time_stage = [&](const std::array<int, 3>& tv, int which, double* ms_out) -> ssi_status {
+  auto time_stage = [&](const std::array<int, 4>& tv, int which, double* ms_out) -> ssi_status {
     const JobPlan p = plan_job(job, ctx, &tv);
     JobBuffers& B = ctx_solve_buffers(ctx);
     SSI_TRY(buffers_reserve(ctx, B, p, s));
@@ -93,26 +105,31 @@ extern "C" ssi_status ssi_autotune(ssi_ctx* ctx, const ssi_job_desc* job, ssi_tu
     double ms[ST_COUNT];
     SSI_TRY(ssi_profile_read(ctx, ms, nullptr, ST_COUNT, nullptr));
     SSI_TRY(check_dev_status(ctx_solve_buffers(ctx).status, s));
-    const double t = which == 0 ? ms[ST_SPLIT] + ms[ST_LAG_GEMM] + ms[ST_LAG_REDUCE]
-                   : which == 1 ? ms[ST_SKETCH_GEMM]
-                                : ms[ST_SMALL_SVD];
+    const double t = which == 0   ? ms[ST_SPLIT] + ms[ST_LAG_GEMM] + ms[ST_LAG_REDUCE]
+                     : which == 1 ? ms[ST_SKETCH_GEMM]
+                     : which == 2 ? ms[ST_SMALL_SVD]
+                                  : ms[ST_QR];
     *ms_out = t / 2.0;
     return SSI_OK;
   };
   if (st == SSI_OK) {
     ctx->prof_on = false;
-    const std::vector<int> cand[3] = {cov_candidates(job, ctx->num_sms),
-                                      split_candidates(job, ctx->num_sms), block_candidates(job)};
-    for (int which = 0; which < 3 && st == SSI_OK; ++which) {
-      double bt = 1e300;
+    const std::vector<int> cand[4] = {cov_candidates(job, ctx->num_sms),
+                                      split_candidates(job, ctx->num_sms), block_candidates(job),
+                                      qr_candidates()};
+    const bool shared = ctx->inflight > 1;
+    for (int which = 0; which < 4 && st == SSI_OK; ++which) {
+      double bt = 1e300, bcost = 1e300;
       int bv = 0;
       for (int v : cand[which]) {
-        std::array<int, 3> tv = best;
+        std::array<int, 4> tv = best;
         tv[which] = v;
         double t = 0.0;
         st = time_stage(tv, which, &t);
         if (st != SSI_OK) break;
-        if (t < bt) {
+        const double cost = (which == 3 && shared) ? t * qr_ctas(job, ctx->num_sms, v) : t;
+        if (cost < bcost) {
+          bcost = cost;
           bt = t;
           bv = v;
         }
@@ -134,8 +151,8 @@ extern "C" ssi_status ssi_autotune(ssi_ctx* ctx, const ssi_job_desc* job, ssi_tu
     out->cov_rows_per_split = best[0];
     out->sketch_splits = best[1];
     out->jacobi_block = best[2];
-    out->reserved = 0;
-    for (int i = 0; i < 3; ++i) out->stage_ms[i] = best_ms[i];
+    out->qr_chunks_per_cta = best[3];
+    for (int i = 0; i < 4; ++i) out->stage_ms[i] = best_ms[i];
   }
   return SSI_OK;
 }
@@ -152,17 +169,19 @@ extern "C" ssi_status ssi_tuning_get(ssi_ctx* ctx, const ssi_job_desc* job, ssi_
   out->cov_rows_per_split = it->second[0];
   out->sketch_splits = it->second[1];
   out->jacobi_block = it->second[2];
-  out->reserved = 0;
-  for (int i = 0; i < 3; ++i) out->stage_ms[i] = 0.0;
+  out->qr_chunks_per_cta = it->second[3];
+  for (int i = 0; i < 4; ++i) out->stage_ms[i] = 0.0;
   return SSI_OK;
 }
 
 extern "C" ssi_status ssi_tuning_set(ssi_ctx* ctx, const ssi_job_desc* job, const ssi_tuning* in) {
   SSI_CHECK(ctx && job && in, "ssi_tuning_set: null pointer");
   SSI_TRY(validate_job(job));
-  SSI_CHECK(in->cov_rows_per_split >= 0 && in->sketch_splits >= 0 && in->jacobi_block >= 0,
+  SSI_CHECK(in->cov_rows_per_split >= 0 && in->sketch_splits >= 0 && in->jacobi_block >= 0 &&
+                in->qr_chunks_per_cta >= 0,
             "ssi_tuning_set: negative choice");
   std::lock_guard<std::mutex> g(ctx->tune_mu);
-  ctx->tuned[job_shape_key(job)] = {in->cov_rows_per_split, in->sketch_splits, in->jacobi_block};
+  ctx->tuned[job_shape_key(job)] = {in->cov_rows_per_split, in->sketch_splits, in->jacobi_block,
+                                    in->qr_chunks_per_cta};
   return SSI_OK;
 }

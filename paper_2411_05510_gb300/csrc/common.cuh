@@ -103,9 +103,10 @@ struct ssi_ctx {
   std::mutex prof_mu;
   std::vector<std::tuple<int, cudaEvent_t, cudaEvent_t>> prof_recs;
   // autotuned plan choices per job shape (ssi_autotune): lag-GEMM samples per split,
-  // Toeplitz GEMM splits, Jacobi columns per block (0 = the model's choice)
+  // Toeplitz GEMM splits, Jacobi columns per block, QR row chunks per CTA (0 = the
+  // model's choice)
   std::mutex tune_mu;
-  std::map<std::string, std::array<int, 3>> tuned;
+  std::map<std::string, std::array<int, 4>> tuned;
 };
 
 namespace ssi {
@@ -143,12 +144,14 @@ ssi_status covariances_ws(ssi_ctx* ctx, Workspace& ws, const CovPlan& plan, cons
 struct RsvdPlan {
   int l, l_pad, i, k, K, Kp, q, L, L_pad;
   int tg_splits;        // reduction splits of the Toeplitz GEMMs
+  int tg_mt;            // 128-row M tiles per CTA of the Toeplitz GEMMs (1 or 2)
   int jacobi_block;     // columns per block of the K x K Jacobi (0: the model's choice)
+  int qr_cpc;           // QR row chunks per CTA (0: the model's choice)
   size_t ws_bytes;
 };
-// splits > 0 / jacobi_block > 0: values chosen by the caller (the autotuner)
+// splits > 0 / jacobi_block > 0 / qr_cpc > 0: values chosen by the caller (the autotuner)
 RsvdPlan rsvd_plan(int l, int i, int k, int oversample, int q, int num_sms, int splits = 0,
-                   int jacobi_block = 0);
+                   int jacobi_block = 0, int qr_cpc = 0);
 // shared_device: other work (another lag of the same solve) runs beside this one, so the
 // QR takes the half-device grid
 // small64: FP64 Jacobi and U = Q U~ in FP64 (U, S double); otherwise FP32, written as

@@ -48,9 +48,9 @@ std::string job_shape_key(const ssi_job_desc* j) {
   return key;
 }
 
-JobPlan plan_job(const ssi_job_desc* j, ssi_ctx* ctx, const std::array<int, 3>* tune) {
+JobPlan plan_job(const ssi_job_desc* j, ssi_ctx* ctx, const std::array<int, 4>* tune) {
   const int num_sms = ctx->num_sms;
-  std::array<int, 3> tv{0, 0, 0};
+  std::array<int, 4> tv{0, 0, 0, 0};
   if (tune) {
     tv = *tune;
   } else {
@@ -65,7 +65,8 @@ JobPlan plan_job(const ssi_job_desc* j, ssi_ctx* ctx, const std::array<int, 3>* 
   // the RSVDs of several lags run at once, each in its own region of the scratch
   size_t rs_total = 0;
   for (int t = 0; t < j->n_lags; ++t) {
-    p.rs.push_back(rsvd_plan(j->l, j->lags[t], j->k, j->oversample, j->q, num_sms, tv[1], tv[2]));
+    p.rs.push_back(rsvd_plan(j->l, j->lags[t], j->k, j->oversample, j->q, num_sms, tv[1], tv[2],
+                             tv[3]));
     p.rs_off.push_back(rs_total);
     rs_total += (p.rs.back().ws_bytes + 255) & ~size_t(255);
   }

@@ -35,7 +35,7 @@ struct JobBuffers {
 ssi_status validate_job(const ssi_job_desc* j);
 // tune: plan choices (lag-GEMM samples per split, Toeplitz splits, Jacobi block; 0 = the
 // model's); nullptr = the context's autotuned choices for the job's shape, if any
-JobPlan plan_job(const ssi_job_desc* j, ssi_ctx* ctx, const std::array<int, 3>* tune = nullptr);
+JobPlan plan_job(const ssi_job_desc* j, ssi_ctx* ctx, const std::array<int, 4>* tune = nullptr);
 std::string job_shape_key(const ssi_job_desc* j);
 ssi_status buffers_reserve(ssi_ctx* ctx, JobBuffers& B, const JobPlan& p, cudaStream_t stream);
 void buffers_free(ssi_ctx* ctx, JobBuffers& B);

@@ -512,7 +512,7 @@ size_t qr_ws_bytes(int ncols, int num_sms) {
 
 // QR of A (rows x ncols, leading dimension ld) in place; optional R (ncols x ncols).
 ssi_status qr_launch(ssi_ctx* ctx, Workspace& ws, float* A, int rows, int ncols, int ld, float* Rout,
-                     int* status, cudaStream_t stream, bool shared_device) {
+                     int* status, cudaStream_t stream, bool shared_device, int chunks_per_cta) {
   if (rows < ncols) {
     set_error("qr: rows (%d) < columns (%d)", rows, ncols);
     return SSI_E_INVALID;
@@ -525,9 +525,12 @@ ssi_status qr_launch(ssi_ctx* ctx, Workspace& ws, float* A, int rows, int ncols,
   p.Rout = Rout;
   // chunks: one per SM (fixed for the device and the shape, so the result is too); a CTA
   // per chunk when the solve has the device to itself, a CTA per two chunks when several
-  // solves (or several lags of one solve) share it
+  // solves (or several lags of one solve) share it, unless the caller (the autotuner)
+  // chose the chunks per CTA.  The grouping changes which CTA sums a chunk, not the
+  // order of any sum.
   const int C = std::max(1, std::min<int>(ctx->num_sms, (int)ceil_div(rows, 32)));
-  const int cpc = (ctx->inflight > 1 || shared_device) ? 2 : 1;
+  const int cpc = chunks_per_cta > 0 ? std::min(chunks_per_cta, C)
+                                     : (ctx->inflight > 1 || shared_device) ? 2 : 1;
   const int P = (int)ceil_div(C, cpc);
   p.n_chunks = C;
   p.chunks_per_cta = cpc;

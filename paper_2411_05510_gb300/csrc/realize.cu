@@ -316,9 +316,11 @@ __device__ __forceinline__ float sgnf(float a, float b) { return b >= 0.f ? fabs
 // One Householder reflector of the Hessenberg reduction applied from both sides,
 // H = (I - beta v v^T) H (I - beta v v^T) on rows/columns j+1.., with v in registers: entry c
 // on lane c % 32, slot c / 32 (the same layout serves the rows of the left update and the
-// columns of the right update); a warp owns whole columns (rows), forms the dot product,
-// reduces it, and updates the elements it still holds in registers.  NV slots cover
-// orders up to 32 NV.
+// columns of the right update); a warp owns HB whole columns (rows) at a time, forms their
+// dot products, reduces the HB sums together (independent shuffle trees, so their
+// latencies overlap), and updates the elements it still holds in registers.  NV slots
+// cover orders up to 32 NV.
+constexpr int HB = 4;
 template <int NV>
 __device__ __forceinline__ void hess_update(float* A, int ld, int n, int j, int len, float beta,
                                             const float* sv, int hw, int hl, int hnw) {
@@ -329,42 +331,64 @@ __device__ __forceinline__ void hess_update(float* A, int ld, int n, int j, int 
     vreg[q] = (c < len) ? sv[c] : 0.f;
   }
   // left: A[j+1:, c] -= beta v (v^T A[j+1:, c]) for c > j (column j is already final)
-  for (int c = j + 1 + hw; c < n; c += hnw) {
-    float a[NV];
-    float dot = 0.f;
+  for (int c0 = j + 1 + HB * hw; c0 < n; c0 += HB * hnw) {
+    float a[HB][NV];
+    float dot[HB];
 #pragma unroll
-    for (int q = 0; q < NV; ++q) {
-      const int r = hl + 32 * q;
-      a[q] = (r < len) ? A[(j + 1 + r) * ld + c] : 0.f;
-      dot = fmaf(a[q], vreg[q], dot);
+    for (int b = 0; b < HB; ++b) {
+      dot[b] = 0.f;
+      const bool ok = c0 + b < n;
+#pragma unroll
+      for (int q = 0; q < NV; ++q) {
+        const int r = hl + 32 * q;
+        a[b][q] = (ok && r < len) ? A[(j + 1 + r) * ld + c0 + b] : 0.f;
+        dot[b] = fmaf(a[b][q], vreg[q], dot[b]);
+      }
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
-    const float sc = dot * beta;
+    for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
-    for (int q = 0; q < NV; ++q) {
-      const int r = hl + 32 * q;
-      if (r < len) A[(j + 1 + r) * ld + c] = fmaf(-sc, vreg[q], a[q]);
+      for (int b = 0; b < HB; ++b) dot[b] += __shfl_xor_sync(0xffffffffu, dot[b], o);
+#pragma unroll
+    for (int b = 0; b < HB; ++b) {
+      if (c0 + b >= n) break;
+      const float sc = dot[b] * beta;
+#pragma unroll
+      for (int q = 0; q < NV; ++q) {
+        const int r = hl + 32 * q;
+        if (r < len) A[(j + 1 + r) * ld + c0 + b] = fmaf(-sc, vreg[q], a[b][q]);
+      }
     }
   }
   __syncthreads();
   // right: A[r, j+1:] -= beta (A[r, j+1:] v) v^T for all rows
-  for (int r = hw; r < n; r += hnw) {
-    float a[NV];
-    float dot = 0.f;
+  for (int r0 = HB * hw; r0 < n; r0 += HB * hnw) {
+    float a[HB][NV];
+    float dot[HB];
 #pragma unroll
-    for (int q = 0; q < NV; ++q) {
-      const int c = hl + 32 * q;
-      a[q] = (c < len) ? A[r * ld + j + 1 + c] : 0.f;
-      dot = fmaf(a[q], vreg[q], dot);
+    for (int b = 0; b < HB; ++b) {
+      dot[b] = 0.f;
+      const bool ok = r0 + b < n;
+#pragma unroll
+      for (int q = 0; q < NV; ++q) {
+        const int c = hl + 32 * q;
+        a[b][q] = (ok && c < len) ? A[(r0 + b) * ld + j + 1 + c] : 0.f;
+        dot[b] = fmaf(a[b][q], vreg[q], dot[b]);
+      }
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
-    const float sc = dot * beta;
+    for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
-    for (int q = 0; q < NV; ++q) {
-      const int c = hl + 32 * q;
-      if (c < len) A[r * ld + j + 1 + c] = fmaf(-sc, vreg[q], a[q]);
+      for (int b = 0; b < HB; ++b) dot[b] += __shfl_xor_sync(0xffffffffu, dot[b], o);
+#pragma unroll
+    for (int b = 0; b < HB; ++b) {
+      if (r0 + b >= n) break;
+      const float sc = dot[b] * beta;
+#pragma unroll
+      for (int q = 0; q < NV; ++q) {
+        const int c = hl + 32 * q;
+        if (c < len) A[(r0 + b) * ld + j + 1 + c] = fmaf(-sc, vreg[q], a[b][q]);
+      }
     }
   }
 }

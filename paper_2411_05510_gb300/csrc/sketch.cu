@@ -12,9 +12,13 @@
 // loads the tile straight from the BF16 covariance store.  For T the tile is K-major
 // (64-byte swizzle, 32 columns), for T^T the same bytes are read MN-major (128-byte
 // swizzle), so one store serves both products.  X is MN-major.  Split-BF16: three
-// MMAs per k-step.  Two TMEM accumulators let the epilogue of one unit overlap the
-// MMAs of the next.  A unit is (M tile, N tile, K split); FP32 partials per split
-// are summed by k_sum_splits.
+// MMAs per k-step.  A CTA takes MT (1 or 2) M tiles against one N tile of X: with two,
+// a stage brings 64 KB for twelve 128 x 256 x 16 MMAs instead of 48 KB for six, which
+// is what keeps the tensor pipe fed from L2.  When the accumulators of a unit use at
+// most half of TMEM, two sets let the epilogue of one unit overlap the MMAs of the
+// next; otherwise the epilogue (a few hundred cycles against the unit's thousands of
+// MMA cycles) runs between units.  A unit is (M tile group, N tile, K split); FP32
+// partials per split are summed by k_sum_splits.
 #include "common.cuh"
 #include "blackwell.cuh"
 
@@ -23,7 +27,8 @@ namespace ssi {
 // qr.cu / svd.cu
 size_t qr_ws_bytes(int ncols, int num_sms);
 ssi_status qr_launch(ssi_ctx* ctx, Workspace& ws, float* A, int rows, int ncols, int ld,
-                     float* Rout, int* status, cudaStream_t stream, bool shared_device);
+                     float* Rout, int* status, cudaStream_t stream, bool shared_device,
+                     int chunks_per_cta = 0);
 size_t jacobi_ws_bytes(int K, int num_sms, bool fp64);
 ssi_status jacobi_launch64(Workspace& ws, const float* R2, int K, double* Ut, double* S, int* status,
                            int num_sms, int block, cudaStream_t stream);
@@ -151,18 +156,22 @@ struct TgParams {
 };
 
 // ------------------------------------------------------------------ tcgen05 Toeplitz GEMM
-template <int MODE, int NB, int STAGES>
+template <int MODE, int NB, int MT, int STAGES>
 __global__ void __launch_bounds__(TG_THREADS, 1)
     k_toeplitz_gemm_tc(const __grid_constant__ CUtensorMap tA_hi, const __grid_constant__ CUtensorMap tA_lo,
                        const __grid_constant__ CUtensorMap tB_hi, const __grid_constant__ CUtensorMap tB_lo,
                        TgParams p, float* __restrict__ partial, int* __restrict__ status) {
   constexpr int NT = 64 * NB;
-  constexpr int A_BYTES = 2 * BOX_BYTES;
+  constexpr int A_BYTES = 2 * BOX_BYTES;          // one M tile: two 64-row boxes
   constexpr int B_BYTES = NB * BOX_BYTES;
-  constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+  constexpr int STAGE_BYTES = MT * 2 * A_BYTES + 2 * B_BYTES;
+  constexpr int ACC = MT * NT;                    // TMEM columns of one unit's accumulators
+  constexpr int NBUF = 2 * ACC <= 512 ? 2 : 1;
   constexpr uint32_t IDESC = bw::idesc_bf16(128, NT, MODE, 1);
-  constexpr uint32_t TMEM_COLS = (2 * NT <= 32) ? 32 : (2 * NT <= 64) ? 64 : (2 * NT <= 128) ? 128
-                                 : (2 * NT <= 256) ? 256 : 512;
+  constexpr uint32_t TMEM_COLS = (NBUF * ACC <= 32) ? 32 : (NBUF * ACC <= 64) ? 64
+                                 : (NBUF * ACC <= 128) ? 128 : (NBUF * ACC <= 256) ? 256 : 512;
+  static_assert(NBUF * ACC <= 512, "accumulators exceed TMEM");
+  static_assert(4 * MT + 2 * NB <= 32, "one lane per box");
 
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(
@@ -179,6 +188,9 @@ __global__ void __launch_bounds__(TG_THREADS, 1)
   auto empty_bar = [&](int s) { return bar_base + 8u * (STAGES + s); };
   auto tfull_bar = [&](int b) { return bar_base + 8u * (2 * STAGES + b); };
   auto tempty_bar = [&](int b) { return bar_base + 8u * (2 * STAGES + 2 + b); };
+  // accumulator set of the uc-th unit of this CTA, and how often that set was used before
+  auto acc_buf = [](int uc) { return NBUF == 2 ? (uc & 1) : 0; };
+  auto acc_use = [](int uc) { return NBUF == 2 ? (uc >> 1) : uc; };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -228,14 +240,14 @@ __global__ void __launch_bounds__(TG_THREADS, 1)
 
   if (warp == 0) {
     // Lane 0 takes the barrier waits and the transaction count; each box of a stage
-    // (A: 2 halves x hi/lo, B: NB atoms x hi/lo) is issued by its own lane.
+    // (A: MT tiles x 2 halves x hi/lo, B: NB atoms x hi/lo) is issued by its own lane.
     int g = 0;
     int armed_phase[STAGES];
     for (int s = 0; s < STAGES; ++s) armed_phase[s] = -1;
     bool ok = true;
     const bool lo_half = (lane & 1) != 0;
-    const bool a_box = lane < 4;
-    const bool b_box = lane >= 4 && lane < 4 + 2 * NB;
+    const bool a_box = lane < 4 * MT;
+    const bool b_box = lane >= 4 * MT && lane < 4 * MT + 2 * NB;
     const CUtensorMap* a_map = lo_half ? &tA_lo : &tA_hi;
     const CUtensorMap* b_map = lo_half ? &tB_lo : &tB_hi;
     for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x) {
@@ -243,7 +255,7 @@ __global__ void __launch_bounds__(TG_THREADS, 1)
       const int nt = (u / p.n_mt) % p.n_nt;
       int j_begin, n_st;
       unit_krange(u, j_begin, n_st);
-      const int m0 = mt * 128;
+      const int m0 = mt * 128 * MT;
       for (int st = 0; st < n_st; ++st, ++g) {
         const int s = g % STAGES;
         const uint32_t ph = (g / STAGES) & 1;
@@ -260,8 +272,8 @@ __global__ void __launch_bounds__(TG_THREADS, 1)
         const uint32_t sb = smem_base + s * STAGE_BYTES;
         const int j0 = j_begin + st * SBK;
         if (a_box) {
-          const int h = lane >> 1;
-          const int mrow = m0 + 64 * h;
+          const int t = lane >> 2, h = (lane >> 1) & 1;
+          const int mrow = m0 + 128 * t + 64 * h;
           int lag, x, y;
           if (MODE == 0) {
             const int a = mrow / p.l_pad, c0 = mrow % p.l_pad;
@@ -276,11 +288,12 @@ __global__ void __launch_bounds__(TG_THREADS, 1)
             x = d0;
             y = (lag - 1) * p.l_pad + c0;
           }
-          bw::tma_load_2d(sb + (lo_half ? A_BYTES : 0) + h * BOX_BYTES, a_map, full_bar(s), x, y);
+          bw::tma_load_2d(sb + t * 2 * A_BYTES + (lo_half ? A_BYTES : 0) + h * BOX_BYTES, a_map,
+                          full_bar(s), x, y);
         } else if (b_box) {
-          const int bb = (lane - 4) >> 1;
+          const int bb = (lane - 4 * MT) >> 1;
           const int x = nt * NT + bb * 64;
-          bw::tma_load_2d(sb + 2 * A_BYTES + (lo_half ? B_BYTES : 0) + bb * BOX_BYTES, b_map,
+          bw::tma_load_2d(sb + MT * 2 * A_BYTES + (lo_half ? B_BYTES : 0) + bb * BOX_BYTES, b_map,
                           full_bar(s), x, j0);
         }
       }
@@ -301,10 +314,10 @@ __global__ void __launch_bounds__(TG_THREADS, 1)
       for (int u = blockIdx.x; u < n_units && ok; u += gridDim.x, ++uc) {
         int j_begin, n_st;
         unit_krange(u, j_begin, n_st);
-        const int buf = uc & 1;
-        if (!wait(tempty_bar(buf), ((uc >> 1) & 1) ^ 1)) { ok = false; break; }
+        const int buf = acc_buf(uc);
+        if (!wait(tempty_bar(buf), (acc_use(uc) & 1) ^ 1)) { ok = false; break; }
         bw::tc_fence_after();
-        const uint32_t d = tmem_base + buf * NT;
+        const uint32_t d = tmem_base + buf * ACC;
         for (int st = 0; st < n_st; ++st, ++g) {
           const int s = g % STAGES;
           const uint32_t ph = (g / STAGES) & 1;
@@ -313,19 +326,25 @@ __global__ void __launch_bounds__(TG_THREADS, 1)
           const uint32_t sb = smem_base + s * STAGE_BYTES;
 #pragma unroll
           for (int kk = 0; kk < SBK / 16; ++kk) {
-            uint64_t ah, al;
-            if (MODE == 0) {
-              ah = bw::smem_desc(sb + kk * 32, 16, 512, bw::SMEM_SW64);
-              al = bw::smem_desc(sb + A_BYTES + kk * 32, 16, 512, bw::SMEM_SW64);
-            } else {
-              ah = bw::smem_desc(sb + kk * 2048, BOX_BYTES, 1024, bw::SMEM_SW128);
-              al = bw::smem_desc(sb + A_BYTES + kk * 2048, BOX_BYTES, 1024, bw::SMEM_SW128);
+            const uint32_t sbb = sb + MT * 2 * A_BYTES;
+            const uint64_t bh = bw::smem_desc(sbb + kk * 2048, BOX_BYTES, 1024, bw::SMEM_SW128);
+            const uint64_t bl = bw::smem_desc(sbb + B_BYTES + kk * 2048, BOX_BYTES, 1024, bw::SMEM_SW128);
+#pragma unroll
+            for (int t = 0; t < MT; ++t) {
+              const uint32_t sa = sb + t * 2 * A_BYTES;
+              uint64_t ah, al;
+              if (MODE == 0) {
+                ah = bw::smem_desc(sa + kk * 32, 16, 512, bw::SMEM_SW64);
+                al = bw::smem_desc(sa + A_BYTES + kk * 32, 16, 512, bw::SMEM_SW64);
+              } else {
+                ah = bw::smem_desc(sa + kk * 2048, BOX_BYTES, 1024, bw::SMEM_SW128);
+                al = bw::smem_desc(sa + A_BYTES + kk * 2048, BOX_BYTES, 1024, bw::SMEM_SW128);
+              }
+              const uint32_t dt = d + t * NT;
+              bw::umma_bf16(dt, ah, bh, IDESC, (st > 0 || kk > 0) ? 1u : 0u);
+              bw::umma_bf16(dt, ah, bl, IDESC, 1u);
+              bw::umma_bf16(dt, al, bh, IDESC, 1u);
             }
-            const uint64_t bh = bw::smem_desc(sb + 2 * A_BYTES + kk * 2048, BOX_BYTES, 1024, bw::SMEM_SW128);
-            const uint64_t bl = bw::smem_desc(sb + 2 * A_BYTES + B_BYTES + kk * 2048, BOX_BYTES, 1024, bw::SMEM_SW128);
-            bw::umma_bf16(d, ah, bh, IDESC, (st > 0 || kk > 0) ? 1u : 0u);
-            bw::umma_bf16(d, ah, bl, IDESC, 1u);
-            bw::umma_bf16(d, al, bh, IDESC, 1u);
           }
           bw::umma_commit(empty_bar(s));
         }
@@ -340,26 +359,29 @@ __global__ void __launch_bounds__(TG_THREADS, 1)
       const int mt = u % p.n_mt;
       const int nt = (u / p.n_mt) % p.n_nt;
       const int sp = (u / p.n_mt) / p.n_nt;
-      const int buf = uc & 1;
+      const int buf = acc_buf(uc);
       bool ok = true;
-      if (lane == 0) ok = wait(tfull_bar(buf), (uc >> 1) & 1);
+      if (lane == 0) ok = wait(tfull_bar(buf), acc_use(uc) & 1);
       ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
       if (!ok) break;
       bw::tc_fence_after();
-      const int row = mt * 128 + quarter * 32 + lane;
-      const bool valid = row < p.L_pad;   // the last M tile may hang over the matrix
-      float* dst = partial + (long long)sp * p.split_stride + (long long)(valid ? row : 0) * p.ld + nt * NT;
 #pragma unroll 1
-      for (int cb = 0; cb < NT / 32; ++cb) {
-        uint32_t r[32];
-        bw::tmem_ld_32x32(tmem_base + ((uint32_t)(quarter * 32) << 16) + buf * NT + cb * 32, r);
-        bw::tmem_ld_wait();
-        if (valid) {
-          float4* d4 = reinterpret_cast<float4*>(dst + cb * 32);
+      for (int t = 0; t < MT; ++t) {
+        const int row = mt * 128 * MT + 128 * t + quarter * 32 + lane;
+        const bool valid = row < p.L_pad;   // the last M tile may hang over the matrix
+        float* dst = partial + (long long)sp * p.split_stride + (long long)(valid ? row : 0) * p.ld + nt * NT;
+#pragma unroll 1
+        for (int cb = 0; cb < NT / 32; ++cb) {
+          uint32_t r[32];
+          bw::tmem_ld_32x32(tmem_base + ((uint32_t)(quarter * 32) << 16) + buf * ACC + t * NT + cb * 32, r);
+          bw::tmem_ld_wait();
+          if (valid) {
+            float4* d4 = reinterpret_cast<float4*>(dst + cb * 32);
 #pragma unroll
-          for (int j = 0; j < 8; ++j)
-            d4[j] = make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]),
-                                __uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3]));
+            for (int j = 0; j < 8; ++j)
+              d4[j] = make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]),
+                                  __uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3]));
+          }
         }
       }
       bw::tc_fence_before();
@@ -452,21 +474,24 @@ __global__ void k_convert(const TI* __restrict__ x, long long n, TO* __restrict_
     y[e] = (TO)x[e];
 }
 
-template <int MODE, int NB>
-constexpr int tg_stages() {
-  return (200 * 1024) / (2 * 2 * BOX_BYTES + 2 * NB * BOX_BYTES) > 6
-             ? 6
-             : (200 * 1024) / (2 * 2 * BOX_BYTES + 2 * NB * BOX_BYTES);
+template <int NB, int MT>
+constexpr int tg_stage_bytes() {
+  return MT * 4 * BOX_BYTES + 2 * NB * BOX_BYTES;
 }
 
-template <int MODE, int NB>
+template <int NB, int MT>
+constexpr int tg_stages() {
+  return (200 * 1024) / tg_stage_bytes<NB, MT>() > 6 ? 6 : (200 * 1024) / tg_stage_bytes<NB, MT>();
+}
+
+template <int MODE, int NB, int MT>
 ssi_status launch_tg(const CUtensorMap& ah, const CUtensorMap& al, const CUtensorMap& bh,
                      const CUtensorMap& bl, const TgParams& p, float* partial, int* status, int grid,
                      cudaStream_t stream) {
-  constexpr int STAGES = tg_stages<MODE, NB>();
-  constexpr int STAGE_BYTES = 4 * BOX_BYTES + 2 * NB * BOX_BYTES;
+  constexpr int STAGES = tg_stages<NB, MT>();
+  constexpr int STAGE_BYTES = tg_stage_bytes<NB, MT>();
   const size_t smem = 1024 + (size_t)STAGES * STAGE_BYTES + 8 * (2 * STAGES + 4) + 16;
-  auto kern = k_toeplitz_gemm_tc<MODE, NB, STAGES>;
+  auto kern = k_toeplitz_gemm_tc<MODE, NB, MT, STAGES>;
   SSI_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   kern<<<grid, TG_THREADS, smem, stream>>>(ah, al, bh, bl, p, partial, status);
   SSI_CUDA(cudaGetLastError());
@@ -474,16 +499,28 @@ ssi_status launch_tg(const CUtensorMap& ah, const CUtensorMap& al, const CUtenso
 }
 
 template <int MODE>
-ssi_status launch_tg_nb(int nb, const CUtensorMap& ah, const CUtensorMap& al, const CUtensorMap& bh,
-                        const CUtensorMap& bl, const TgParams& p, float* partial, int* status,
-                        int grid, cudaStream_t stream) {
-  switch (nb) {
-    case 1: return launch_tg<MODE, 1>(ah, al, bh, bl, p, partial, status, grid, stream);
-    case 2: return launch_tg<MODE, 2>(ah, al, bh, bl, p, partial, status, grid, stream);
-    case 3: return launch_tg<MODE, 3>(ah, al, bh, bl, p, partial, status, grid, stream);
-    case 4: return launch_tg<MODE, 4>(ah, al, bh, bl, p, partial, status, grid, stream);
-    default: set_error("toeplitz gemm: unsupported N tiling %d", nb); return SSI_E_INVALID;
+ssi_status launch_tg_nb(int nb, int mt, const CUtensorMap& ah, const CUtensorMap& al,
+                        const CUtensorMap& bh, const CUtensorMap& bl, const TgParams& p,
+                        float* partial, int* status, int grid, cudaStream_t stream) {
+  if (mt == 2) {
+    switch (nb) {
+      case 1: return launch_tg<MODE, 1, 2>(ah, al, bh, bl, p, partial, status, grid, stream);
+      case 2: return launch_tg<MODE, 2, 2>(ah, al, bh, bl, p, partial, status, grid, stream);
+      case 3: return launch_tg<MODE, 3, 2>(ah, al, bh, bl, p, partial, status, grid, stream);
+      case 4: return launch_tg<MODE, 4, 2>(ah, al, bh, bl, p, partial, status, grid, stream);
+      default: break;
+    }
+  } else {
+    switch (nb) {
+      case 1: return launch_tg<MODE, 1, 1>(ah, al, bh, bl, p, partial, status, grid, stream);
+      case 2: return launch_tg<MODE, 2, 1>(ah, al, bh, bl, p, partial, status, grid, stream);
+      case 3: return launch_tg<MODE, 3, 1>(ah, al, bh, bl, p, partial, status, grid, stream);
+      case 4: return launch_tg<MODE, 4, 1>(ah, al, bh, bl, p, partial, status, grid, stream);
+      default: break;
+    }
   }
+  set_error("toeplitz gemm: unsupported tiling (N atoms %d, M tiles %d)", nb, mt);
+  return SSI_E_INVALID;
 }
 
 // Reduction splits of the Toeplitz products: the count in [2, 16] whose units
@@ -533,7 +570,7 @@ ssi_status gaussian_omega_launch(int rows, int cols, int ld, uint64_t seed, floa
 }
 
 RsvdPlan rsvd_plan(int l, int i, int k, int oversample, int q, int num_sms, int splits_req,
-                   int jacobi_block) {
+                   int jacobi_block, int qr_cpc) {
   RsvdPlan r{};
   r.l = l;
   r.i = i;
@@ -545,12 +582,16 @@ RsvdPlan rsvd_plan(int l, int i, int k, int oversample, int q, int num_sms, int 
   r.L_pad = r.l_pad * i;
   const int n_nt = (int)ceil_div(round_up(r.K, 64), 256);
   r.Kp = (int)round_up(r.K, 64 * n_nt);
-  const int n_mt = r.L_pad / 128 + (r.L_pad % 128 ? 1 : 0);
+  // two M tiles per CTA halve the operand bytes per MMA of X; small T keeps one so that
+  // the units still fill the SMs
+  r.tg_mt = r.L_pad >= 2048 ? 2 : 1;
+  const int n_mt = (int)ceil_div(r.L_pad, 128 * r.tg_mt);
   int S = splits_req > 0 ? std::min(splits_req, 64) : toeplitz_splits(r.L_pad, n_mt * n_nt, num_sms);
   const int krows = (int)round_up(ceil_div(r.L_pad, S), SBK);
   S = (int)ceil_div(r.L_pad, krows);
   r.tg_splits = S;
   r.jacobi_block = jacobi_block;
+  r.qr_cpc = qr_cpc;
   const int n_lag = 2 * i - 1;
   const size_t rblk = (size_t)n_lag * r.l_pad * r.l_pad;
   const size_t xsz = (size_t)r.L_pad * r.Kp;
@@ -588,7 +629,7 @@ ssi_status toeplitz_rsvd_ws(ssi_ctx* ctx, Workspace& ws, const RsvdPlan& r, cons
   p.i = r.i;
   p.l_pad = r.l_pad;
   p.L_pad = r.L_pad;
-  p.n_mt = (int)ceil_div(r.L_pad, 128);
+  p.n_mt = (int)ceil_div(r.L_pad, 128 * r.tg_mt);
   p.n_nt = n_nt;
   p.krows = (int)round_up(ceil_div(r.L_pad, r.tg_splits), SBK);
   p.n_split = (int)ceil_div(r.L_pad, p.krows);
@@ -654,9 +695,11 @@ ssi_status toeplitz_rsvd_ws(ssi_ctx* ctx, Workspace& ws, const RsvdPlan& r, cons
     if (tc) {
       ProfScope ps(ctx, ST_SKETCH_GEMM, stream);
       if (mode == 0)
-        SSI_TRY(launch_tg_nb<0>(nb, tAn_h, tAn_l, tX_h, tX_l, p, part, dev_status, grid_tc, stream));
+        SSI_TRY(launch_tg_nb<0>(nb, r.tg_mt, tAn_h, tAn_l, tX_h, tX_l, p, part, dev_status, grid_tc,
+                                stream));
       else
-        SSI_TRY(launch_tg_nb<1>(nb, tAt_h, tAt_l, tX_h, tX_l, p, part, dev_status, grid_tc, stream));
+        SSI_TRY(launch_tg_nb<1>(nb, r.tg_mt, tAt_h, tAt_l, tX_h, tX_l, p, part, dev_status, grid_tc,
+                                stream));
     } else {
       ProfScope ps(ctx, ST_SKETCH_GEMM, stream);
       dim3 g((unsigned)(r.L_pad / 64), (unsigned)(r.Kp / 64), (unsigned)p.n_split);
@@ -675,7 +718,8 @@ ssi_status toeplitz_rsvd_ws(ssi_ctx* ctx, Workspace& ws, const RsvdPlan& r, cons
     ws.off = ws_mark;
     ProfScope ps(ctx, ST_QR, stream);
     count_launches(ctx, 1);
-    return qr_launch(ctx, ws, Yb, r.L_pad, r.K, r.Kp, Rout, dev_status, stream, shared_device);
+    return qr_launch(ctx, ws, Yb, r.L_pad, r.K, r.Kp, Rout, dev_status, stream, shared_device,
+                     r.qr_cpc);
   };
 
   // Y = T Omega; Q = qr(Y)

@@ -18,12 +18,27 @@
 // after max_sweeps (status bit set).  Every reduction runs in a fixed order, so the
 // result does not depend on timing.
 //
+// When the grid is small enough for one thread-block cluster (C <= 8 CTAs), the rounds
+// run in k_cluster_jacobi instead: the same schedule and the same rotations in the same
+// order (so the same result), but the blocks stay in shared memory for the whole launch.
+// Between rounds each CTA copies the two blocks of its next round out of the shared
+// memory of the CTAs that hold them (distributed shared memory, double-buffered), and
+// the CTAs meet at the cluster's hardware barrier instead of a barrier on a global
+// counter.
+//
 // The scalar type is FP32 (the default small-problem arithmetic) or FP64.
 #include <algorithm>
 #include <cmath>
+#include <map>
+#include <mutex>
+#include <utility>
+
+#include <cooperative_groups.h>
 
 #include "blackwell.cuh"
 #include "common.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace ssi {
 
@@ -233,6 +248,152 @@ __global__ void __launch_bounds__(BJ_THREADS, 1) k_block_jacobi(BjParams<T> p) {
   }
 }
 
+// position of player P at round r of the circle schedule (the inverse of circle_player)
+__device__ __forceinline__ int circle_pos(int P, int r, int np) {
+  if (P == 0) return 0;
+  int v = (P - 1 - r) % (np - 1);
+  if (v < 0) v += np - 1;
+  return 1 + v;
+}
+
+constexpr int BJ_CLUSTER_MAX = 8;   // portable cluster size
+
+// The block ordering of k_block_jacobi on one cluster of C = gridDim.x CTAs (grid =
+// cluster).  Shared memory holds two buffers of two blocks (bw x ldk each); round g
+// computes on buffer g & 1 and then pulls the next round's blocks into the other one.
+// A peer reads buffer g & 1 of this CTA only between the barriers that close rounds g
+// and g + 1, and this CTA rewrites it only after the barrier closing round g + 1, so one
+// cluster barrier per round suffices.  Every CTA takes the same number of barriers: the
+// end of a sweep is decided from every CTA's rotation flag, read after the barrier.
+template <typename T>
+__global__ void __launch_bounds__(BJ_THREADS, 1) k_cluster_jacobi(BjParams<T> p) {
+  extern __shared__ __align__(16) unsigned char bj_smem_raw[];
+  T* smem = reinterpret_cast<T*>(bj_smem_raw);
+  cg::cluster_group cl = cg::this_cluster();
+  __shared__ int s_rot;
+  __shared__ int s_flag[2];
+  __shared__ T s_norm[2][64];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int K = p.K, bw = p.bw, np = p.n_blk, C = np / 2;
+  const int me = (int)cl.block_rank();
+  const int ld = p.ldk;
+  const size_t slot = (size_t)bw * ld;
+  auto buf = [&](int b, int s) { return smem + (size_t)(2 * b + s) * slot; };
+  auto ncols = [&](int P) { return max(0, min(bw, K - P * bw)); };
+  // round 0: the CTA's two blocks straight from R2 (column c of B = row c of R2)
+  for (int s = 0; s < 2; ++s) {
+    const int P = circle_player(s ? np - 1 - me : me, 0, np);
+    const int c0 = P * bw, nc = ncols(P);
+    T* dst = buf(0, s);
+    for (int e = tid; e < nc * K; e += BJ_THREADS)
+      dst[(size_t)(e / K) * ld + e % K] = (T)p.R2[(size_t)(c0 + e / K) * K + e % K];
+  }
+  if (tid == 0) {
+    s_flag[0] = 0;
+    s_flag[1] = 0;
+  }
+  __syncthreads();
+  int cur = 0, pa = 0, pb = 0;
+  int sweep = 0;
+  bool converged = false;
+  for (; sweep < p.max_sweeps && !converged; ++sweep) {
+    if (tid == 0) s_rot = 0;
+    bool rot = false;
+    for (int rnd = 0; rnd < np - 1; ++rnd) {
+      pa = circle_player(me, rnd, np);
+      pb = circle_player(np - 1 - me, rnd, np);
+      const int na = ncols(pa), nb = ncols(pb);
+      T* A = buf(cur, 0);
+      T* Bk = buf(cur, 1);
+      if (rnd == 0) {
+        const int bwe = bw + (bw & 1), half = bwe / 2;
+        for (int ir = 0; ir < bwe - 1; ++ir) {
+          for (int q = warp; q < 2 * half; q += BJ_WARPS) {
+            const int which = q / half, j = q % half;
+            int u = circle_player(j, ir, bwe), v = circle_player(bwe - 1 - j, ir, bwe);
+            const int ncol = which ? nb : na;
+            if (u < ncol && v < ncol) {
+              T* base = which ? Bk : A;
+              rot |= rotate_pair(base + (size_t)u * ld, base + (size_t)v * ld, K, p.tol, lane);
+            }
+          }
+          __syncthreads();
+        }
+      }
+      for (int ir = 0; ir < bw; ++ir) {
+        for (int j = warp; j < bw; j += BJ_WARPS) {
+          const int v = (j + ir) % bw;
+          if (j < na && v < nb)
+            rot |= rotate_pair(A + (size_t)j * ld, Bk + (size_t)v * ld, K, p.tol, lane);
+        }
+        __syncthreads();
+      }
+      const bool last = rnd == np - 2;
+      if (last) {
+        if (rot && lane == 0) s_rot = 1;
+        __syncthreads();
+        if (tid == 0) s_flag[sweep & 1] = s_rot;
+      }
+      cl.sync();
+      if (last) {
+        int any = 0;
+        for (int r = 0; r < C; ++r) any |= *cl.map_shared_rank(&s_flag[sweep & 1], r);
+        converged = any == 0;
+        if (converged || sweep + 1 == p.max_sweeps) break;   // the blocks stay where they are
+      }
+      // pull the next round's two blocks (round rnd + 1, modulo np - 1)
+      const int r1 = rnd + 1;
+      for (int s = 0; s < 2; ++s) {
+        const int P = circle_player(s ? np - 1 - me : me, r1, np);
+        const int pos = circle_pos(P, rnd, np);
+        const int holder = pos < C ? pos : np - 1 - pos, hs = pos < C ? 0 : 1;
+        const uint4* src = reinterpret_cast<const uint4*>(cl.map_shared_rank(buf(cur, hs), holder));
+        uint4* dst = reinterpret_cast<uint4*>(buf(cur ^ 1, s));
+        const int n16 = (int)((size_t)ncols(P) * ld * sizeof(T) / 16);
+        for (int e = tid; e < n16; e += BJ_THREADS) dst[e] = src[e];
+      }
+      __syncthreads();
+      cur ^= 1;
+    }
+  }
+  if (!converged && me == 0 && tid == 0) atomicOr(p.status, DEV_NOTCONVERGED);
+  // column norms of the CTA's two blocks (players pa and pb of the last round)
+  for (int q = warp; q < 2 * bw; q += BJ_WARPS) {
+    const int s = q / bw, j = q % bw, P = s ? pb : pa;
+    if (j >= ncols(P)) continue;
+    const T* col = buf(cur, s) + (size_t)j * ld;
+    T v = 0;
+    for (int r = lane; r < K; r += 32) v = fma(col[r], col[r], v);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) {
+      s_norm[s][j] = bj_sqrt(v);
+      p.norms[P * bw + j] = bj_sqrt(v);
+    }
+  }
+  __threadfence();
+  cl.sync();
+  for (int q = warp; q < 2 * bw; q += BJ_WARPS) {
+    const int s = q / bw, j = q % bw, P = s ? pb : pa;
+    if (j >= ncols(P)) continue;
+    const int c = P * bw + j;
+    const T v = s_norm[s][j];
+    int rank = 0;
+    for (int d = lane; d < K; d += 32) {
+      const T u = *(volatile T*)&p.norms[d];
+      rank += (u > v) || (u == v && d < c);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) rank += __shfl_xor_sync(0xffffffffu, rank, o);
+    if (lane == 0) p.S[rank] = v;
+    const T inv = v > T(0) ? T(1) / v : T(0);
+    const T* col = buf(cur, s) + (size_t)j * ld;
+    for (int r = lane; r < K; r += 32) p.Ut[(size_t)r * K + rank] = col[r] * inv;
+  }
+  // no CTA leaves while a peer may still read its shared memory
+  cl.sync();
+}
+
 // Grid of the block ordering: C CTAs, 2C blocks of bw columns.  FP32 rounds are short
 // and latency-bound, so fewer, wider blocks (about 14 columns) keep the barrier count
 // low; FP64 work is bound by the FP64 pipes (two FMA per clock per SM), so it spreads
@@ -267,6 +428,40 @@ size_t bj_ws_bytes_t(int K, int num_sms) {
   return w.bytes;
 }
 
+// Whether a cluster of C CTAs with `smem` bytes of dynamic shared memory each can be
+// resident on this device (asked once per shape and device).
+template <typename T>
+bool cluster_fits(int C, size_t smem) {
+  static std::mutex mu;
+  static std::map<std::pair<int, std::pair<int, size_t>>, bool> known;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  std::lock_guard<std::mutex> lk(mu);
+  const auto key = std::make_pair(dev, std::make_pair(C, smem));
+  auto it = known.find(key);
+  if (it != known.end()) return it->second;
+  bool ok = cudaFuncSetAttribute(k_cluster_jacobi<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)BJ_SMEM_MAX) == cudaSuccess;
+  if (ok) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(C);
+    cfg.blockDim = dim3(BJ_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    ok = cudaOccupancyMaxActiveClusters(&n, k_cluster_jacobi<T>, &cfg) == cudaSuccess && n > 0;
+  }
+  cudaGetLastError();   // a refused query leaves no sticky error behind
+  known[key] = ok;
+  return ok;
+}
+
 template <typename T>
 ssi_status bj_launch(Workspace& ws, const float* R2, int K, T* Ut, T* S, int* status, int num_sms,
                      int block, T tol, int max_sweeps, cudaStream_t stream) {
@@ -296,6 +491,28 @@ ssi_status bj_launch(Workspace& ws, const float* R2, int K, T* Ut, T* S, int* st
     p.ldk = 0;   // the blocks stay in global memory (L2-resident)
   } else {
     p.ldk = (int)round_up(K, 2);
+  }
+  if (g.C <= BJ_CLUSTER_MAX && g.bw <= 64) {
+    // one cluster: four blocks (two buffers of two) in shared memory, 16-byte rows
+    const int ldk = (int)round_up(K, 4);
+    const size_t csmem = (size_t)4 * g.bw * ldk * sizeof(T);
+    if (csmem <= BJ_SMEM_MAX && cluster_fits<T>(g.C, csmem)) {
+      p.ldk = ldk;
+      cudaLaunchConfig_t cfg{};
+      cfg.gridDim = dim3(g.C);
+      cfg.blockDim = dim3(BJ_THREADS);
+      cfg.dynamicSmemBytes = csmem;
+      cfg.stream = stream;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = g.C;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      SSI_CUDA(cudaLaunchKernelEx(&cfg, k_cluster_jacobi<T>, p));
+      return SSI_OK;
+    }
   }
   SSI_CUDA(cudaMemsetAsync(p.flags, 0, 256 * sizeof(int), stream));
   SSI_CUDA(cudaMemsetAsync(p.bar, 0, 64 * sizeof(unsigned), stream));

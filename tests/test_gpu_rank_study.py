@@ -4,21 +4,24 @@ the GPU path against the same search run by the oracle.
 Record: the 10-DOF frame of Sec. 3.1 (Rayleigh 1 % at modes 1 and 4, white forces at
 every floor, 10 floor accelerations, fs = 200 Hz, 5 min), SNR 20 dB.  Orders 10..100 step
 2; HC xi <= 10 %, MPC > 60 %, MPD < 50 %; SC between orders 2 %, 2 %, 5 %; the stable
-poles clustered into modes (tau 0.05); the RSVD's modes match the SVD's when each SVD mode
-nearest to one of the frame's ten generating frequencies has an RSVD mode within 1 % in
-frequency, 1 % in damping and 2 % in 1 - MAC.
+poles clustered into modes (tau 0.05); the RSVD's modes (q = 1) match the SVD's when each
+SVD mode nearest to one of the frame's ten generating frequencies has an RSVD mode within
+1 % in frequency, 1 % in damping and 2 % in 1 - MAC (Sec. 3.1's tolerances).
 
 For j_b = 100 and 120 (T = 1000 and 1200):
-  * the SVD of T: the GPU's full-width range finder against the oracle's Jacobi SVD,
-    leading 2 m = 20 singular values to 1e-4, and the same number of identified modes,
+  * the SVD of T: the GPU's full-width range finder against the singular values of T from
+    LAPACK (numpy), leading 2 m = 20 to 1e-4, and the same number of identified modes,
     each within 1e-3 in frequency;
   * the minimum rank kbar on the grid 2.5 %, 5 %, ...: the GPU's search and the oracle's
     agree to one grid step (a mode whose match criterion sits at its threshold may tip
-    either way between two FP arithmetics).
-The oracle leg (two Jacobi SVDs of 1000-1200 columns and the candidate RSVDs) takes
-several minutes of host time.
+    either way between two FP arithmetics), and so do the decisions before it.
+The oracle leg's reference identification takes the full SVD of T from LAPACK (the
+realisation does not depend on the signs of the singular vectors); its candidates are the
+oracle's RSVD with the same Omega.  Both j_b run in parallel host processes.
 """
+import concurrent.futures as cf
 import math
+import multiprocessing as mp
 
 import numpy as np
 import pytest
@@ -32,6 +35,7 @@ pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 ORDERS = list(range(10, 101, 2))
 TOL = (0.01, 0.01, 0.02)
 SEED = 1
+Q = 1
 JBS = (100, 120)
 
 
@@ -44,9 +48,9 @@ def _record():
 def _oracle_identify(R, jb, l, dt, K):
     T = O.block_toeplitz(R, jb)
     if K >= T.shape[0]:
-        U, s = O.full_svd(T)
+        U, s, _ = np.linalg.svd(T)
     else:
-        U, s = O.rsvd(T, K, 0, 0, SEED)
+        U, s = O.rsvd(T, max(ORDERS), K - max(ORDERS), Q, SEED)
     diag = [[]]
     for n in ORDERS:
         mu, f, xi, Phi, _ = O.realize(U, s, l, jb, n, dt)
@@ -60,28 +64,33 @@ def _oracle_identify(R, jb, l, dt, K):
     return out, s
 
 
+def _oracle_search(jb):
+    from paper_2411_05510_gb300 import rank_study as RS
+    w, Y, f_true = _record()
+    l, dt = Y.shape[0], 1.0 / w["fs"]
+    R = O.covariances(Y.astype(np.float64), 2 * jb - 1)
+    T = l * jb
+    ref, s_ref = _oracle_identify(R, jb, l, dt, T)
+    kbar, trace = None, []
+    for pct in RS.rank_grid(2.5, 50.0, 2.5):
+        K = max(max(ORDERS), int(math.ceil(pct * T / 100.0 - 1e-9)))
+        cand, _ = _oracle_identify(R, jb, l, dt, K)
+        ok = RS.modes_match(ref, cand, TOL, f_true)
+        trace.append((pct, K, ok, len(cand)))
+        if ok:
+            kbar = pct
+            break
+    return jb, dict(ref=ref, s=s_ref, kbar=kbar, trace=trace)
+
+
 @pytest.fixture(scope="module")
 def study():
     from paper_2411_05510_gb300 import rank_study as RS
     w, Y, f_true = _record()
-    l, dt = Y.shape[0], 1.0 / w["fs"]
     R = O.covariances(Y.astype(np.float64), 2 * max(JBS) - 1)
-    grid = RS.rank_grid(2.5, 50.0, 2.5)
-    res = {}
-    for jb in JBS:
-        T = l * jb
-        ref, s_ref = _oracle_identify(R, jb, l, dt, T)
-        kbar, trace = None, []
-        for pct in grid:
-            K = max(max(ORDERS), int(math.ceil(pct * T / 100.0 - 1e-9)))
-            cand, _ = _oracle_identify(R, jb, l, dt, K)
-            ok = RS.modes_match(ref, cand, TOL, f_true)
-            trace.append((pct, K, ok, len(cand)))
-            if ok:
-                kbar = pct
-                break
-        res[jb] = dict(ref=ref, s=s_ref, kbar=kbar, trace=trace)
-    return dict(w=w, Y=Y, R=R, grid=grid, ora=res, f_true=f_true)
+    with cf.ProcessPoolExecutor(len(JBS), mp_context=mp.get_context("spawn")) as ex:
+        res = dict(ex.map(_oracle_search, JBS))
+    return dict(w=w, Y=Y, R=R, grid=RS.rank_grid(2.5, 50.0, 2.5), ora=res, f_true=f_true)
 
 
 @pytest.mark.parametrize("jb", JBS)
@@ -91,7 +100,7 @@ def test_minimum_rank_matches_oracle_search(study, jb):
     w, Y = study["w"], study["Y"]
     l = Y.shape[0]
     ctx = P.Context(0)
-    # the SVD of T: the full-width range finder against the oracle's Jacobi SVD
+    # the SVD of T: the full-width range finder against LAPACK's singular values
     Rd = torch.from_numpy(np.ascontiguousarray(study["R"][:2 * jb - 1])).cuda()
     _, sg = P.ssi_toeplitz_rsvd(ctx, Rd, l, jb, l * jb, 0, 0, SEED, "split_bf16")
     P.check_sync(ctx)
@@ -100,7 +109,7 @@ def test_minimum_rank_matches_oracle_search(study, jb):
     assert rel.max() <= 1e-4, rel.max()
     Yd = torch.from_numpy(Y).cuda()
     kbar, ref, trace = RS.minimum_rank(ctx, Yd, w["fs"], jb, ORDERS, study["grid"], TOL,
-                                       f_names=study["f_true"], seed=SEED)
+                                       f_names=study["f_true"], seed=SEED, q=Q)
     ctx.close()
     ora = study["ora"][jb]
     print(f"jb={jb}: GPU kbar {kbar} trace {trace}; oracle kbar {ora['kbar']} trace {ora['trace']}")
@@ -110,3 +119,7 @@ def test_minimum_rank_matches_oracle_search(study, jb):
     assert kbar is not None and ora["kbar"] is not None
     g = study["grid"]
     assert abs(g.index(kbar) - g.index(ora["kbar"])) <= 1, (kbar, ora["kbar"])
+    # the decisions before kbar agree step by step
+    for a, b in zip(trace, ora["trace"]):
+        if a[0] < min(kbar, ora["kbar"]):
+            assert a[2] == b[2], (a, b)
