@@ -392,8 +392,9 @@ ssi_status ssi_solve(ssi_ctx* ctx, const ssi_job_desc* job, ssi_pole* poles, flo
  * reduction splits, the K x K Jacobi's columns per block and the sketch QR's row chunks
  * per CTA.  ssi_autotune runs solves of `job` (its record included) on an internal
  * stream, one choice at a time, each candidate once untimed and twice timed by the stage
- * profiler, keeps the fastest (for the QR grid, when the context expects several solves
- * at once, the smallest time x CTAs), and stores the four values in the context under
+ * profiler, keeps the fastest (the QR grid is tuned for the shared device only: 2 or 4
+ * chunks per CTA when the context expects several solves at once; a solve alone takes the
+ * whole-device grid), and stores the four values in the context under
  * the job's shape (l, N, lags, k, oversample, precisions); later ssi_solve calls and
  * serving jobs of that shape use them.  The results change only by rounding (the split
  * and block structure orders the sums; the QR grid changes none of its sums).
@@ -405,7 +406,7 @@ typedef struct {
   int32_t cov_rows_per_split;   /* lag GEMM: samples per FP32 partial sum */
   int32_t sketch_splits;        /* Toeplitz GEMMs: reduction splits */
   int32_t jacobi_block;         /* K x K Jacobi: columns per block */
-  int32_t qr_chunks_per_cta;    /* sketch QR: row chunks (one per SM) per CTA of its grid */
+  int32_t qr_chunks_per_cta;    /* sketch QR under concurrency: row chunks (one per SM) per CTA */
   double stage_ms[4];           /* ms per solve of each stage with the chosen value */
 } ssi_tuning;
 ssi_status ssi_autotune(ssi_ctx* ctx, const ssi_job_desc* job, ssi_tuning* out);

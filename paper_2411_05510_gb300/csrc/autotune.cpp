@@ -6,14 +6,20 @@
 // the K x K Jacobi's block width (columns per block of the parallel ordering, which
 // trades grid barriers against the work of one outer round) and the sketch QR's grid (row
 // chunks per CTA: the rows are cut into one chunk per SM, and fewer CTAs meet at cheaper
-// barriers but each does more work).  ssi_autotune times real solves of the job on the
-// calling thread: for each choice in turn (coordinate descent), every candidate runs one
-// untimed and two timed solves with the context's stage profiler on, and the candidate
-// with the smallest time of its own stage is kept -- for the QR grid, when the context
-// expects several solves at once (ssi_set_concurrency), the smallest time x CTAs, the
-// share of the device a QR holds.  The four values are stored in the context under the
-// job's shape (channels, samples, lags, k, oversampling, precisions) and every later plan
-// of that shape, by ssi_solve or the serving loop, uses them.
+// barriers but each does more work, and above two chunks per CTA the rows no longer fit
+// shared memory).  ssi_autotune times real solves of the job on the calling thread: for
+// each choice in turn (coordinate descent), every candidate runs one untimed and two
+// timed solves with the context's stage profiler on, and the candidate with the smallest
+// time of its own stage is kept.  The QR grid is tuned for the shared device only
+// (ssi_set_concurrency > 1): a cooperative grid of every SM cannot start while another
+// solve's kernels hold SMs, so its candidates are grids of at most half the SMs (2 and 4
+// chunks per CTA); a solve alone on the device always takes the whole-device grid (one
+// chunk per CTA: 3.7 ms per solve on the benchmark's shape, against 5.2 ms with two).  (A
+// score of time x CTAs, tried first, picked 8 chunks per CTA: 20.8 ms per solve instead of
+// 3.7, a QR that holds few SMs but stays on the solve's critical path for longer.)  The
+// four values are stored in the context under the job's shape (channels, samples, lags,
+// k, oversampling, precisions) and every later plan of that shape, by ssi_solve or the
+// serving loop, uses them.
 #include <algorithm>
 #include <array>
 #include <cmath>
@@ -56,13 +62,9 @@ std::vector<int> block_candidates(const ssi_job_desc* j) {
   return {6, 8, 10, 14, 20, 28};
 }
 
-std::vector<int> qr_candidates() { return {1, 2, 4, 8}; }
-
-// CTAs of the QR grid with `cpc` chunks per CTA (as qr_launch forms it)
-int qr_ctas(const ssi_job_desc* j, int num_sms, int cpc) {
-  const int rows = (int)round_up(j->l, 64) * j->lags[0];
-  const int C = std::max(1, std::min<int>(num_sms, (int)ceil_div(rows, 32)));
-  return (int)ceil_div(C, std::min(cpc, C));
+std::vector<int> qr_candidates(bool shared) {
+  if (shared) return {2, 4};
+  return {1};
 }
 
 }  // namespace
@@ -116,10 +118,9 @@ extern "C" ssi_status ssi_autotune(ssi_ctx* ctx, const ssi_job_desc* job, ssi_tu
     ctx->prof_on = false;
     const std::vector<int> cand[4] = {cov_candidates(job, ctx->num_sms),
                                       split_candidates(job, ctx->num_sms), block_candidates(job),
-                                      qr_candidates()};
-    const bool shared = ctx->inflight > 1;
+                                      qr_candidates(ctx->inflight > 1)};
     for (int which = 0; which < 4 && st == SSI_OK; ++which) {
-      double bt = 1e300, bcost = 1e300;
+      double bt = 1e300;
       int bv = 0;
       for (int v : cand[which]) {
         std::array<int, 4> tv = best;
@@ -127,9 +128,7 @@ extern "C" ssi_status ssi_autotune(ssi_ctx* ctx, const ssi_job_desc* job, ssi_tu
         double t = 0.0;
         st = time_stage(tv, which, &t);
         if (st != SSI_OK) break;
-        const double cost = (which == 3 && shared) ? t * qr_ctas(job, ctx->num_sms, v) : t;
-        if (cost < bcost) {
-          bcost = cost;
+        if (t < bt) {
           bt = t;
           bv = v;
         }

@@ -524,13 +524,12 @@ ssi_status qr_launch(ssi_ctx* ctx, Workspace& ws, float* A, int rows, int ncols,
   p.ld = ld;
   p.Rout = Rout;
   // chunks: one per SM (fixed for the device and the shape, so the result is too); a CTA
-  // per chunk when the solve has the device to itself, a CTA per two chunks when several
-  // solves (or several lags of one solve) share it, unless the caller (the autotuner)
-  // chose the chunks per CTA.  The grouping changes which CTA sums a chunk, not the
-  // order of any sum.
+  // per chunk when the solve has the device to itself, and when several solves (or
+  // several lags of one solve) share it, a CTA per two chunks or the autotuner's choice
+  // for that case.  The grouping changes which CTA sums a chunk, not the order of any sum.
   const int C = std::max(1, std::min<int>(ctx->num_sms, (int)ceil_div(rows, 32)));
-  const int cpc = chunks_per_cta > 0 ? std::min(chunks_per_cta, C)
-                                     : (ctx->inflight > 1 || shared_device) ? 2 : 1;
+  const bool shared = ctx->inflight > 1 || shared_device;
+  const int cpc = !shared ? 1 : chunks_per_cta > 0 ? std::min(chunks_per_cta, C) : 2;
   const int P = (int)ceil_div(C, cpc);
   p.n_chunks = C;
   p.chunks_per_cta = cpc;

@@ -101,17 +101,56 @@ __device__ bool bj_grid_sync(const BjParams<T>& p, unsigned& n_bar) {
 
 __device__ __forceinline__ float bj_sqrt(float x) { return sqrtf(x); }
 __device__ __forceinline__ double bj_sqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float bj_pow2_inv(float m) { return ldexpf(1.f, -ilogbf(m)); }
+__device__ __forceinline__ double bj_pow2_inv(double m) { return ldexp(1.0, -ilogb(m)); }
+
+// Rotation of columns x, y with a = x.x, b = y.y, g = x.y that makes them orthogonal
+// (Hestenes): with d = (b - a) / 2, t = tan(theta) = sign(d) g / (|d| + hypot(d, g)),
+// c = 1 / sqrt(1 + t^2), s = c t.  Written with D = |d| + hypot(d, g) and
+// h = hypot(D, g): c = D / h, s = sign(d) g / h -- two square roots and one division on
+// the critical path.  d and g are first scaled by a power of two near 1 / max(a, b)
+// (exact), so the squares neither overflow nor lose the larger term.
+template <typename T>
+__device__ __forceinline__ void rotation(T a, T b, T g, T& c, T& s) {
+  const T sc = bj_pow2_inv(a > b ? a : b);
+  const T d = (b - a) * (sc * T(0.5)), gs = g * sc;
+  const T r = bj_sqrt(fma(d, d, gs * gs));
+  const T D = fabs(d) + r;
+  const T inv = T(1) / bj_sqrt(fma(D, D, gs * gs));
+  c = D * inv;
+  s = (d >= T(0) ? gs : -gs) * inv;
+}
 
 // One Jacobi rotation of columns x and y (length K) by one warp; returns whether it
-// rotated (the same in every lane).
+// rotated (the same in every lane).  Columns of up to 32 * BJ_REG entries (8 FP32 or 4
+// FP64 registers a lane per column) stay in registers between the dot products and the
+// update.
 template <typename T>
 __device__ __forceinline__ bool rotate_pair(T* x, T* y, int K, T tol, int lane) {
+  constexpr int BJ_REG = sizeof(T) == 8 ? 4 : 8;
   T a = 0, b = 0, g = 0;
-  for (int r = lane; r < K; r += 32) {
-    const T xv = x[r], yv = y[r];
-    a = fma(xv, xv, a);
-    b = fma(yv, yv, b);
-    g = fma(xv, yv, g);
+  const bool in_reg = K <= 32 * BJ_REG;
+  T xr[BJ_REG], yr[BJ_REG];
+  if (in_reg) {
+#pragma unroll
+    for (int q = 0; q < BJ_REG; ++q) {
+      const int r = lane + 32 * q;
+      xr[q] = r < K ? x[r] : T(0);
+      yr[q] = r < K ? y[r] : T(0);
+    }
+#pragma unroll
+    for (int q = 0; q < BJ_REG; ++q) {
+      a = fma(xr[q], xr[q], a);
+      b = fma(yr[q], yr[q], b);
+      g = fma(xr[q], yr[q], g);
+    }
+  } else {
+    for (int r = lane; r < K; r += 32) {
+      const T xv = x[r], yv = y[r];
+      a = fma(xv, xv, a);
+      b = fma(yv, yv, b);
+      g = fma(xv, yv, g);
+    }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -119,15 +158,25 @@ __device__ __forceinline__ bool rotate_pair(T* x, T* y, int K, T tol, int lane) 
     b += __shfl_xor_sync(0xffffffffu, b, o);
     g += __shfl_xor_sync(0xffffffffu, g, o);
   }
-  if (!(a > T(0) && b > T(0)) || !(fabs(g) > tol * bj_sqrt(a * b))) return false;
-  const T zeta = (b - a) / (T(2) * g);
-  const T t = (zeta >= T(0) ? T(1) : T(-1)) / (fabs(zeta) + bj_sqrt(T(1) + zeta * zeta));
-  const T c = T(1) / bj_sqrt(T(1) + t * t);
-  const T s = c * t;
-  for (int r = lane; r < K; r += 32) {
-    const T xv = x[r], yv = y[r];
-    x[r] = c * xv - s * yv;
-    y[r] = s * xv + c * yv;
+  // rotate when |g| > tol sqrt(a b), i.e. g^2 > tol^2 a b (a, b > 0)
+  if (!(a > T(0) && b > T(0)) || !(g * g > (tol * tol) * (a * b))) return false;
+  T c, s;
+  rotation(a, b, g, c, s);
+  if (in_reg) {
+#pragma unroll
+    for (int q = 0; q < BJ_REG; ++q) {
+      const int r = lane + 32 * q;
+      if (r < K) {
+        x[r] = c * xr[q] - s * yr[q];
+        y[r] = s * xr[q] + c * yr[q];
+      }
+    }
+  } else {
+    for (int r = lane; r < K; r += 32) {
+      const T xv = x[r], yv = y[r];
+      x[r] = c * xv - s * yv;
+      y[r] = s * xv + c * yv;
+    }
   }
   return true;
 }

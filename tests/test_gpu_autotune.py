@@ -29,7 +29,7 @@ def test_autotune_choices_are_stored_and_keep_parity(small):
     poles0, phi0, S0 = P.ssi_solve(ctx, desc)
     t = P.ssi_autotune(ctx, desc)
     assert t["cov_rows_per_split"] >= 512 and t["sketch_splits"] >= 1 and t["jacobi_block"] >= 1, t
-    assert t["qr_chunks_per_cta"] in (1, 2, 4, 8), t
+    assert t["qr_chunks_per_cta"] == 1, t   # one solve at a time: the whole-device QR grid
     assert all(x > 0 for x in t["stage_ms"]), t
     keys = ("cov_rows_per_split", "sketch_splits", "jacobi_block", "qr_chunks_per_cta")
     g = P.ssi_tuning_get(ctx, desc)
