@@ -319,7 +319,7 @@ __device__ __forceinline__ float sgnf(float a, float b) { return b >= 0.f ? fabs
 // columns of the right update); a warp owns HB whole columns (rows) at a time, forms their
 // dot products, reduces the HB sums together (independent shuffle trees, so their
 // latencies overlap), and updates the elements it still holds in registers.  NV slots
-// cover orders up to 32 NV.
+// cover reflectors of up to 32 NV entries.
 constexpr int HB = 4;
 template <int NV>
 __device__ __forceinline__ void hess_update(float* A, int ld, int n, int j, int len, float beta,
@@ -487,9 +487,23 @@ __global__ void __launch_bounds__(EIG_THREADS, 1)
     }
     if (tid == 0) v[n - 1] = beta;   // v has len <= n-2 entries; beta stored at the end
     __syncthreads();
-    if (beta != 0.f)
-      hess_update<((BIG ? N_MAX : SMEM_N_MAX) + 31) / 32>(A, ld, n, j, len, beta, sv, tid >> 5,
-                                                         tid & 31, nth >> 5);
+    if (beta != 0.f) {
+      // as many 32-entry register slots as this reflector has entries: the instruction
+      // count of an update scales with the slots, and the reflectors shrink (the
+      // global-memory kernel keeps one variant)
+      const int hw = tid >> 5, hl = tid & 31, hnw = nth >> 5;
+      switch (BIG ? 0 : (len + 31) / 32) {
+        case 1: hess_update<1>(A, ld, n, j, len, beta, sv, hw, hl, hnw); break;
+        case 2: hess_update<2>(A, ld, n, j, len, beta, sv, hw, hl, hnw); break;
+        case 3: hess_update<3>(A, ld, n, j, len, beta, sv, hw, hl, hnw); break;
+        case 4: hess_update<4>(A, ld, n, j, len, beta, sv, hw, hl, hnw); break;
+        case 5: hess_update<5>(A, ld, n, j, len, beta, sv, hw, hl, hnw); break;
+        case 6: hess_update<6>(A, ld, n, j, len, beta, sv, hw, hl, hnw); break;
+        case 7: hess_update<7>(A, ld, n, j, len, beta, sv, hw, hl, hnw); break;
+        default: hess_update<((BIG ? N_MAX : SMEM_N_MAX) + 31) / 32>(A, ld, n, j, len, beta, sv, hw,
+                                                                    hl, hnw);
+      }
+    }
     __syncthreads();
   }
 
