@@ -59,7 +59,7 @@ std::vector<int> split_candidates(const ssi_job_desc* j, int num_sms) {
 
 std::vector<int> block_candidates(const ssi_job_desc* j) {
   if (j->small == SSI_SMALL_FP64) return {1, 2, 3, 4, 6};
-  return {6, 8, 10, 14, 20, 28};
+  return {6, 8, 10, 12, 14, 16, 20, 28};
 }
 
 std::vector<int> qr_candidates(bool shared) {
