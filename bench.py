@@ -81,6 +81,7 @@ def parse():
     ap.add_argument("--no-fp64-small", action="store_true")
     ap.add_argument("--no-3d", action="store_true")
     ap.add_argument("--no-mix", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--rank-jb-max", type=int, default=500,
                     help="largest time-lag step of --workload rank_study")
@@ -321,6 +322,49 @@ def run_reference(args, world, rank):
 
 
 # ----------------------------------------------------------------------------- serving mix
+def batch_measure(args, dev, n_jobs=8, reps=3):
+    """Eight jobs of the serving mix's shapes (records resident in HBM), solved one
+    ssi_solve after another on one stream, and in one ssi_solve_batch call (their front
+    stages on four forked streams, one k_eig and one k_eig_vectors launch for all of
+    them).  Device time per batch with CUDA events, best of `reps` after a warm-up."""
+    import torch
+    import paper_2411_05510_gb300 as P
+    mix = S.serving_mix(n_jobs, seed=11)
+    Ys = [torch.from_numpy(S.record(w, np.float32)[0]).to(dev) for w in mix]
+    descs = [P.job_desc(Y, w["fs"], w["lags"], w["orders"], k=w["k"], oversample=w["oversample"],
+                        q=w["q"], prec=args.prec, seed=12345) for w, Y in zip(mix, Ys)]
+    ctx = P.Context(dev.index or 0)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn):
+        best = None
+        for r in range(reps + 1):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize(dev)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            P.check_sync(ctx, dev)
+            if r > 0:
+                t = e0.elapsed_time(e1)
+                best = t if best is None else min(best, t)
+        return best
+
+    ctx.profile_read()
+    t_sep = timed(lambda: [P.ssi_solve(ctx, d, device=dev) for d in descs])
+    n_sep = ctx.profile_read()[2]
+    t_bat = timed(lambda: P.ssi_solve_batch(ctx, descs, device=dev))
+    n_bat = ctx.profile_read()[2]
+    ctx.close()
+    return {"value": n_jobs / (t_bat / 1e3), "unit": "solves/s", "jobs": n_jobs,
+            "ms_per_batch": t_bat, "separate_solves_per_s": n_jobs / (t_sep / 1e3),
+            "ms_separate": t_sep, "launches_per_batch": n_bat / (reps + 1),
+            "launches_separate": n_sep / (reps + 1),
+            "shapes": [{"l": w["l"], "N": w["N"], "i": w["lags"][0], "k": w["k"]} for w in mix],
+            "api": "ssi_solve_batch against one ssi_solve per job (CUDA events, best of 3)"}
+
+
 def serving_mix_measure(args, world, rank, n_jobs):
     """The serving configuration: a seeded stream of heterogeneous jobs (16/48/96/186
     channels, N 30000-360000, i 20-80, 5-30 modes), records in pinned host memory, admitted
@@ -1060,6 +1104,12 @@ def main():
             r3["config"] = {"lags": w3["lags"], "orders": "2..200 step 2", "k": w3["k"],
                             "oversample": w3["oversample"], "q": w3["q"], "realisations": 900}
             out["diagram_3d"] = r3
+
+    # several jobs in one call: the mix's job shapes, their eig launches shared
+    if not args.no_batch:
+        rb = batch_measure(args, dev, n_jobs=8)
+        if rank == 0:
+            out["batch"] = rb
 
     # the serving configuration: a heterogeneous job stream through ssi_submit / ssi_poll
     if not args.no_mix:

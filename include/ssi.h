@@ -386,6 +386,27 @@ ssi_status ssi_solve(ssi_ctx* ctx, const ssi_job_desc* job, ssi_pole* poles, flo
                      double* S_out, void* stream);
 
 /* ------------------------------------------------------------------------------
+ * Several jobs in one call, their eigen-decompositions in one launch (the batching
+ * pattern: "jobs of different sizes in one launch"; the paper solves one record at a
+ * time and has no counterpart).  Each job's covariances, range finder and per-lag
+ * factorisations run as in ssi_solve, on up to four internal streams forked from
+ * `stream`. Then one k_eig launch (plus one for orders above 224, if any) and one
+ * k_eig_vectors launch take every (job, lag, order) realisation of the batch, largest
+ * orders first across the jobs. Then each job's stability criteria run on `stream`.
+ * Results are identical to n_jobs separate ssi_solve calls: the same kernels compute
+ * every item in the same arithmetic. Jobs may differ in channels, record length, lags,
+ * orders, k and GEMM precision; all must use SSI_SMALL_FP32 (the FP64 eigensolver runs
+ * one job at a time), else SSI_E_INVALID. poles[i], phi[i]: device buffers of
+ * ssi_job_sizes(&jobs[i]) size; S_out (optional) per job as in ssi_solve.
+ * 1 <= n_jobs <= SSI_BATCH_MAX. Buffers are kept in the context for the next call; like
+ * ssi_solve, one call at a time per context.
+ * ---------------------------------------------------------------------------- */
+#define SSI_BATCH_MAX 64
+ssi_status ssi_solve_batch(ssi_ctx* ctx, int n_jobs, const ssi_job_desc* jobs,
+                           ssi_pole* const* poles, float* const* phi, double* const* S_out,
+                           void* stream);
+
+/* ------------------------------------------------------------------------------
  * Autotuner of a job shape's plan choices (the batching pattern: tile and split shapes
  * picked from timed candidates; the paper has no counterpart).  Four choices are made
  * by cost models otherwise: the lag GEMM's samples per time split, the Toeplitz GEMMs'

@@ -111,6 +111,8 @@ PROTOTYPES = {
     "ssi_job_sizes": (_c.c_int, [_c.POINTER(SsiJobDesc), _c.POINTER(_c.c_int64),
                                  _c.POINTER(_c.c_int64)]),
     "ssi_solve": (_c.c_int, [_P, _c.POINTER(SsiJobDesc), _P, _P, _P, _P]),
+    "ssi_solve_batch": (_c.c_int, [_P, _c.c_int, _c.POINTER(SsiJobDesc), _c.POINTER(_P),
+                                   _c.POINTER(_P), _c.POINTER(_P), _P]),
     "ssi_sync_status": (_c.c_int, [_P, _P]),
     "ssi_autotune": (_c.c_int, [_P, _c.POINTER(SsiJobDesc), _c.POINTER(SsiTuning)]),
     "ssi_tuning_get": (_c.c_int, [_P, _c.POINTER(SsiJobDesc), _c.POINTER(SsiTuning)]),

@@ -22,7 +22,7 @@ __all__ = [
     "stab_params", "job_desc", "ssi_rank_rule", "ssi_lag_rule", "ssi_time_lag", "check_sync",
     "ssi_job_sizes", "ssi_serve_config", "ssi_submit", "ssi_poll", "ssi_release",
     "cluster_params", "ssi_cluster", "CovStream", "ssi_autotune", "ssi_tuning_get",
-    "ssi_tuning_set",
+    "ssi_tuning_set", "ssi_solve_batch",
 ]
 
 PREC = {"fp32": SSI_PREC_FP32, "split_bf16": SSI_PREC_SPLIT_BF16}
@@ -289,6 +289,26 @@ def ssi_solve(ctx: Context, desc: SsiJobDesc, device="cuda", with_s: bool = True
                         ctypes.c_void_p(S.data_ptr() if S is not None else 0),
                         _stream(torch.device(device))), "ssi_solve")
     return poles, phi, S
+
+
+def ssi_solve_batch(ctx: Context, descs, device="cuda", with_s: bool = True):
+    """Several jobs in one call, their eigen-decompositions in one launch; returns a list of
+    (poles, phi, S) as ssi_solve does for each job."""
+    n = len(descs)
+    outs = []
+    for d in descs:
+        n_slots, phi_floats = ssi_job_sizes(d)
+        poles = torch.zeros((n_slots, _lib.POLE_BYTES), dtype=torch.uint8, device=device)
+        phi = torch.zeros((phi_floats,), dtype=torch.float32, device=device)
+        S = torch.zeros((d.n_lags, d.k), dtype=torch.float64, device=device) if with_s else None
+        outs.append((poles, phi, S))
+    arr = (SsiJobDesc * n)(*descs)
+    P = (ctypes.c_void_p * n)(*[o[0].data_ptr() for o in outs])
+    F = (ctypes.c_void_p * n)(*[o[1].data_ptr() for o in outs])
+    Sp = (ctypes.c_void_p * n)(*[o[2].data_ptr() for o in outs]) if with_s else None
+    check(lib.ssi_solve_batch(ctx.ptr, n, arr, P, F, Sp, _stream(torch.device(device))),
+          "ssi_solve_batch")
+    return outs
 
 
 def _tuning_dict(t: SsiTuning) -> dict:

@@ -75,6 +75,7 @@ struct WsPlan {
 
 struct Serving;     // serving.cpp
 struct JobBuffers;  // pipeline.h
+struct BatchState;  // pipeline.cpp
 
 }  // namespace ssi
 
@@ -97,6 +98,7 @@ struct ssi_ctx {
   int* dev_status = nullptr;  // device status word of the direct calls
   ssi::Serving* serving = nullptr;
   ssi::JobBuffers* solve = nullptr;  // buffers of ssi_solve
+  ssi::BatchState* batch = nullptr;  // buffers, streams and tables of ssi_solve_batch
   std::atomic<int> inflight{1};        // solves expected to share the device at once
   std::atomic<long long> launches{0};  // kernels launched through this context
   bool prof_on = false;               // per-stage CUDA-event timers
@@ -169,9 +171,20 @@ struct RealizePlan {
 };
 RealizePlan realize_plan(int n_lags, const int* lags, int l, int k, const int* orders,
                          int n_orders);
+// A realisation prepared but not launched (csrc/realize.cu): with `defer`, realize_ws
+// runs the Gram matrices and factorisations and returns the eig launches' parameters in
+// *defer (free with realize_prep_free); realize_batch_launch then runs the
+// eigen-decompositions of several jobs in one launch each (k_eig, k_eig_vectors), with
+// their parameter blocks and item tables in `table` (realize_batch_table_bytes).
+struct RealizePrep;
 ssi_status realize_ws(ssi_ctx* ctx, Workspace& ws, const RealizePlan& plan, const int* lags,
                       const float* const* U, const int* orders, double dt, ssi_pole* poles,
-                      float* phi, int* dev_status, cudaStream_t stream);
+                      float* phi, int* dev_status, cudaStream_t stream,
+                      RealizePrep** defer = nullptr);
+ssi_status realize_batch_launch(ssi_ctx* ctx, RealizePrep* const* preps, int n, void* table,
+                                size_t table_cap, cudaStream_t stream);
+size_t realize_batch_table_bytes(RealizePrep* const* preps, int n);
+void realize_prep_free(RealizePrep* p);
 
 // FP64 small problems (csrc/eig64.cu): U per lag is (l*i) x k FP64
 size_t realize64_ws_bytes(int n_lags, const int* lags, int l, int k, const int* orders, int n_orders);

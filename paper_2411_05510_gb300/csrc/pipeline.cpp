@@ -90,32 +90,58 @@ JobPlan plan_job(const ssi_job_desc* j, ssi_ctx* ctx, const std::array<int, 4>* 
   return p;
 }
 
-ssi_status run_job(ssi_ctx* ctx, const ssi_job_desc* j, const JobPlan& p, JobBuffers& B,
-                   ssi_pole* poles, float* phi, double* S_out, cudaStream_t stream) {
-  // carve the job buffers
+namespace {
+
+// the job's buffers carved out of B.buf (the same layout on every call of a plan)
+struct JobCarve {
+  int* status;
+  double* R;
+  std::vector<void*> U;
+  char* S;
+  float* Ydev;
+  size_t esz;
+};
+
+ssi_status carve_job(const ssi_job_desc* j, const JobPlan& p, JobBuffers& B, JobCarve& c) {
   Workspace carve;
   carve.base = static_cast<char*>(B.buf);
   carve.cap = B.buf_cap;
   // the status words first: their address must not depend on the job's sizes, because
   // they are cleared only when the buffer is allocated and then reset by each read
-  int* status = carve.take<int>(64);
-  double* R = carve.take<double>((size_t)p.max_lag * j->l * j->l);
+  c.status = carve.take<int>(64);
+  c.R = carve.take<double>((size_t)p.max_lag * j->l * j->l);
   const bool s64 = j->small == SSI_SMALL_FP64;
-  const size_t esz = s64 ? sizeof(double) : sizeof(float);
-  std::vector<void*> U(j->n_lags);
-  for (int t = 0; t < j->n_lags; ++t) U[t] = carve.take<char>(esz * j->l * j->lags[t] * j->k);
-  char* S = carve.take<char>(esz * j->n_lags * j->k);
-  float* Ydev = j->y_on_host ? carve.take<float>((size_t)j->l * j->N) : nullptr;
-  if (!R || !S || !status || (j->y_on_host && !Ydev)) {
+  c.esz = s64 ? sizeof(double) : sizeof(float);
+  c.U.assign(j->n_lags, nullptr);
+  for (int t = 0; t < j->n_lags; ++t) c.U[t] = carve.take<char>(c.esz * j->l * j->lags[t] * j->k);
+  c.S = carve.take<char>(c.esz * j->n_lags * j->k);
+  c.Ydev = j->y_on_host ? carve.take<float>((size_t)j->l * j->N) : nullptr;
+  if (!c.R || !c.S || !c.status || (j->y_on_host && !c.Ydev)) {
     set_error("solve: job buffers too small");
     return SSI_E_NOMEM;
   }
+  return SSI_OK;
+}
+
+}  // namespace
+
+ssi_status run_job(ssi_ctx* ctx, const ssi_job_desc* j, const JobPlan& p, JobBuffers& B,
+                   ssi_pole* poles, float* phi, double* S_out, cudaStream_t stream,
+                   RealizePrep** defer) {
+  JobCarve c;
+  SSI_TRY(carve_job(j, p, B, c));
+  int* status = c.status;
+  double* R = c.R;
+  const bool s64 = j->small == SSI_SMALL_FP64;
+  const size_t esz = c.esz;
+  std::vector<void*>& U = c.U;
+  char* S = c.S;
   B.status = status;
   const float* Y = j->Y;
   if (j->y_on_host) {
-    SSI_CUDA(cudaMemcpyAsync(Ydev, j->Y, sizeof(float) * (size_t)j->l * j->N, cudaMemcpyHostToDevice,
-                             stream));
-    Y = Ydev;
+    SSI_CUDA(cudaMemcpyAsync(c.Ydev, j->Y, sizeof(float) * (size_t)j->l * j->N,
+                             cudaMemcpyHostToDevice, stream));
+    Y = c.Ydev;
   }
   if (!B.status_cleared) {
     SSI_CUDA(cudaMemsetAsync(status, 0, 64 * sizeof(int), stream));
@@ -152,6 +178,7 @@ ssi_status run_job(ssi_ctx* ctx, const ssi_job_desc* j, const JobPlan& p, JobBuf
   }
   std::vector<int> lags(j->lags, j->lags + j->n_lags), orders(j->orders, j->orders + j->n_orders);
   if (s64) {
+    SSI_CHECK(!defer, "solve: deferred realisations need FP32 small problems");
     std::vector<const double*> Ud(j->n_lags);
     for (int t = 0; t < j->n_lags; ++t) Ud[t] = static_cast<const double*>(U[t]);
     SSI_TRY(realize64_ws(ctx, B.ws, j->n_lags, lags.data(), j->l, j->k, Ud.data(), orders.data(),
@@ -160,16 +187,26 @@ ssi_status run_job(ssi_ctx* ctx, const ssi_job_desc* j, const JobPlan& p, JobBuf
     std::vector<const float*> Uc(j->n_lags);
     for (int t = 0; t < j->n_lags; ++t) Uc[t] = static_cast<const float*>(U[t]);
     SSI_TRY(realize_ws(ctx, B.ws, p.rz, lags.data(), Uc.data(), orders.data(), 1.0 / j->fs, poles,
-                       phi, status, stream));
+                       phi, status, stream, defer));
+    if (defer) return SSI_OK;
   }
+  return finish_job(ctx, j, p, B, poles, phi, S_out, stream);
+}
+
+ssi_status finish_job(ssi_ctx* ctx, const ssi_job_desc* j, const JobPlan& p, JobBuffers& B,
+                      ssi_pole* poles, float* phi, double* S_out, cudaStream_t stream) {
+  JobCarve c;
+  SSI_TRY(carve_job(j, p, B, c));
+  std::vector<int> orders(j->orders, j->orders + j->n_orders);
   SSI_TRY(stabilize_ws(ctx, B.ws, j->n_lags, j->n_orders, orders.data(), j->l, poles, phi, &j->stab,
                        stream));
   if (S_out) {
-    if (s64)
-      SSI_CUDA(cudaMemcpyAsync(S_out, S, sizeof(double) * (size_t)j->n_lags * j->k,
+    if (j->small == SSI_SMALL_FP64)
+      SSI_CUDA(cudaMemcpyAsync(S_out, c.S, sizeof(double) * (size_t)j->n_lags * j->k,
                                cudaMemcpyDeviceToDevice, stream));
     else
-      SSI_TRY(convert_f2d(reinterpret_cast<const float*>(S), (long long)j->n_lags * j->k, S_out, stream));
+      SSI_TRY(convert_f2d(reinterpret_cast<const float*>(c.S), (long long)j->n_lags * j->k, S_out,
+                          stream));
   }
   return SSI_OK;
 }
@@ -204,6 +241,19 @@ void buffers_free(ssi_ctx* ctx, JobBuffers& B) {
   B = JobBuffers{};
 }
 
+// State of ssi_solve_batch kept in the context between calls: one set of job buffers per
+// job of the largest batch so far, the streams the jobs' front stages run on, and the
+// device table of the batched eig launches.
+constexpr int BATCH_STREAMS = 4;
+struct BatchState {
+  std::vector<JobBuffers*> bufs;
+  cudaStream_t stream[BATCH_STREAMS] = {};
+  cudaEvent_t fork = nullptr;
+  cudaEvent_t join[BATCH_STREAMS] = {};
+  void* table = nullptr;
+  size_t table_cap = 0;
+};
+
 JobBuffers& ctx_solve_buffers(ssi_ctx* ctx) {
   if (!ctx->solve) ctx->solve = new JobBuffers();
   return *ctx->solve;
@@ -214,6 +264,23 @@ void solve_buffers_destroy(ssi_ctx* ctx) {
     buffers_free(ctx, *ctx->solve);
     delete ctx->solve;
     ctx->solve = nullptr;
+  }
+  if (BatchState* bs = ctx->batch) {
+    for (JobBuffers* b : bs->bufs) {
+      buffers_free(ctx, *b);
+      delete b;
+    }
+    for (int a = 0; a < BATCH_STREAMS; ++a) {
+      if (bs->stream[a]) {
+        cudaStreamSynchronize(bs->stream[a]);
+        cudaStreamDestroy(bs->stream[a]);
+      }
+      if (bs->join[a]) cudaEventDestroy(bs->join[a]);
+    }
+    if (bs->fork) cudaEventDestroy(bs->fork);
+    if (bs->table) ctx_free(ctx, bs->table, bs->table_cap);
+    delete bs;
+    ctx->batch = nullptr;
   }
 }
 
@@ -254,3 +321,70 @@ extern "C" ssi_status ssi_sync_status(ssi_ctx* ctx, void* stream) {
   if (B.status) return check_dev_status(B.status, s);
   return SSI_OK;
 }
+
+extern "C" ssi_status ssi_solve_batch(ssi_ctx* ctx, int n_jobs, const ssi_job_desc* jobs,
+                                      ssi_pole* const* poles, float* const* phi,
+                                      double* const* S_out, void* stream) {
+  SSI_CHECK(ctx && jobs && poles && phi, "ssi_solve_batch: null pointer");
+  SSI_CHECK(n_jobs >= 1 && n_jobs <= SSI_BATCH_MAX, "ssi_solve_batch: 1 <= n_jobs <= %d",
+            SSI_BATCH_MAX);
+  for (int i = 0; i < n_jobs; ++i) {
+    SSI_TRY(validate_job(&jobs[i]));
+    SSI_CHECK(poles[i] && phi[i], "ssi_solve_batch: null output of job %d", i);
+    SSI_CHECK(jobs[i].small == SSI_SMALL_FP32,
+              "ssi_solve_batch: job %d has FP64 small problems (the batched eig is FP32)", i);
+  }
+  SSI_CUDA(cudaSetDevice(ctx->device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (!ctx->batch) ctx->batch = new BatchState();
+  BatchState& bs = *ctx->batch;
+  if (!bs.fork) {
+    SSI_CUDA(cudaEventCreateWithFlags(&bs.fork, cudaEventDisableTiming));
+    for (int a = 0; a < BATCH_STREAMS; ++a) {
+      SSI_CUDA(cudaStreamCreateWithFlags(&bs.stream[a], cudaStreamNonBlocking));
+      SSI_CUDA(cudaEventCreateWithFlags(&bs.join[a], cudaEventDisableTiming));
+    }
+  }
+  while ((int)bs.bufs.size() < n_jobs) bs.bufs.push_back(new JobBuffers());
+  std::vector<JobPlan> plans(n_jobs);
+  for (int i = 0; i < n_jobs; ++i) {
+    plans[i] = plan_job(&jobs[i], ctx);
+    SSI_TRY(buffers_reserve(ctx, *bs.bufs[i], plans[i], s));
+  }
+  // each job's covariances, RSVD and factorisations on one of the batch streams (jobs i,
+  // i + 4, ... one after another), forked from and joined back to the caller's stream
+  const int n_str = std::min(n_jobs, BATCH_STREAMS);
+  SSI_CUDA(cudaEventRecord(bs.fork, s));
+  for (int a = 0; a < n_str; ++a) SSI_CUDA(cudaStreamWaitEvent(bs.stream[a], bs.fork, 0));
+  std::vector<RealizePrep*> preps(n_jobs, nullptr);
+  ssi_status st = SSI_OK;
+  for (int i = 0; i < n_jobs && st == SSI_OK; ++i)
+    st = run_job(ctx, &jobs[i], plans[i], *bs.bufs[i], poles[i], phi[i],
+                 S_out ? S_out[i] : nullptr, bs.stream[i % n_str], &preps[i]);
+  for (int a = 0; a < n_str; ++a) {
+    cudaEventRecord(bs.join[a], bs.stream[a]);
+    cudaStreamWaitEvent(s, bs.join[a], 0);
+  }
+  // one launch of each eig kernel over every job's realisations, then each job's stability
+  if (st == SSI_OK) {
+    const size_t need = realize_batch_table_bytes(preps.data(), n_jobs);
+    if (bs.table_cap < need) {
+      if (bs.table) {
+        cudaStreamSynchronize(s);
+        ctx_free(ctx, bs.table, bs.table_cap);
+        bs.table = nullptr;
+        bs.table_cap = 0;
+      }
+      st = ctx_alloc(ctx, &bs.table, need);
+      if (st == SSI_OK) bs.table_cap = need;
+    }
+  }
+  if (st == SSI_OK) st = realize_batch_launch(ctx, preps.data(), n_jobs, bs.table, bs.table_cap, s);
+  for (int i = 0; i < n_jobs && st == SSI_OK; ++i)
+    st = finish_job(ctx, &jobs[i], plans[i], *bs.bufs[i], poles[i], phi[i],
+                    S_out ? S_out[i] : nullptr, s);
+  for (RealizePrep* r : preps)
+    if (r) realize_prep_free(r);
+  return st;
+}
+

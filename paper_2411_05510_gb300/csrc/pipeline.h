@@ -39,8 +39,14 @@ JobPlan plan_job(const ssi_job_desc* j, ssi_ctx* ctx, const std::array<int, 4>* 
 std::string job_shape_key(const ssi_job_desc* j);
 ssi_status buffers_reserve(ssi_ctx* ctx, JobBuffers& B, const JobPlan& p, cudaStream_t stream);
 void buffers_free(ssi_ctx* ctx, JobBuffers& B);
+// defer (FP32 small problems only): stop after the realisations' factorisations and
+// return their pending eig launches in *defer; finish_job then runs what follows them
+// (stability, singular values out) once the eig launches are made
 ssi_status run_job(ssi_ctx* ctx, const ssi_job_desc* j, const JobPlan& p, JobBuffers& B,
-                   ssi_pole* poles, float* phi, double* S_out, cudaStream_t stream);
+                   ssi_pole* poles, float* phi, double* S_out, cudaStream_t stream,
+                   RealizePrep** defer = nullptr);
+ssi_status finish_job(ssi_ctx* ctx, const ssi_job_desc* j, const JobPlan& p, JobBuffers& B,
+                      ssi_pole* poles, float* phi, double* S_out, cudaStream_t stream);
 JobBuffers& ctx_solve_buffers(ssi_ctx* ctx);
 
 }  // namespace ssi

@@ -20,7 +20,9 @@
 //                 by back substitution on the quasi-triangular factor, back
 //                 transformation through the logged reflectors, Phi = U[:l,:n] Psi~,
 //                 pole parameters, MPC and MPD.  Largest orders are scheduled first.
+#include <algorithm>
 #include <cfloat>
+#include <cstring>
 #include <vector>
 
 #include "blackwell.cuh"
@@ -395,15 +397,27 @@ __device__ __forceinline__ void hess_update(float* A, int ld, int n, int j, int 
 
 // BIG: orders above SMEM_N_MAX, A in the realisation's global scratch (a separate
 // instantiation, so that the shared-memory kernel of the smaller orders is unchanged).
-// Work items count from item_base: largest orders first.
+// Work items count from item_base: largest orders first.  The parameters of the
+// realisation(s) are in device memory: one block P[0] when `items` is null (the CTA's item
+// is its index), or one block per job of a batch, the CTA's (job, order index, lag) then
+// read from `items`.
 template <bool BIG>
 __global__ void __launch_bounds__(EIG_THREADS, 1)
-    k_eig(EigParams p, int item_base) {
+    k_eig(const EigParams* __restrict__ P, const int4* __restrict__ items, int item_base) {
   extern __shared__ float smem[];
-  // work item: largest orders first
-  const int item = blockIdx.x + item_base;
-  const int mi = p.n_orders - 1 - (item / p.lt.n_lags);
-  const int t = item % p.lt.n_lags;
+  int job = 0, mi, t;
+  if (items) {
+    const int4 it = items[blockIdx.x + item_base];
+    job = it.x;
+    mi = it.y;
+    t = it.z;
+  } else {
+    // work item: largest orders first
+    const int item = blockIdx.x + item_base;
+    mi = P[0].n_orders - 1 - (item / P[0].lt.n_lags);
+    t = item % P[0].lt.n_lags;
+  }
+  const EigParams& p = P[job];
   const int n = p.orders[mi];
   const int k = p.lt.k, l = p.lt.l;
   const int tid = threadIdx.x, nth = blockDim.x;
@@ -1248,18 +1262,28 @@ constexpr int ZRING = 4;            // window records in flight
 constexpr int VRING = 4;            // Hessenberg reflectors in flight
 
 __global__ void __launch_bounds__(VEC_THREADS)
-    k_eig_vectors(EigParams p) {
+    k_eig_vectors(const EigParams* __restrict__ P, const int4* __restrict__ items) {
   extern __shared__ float vsm[];
-  // block -> (lag, order, column block), largest orders first
-  const int per_lag = p.vec_blocks_per_lag;
-  const int t = blockIdx.x % p.lt.n_lags;
-  int q = blockIdx.x / p.lt.n_lags;   // block index within the lag, largest orders first
-  int mi = p.n_orders - 1;
-  while (mi > 0 && q >= p.vec_blocks[mi]) {
-    q -= p.vec_blocks[mi];
-    --mi;
+  int job = 0, t, q, mi;
+  if (items) {
+    // a batch: (job, order index, lag, column block) from the table
+    const int4 it = items[blockIdx.x];
+    job = it.x;
+    mi = it.y;
+    t = it.z;
+    q = it.w;
+  } else {
+    // block -> (lag, order, column block), largest orders first
+    const EigParams& p0 = P[0];
+    t = blockIdx.x % p0.lt.n_lags;
+    q = blockIdx.x / p0.lt.n_lags;   // block index within the lag, largest orders first
+    mi = p0.n_orders - 1;
+    while (mi > 0 && q >= p0.vec_blocks[mi]) {
+      q -= p0.vec_blocks[mi];
+      --mi;
+    }
   }
-  (void)per_lag;
+  const EigParams& p = P[job];
   const int n = p.orders[mi];
   const int k = p.lt.k, l = p.lt.l;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nwarps = VEC_THREADS / 32;
@@ -1463,6 +1487,14 @@ ssi_status lag_factor64_launch(const double* GH, int k, int n_lags, double* RM, 
   return SSI_OK;
 }
 
+// a prepared realisation: the parameter block of its eigen-decompositions (host copy and
+// device copy in the job's scratch) and its largest order
+struct RealizePrep {
+  EigParams ep;
+  EigParams* dev;
+  int max_order;
+};
+
 RealizePlan realize_plan(int n_lags, const int* lags, int l, int k, const int* orders, int n_orders) {
   RealizePlan r{};
   r.n_lags = n_lags;
@@ -1486,13 +1518,14 @@ RealizePlan realize_plan(int n_lags, const int* lags, int l, int k, const int* o
   w.add<float>((size_t)n_lags * 2 * k * k);                          // Rinv | M
   w.add<float>((size_t)n_lags * work);                               // eig scratch
   if (k > FACTOR_SMEM_K) w.add<float>((size_t)n_lags * ((size_t)k * (k + 1) + k));  // factors
+  w.add<EigParams>(1);                                               // eig launch parameters
   r.ws_bytes = w.bytes;
   return r;
 }
 
 ssi_status realize_ws(ssi_ctx* ctx, Workspace& ws, const RealizePlan& r, const int* lags,
                       const float* const* U, const int* orders, double dt, ssi_pole* poles,
-                      float* phi, int* dev_status, cudaStream_t stream) {
+                      float* phi, int* dev_status, cudaStream_t stream, RealizePrep** defer) {
   ws.reset();
   SSI_CHECK(r.n_lags <= MAX_LAGS, "realize: at most %d lags per call", MAX_LAGS);
   SSI_CHECK(r.n_orders <= 512, "realize: at most 512 orders per call");
@@ -1519,15 +1552,16 @@ ssi_status realize_ws(ssi_ctx* ctx, Workspace& ws, const RealizePlan& r, const i
     work += eig_work_floats(orders[m], r.l) + 64;
   }
   float* eigw = ws.take<float>((size_t)r.n_lags * work);
+  EigParams* ep_dev = ws.take<EigParams>(1);
   float* Rg = (k > FACTOR_SMEM_K) ? ws.take<float>((size_t)r.n_lags * ((size_t)k * (k + 1) + k))
                                   : nullptr;
-  if (!partial || !GH || !RM || !eigw || (k > FACTOR_SMEM_K && !Rg)) {
+  if (!partial || !GH || !RM || !eigw || !ep_dev || (k > FACTOR_SMEM_K && !Rg)) {
     set_error("realize: workspace too small");
     return SSI_E_NOMEM;
   }
   const int tiles = (int)ceil_div(k, 64);
   dim3 g1((unsigned)(tiles * tiles), (unsigned)n_chunks, (unsigned)(2 * r.n_lags));
-  count_launches(ctx, 5);
+  count_launches(ctx, 3);   // Gram, its reduction, the factorisation (the eig launches count their own)
   {
   ProfScope ps(ctx, ST_GRAM, stream);
   k_gram_gh<<<g1, 256, 0, stream>>>(lt, n_chunks, partial);
@@ -1559,48 +1593,120 @@ ssi_status realize_ws(ssi_ctx* ctx, Workspace& ws, const RealizePlan& r, const i
   ep.poles = poles;
   ep.phi = phi;
   ep.status = dev_status;
-  // the CTAs' layouts differ by order; each launch reserves its largest.  Orders above
-  // SMEM_N_MAX (the largest of the diagram) run in their own launch, first.
-  int n_big = 0, esmem_s = 0, esmem_b = 0;
-  for (int m = 0; m < r.n_orders; ++m) {
-    if (orders[m] > SMEM_N_MAX) {
-      ++n_big;
-      esmem_b = std::max(esmem_b, eig_smem_floats(orders[m]));
-    } else {
-      esmem_s = std::max(esmem_s, eig_smem_floats(orders[m]));
-    }
-  }
-  SSI_CUDA(cudaFuncSetAttribute(k_eig<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(esmem_s * sizeof(float))));
-  SSI_CUDA(cudaFuncSetAttribute(k_eig<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(std::max(esmem_b, 1) * sizeof(float))));
   int vec_total = 0;
   for (int m = 0; m < r.n_orders; ++m) {
     ep.vec_blocks[m] = (int)ceil_div(orders[m], VEC_COLS);
     vec_total += ep.vec_blocks[m];
   }
   ep.vec_blocks_per_lag = vec_total;
+  // the parameter block in device memory, behind the factorisations on the stream (a
+  // pageable source is staged before the call returns)
+  SSI_CUDA(cudaMemcpyAsync(ep_dev, &ep, sizeof(EigParams), cudaMemcpyHostToDevice, stream));
+  RealizePrep* prep = new RealizePrep{ep, ep_dev, r.max_order};
+  if (defer) {
+    *defer = prep;
+    return SSI_OK;
+  }
+  const ssi_status st = realize_batch_launch(ctx, &prep, 1, nullptr, 0, stream);
+  delete prep;
+  return st;
+}
+
+// Launches of the eigen-decompositions.  The CTAs' layouts differ by order, so each launch
+// reserves its largest; orders above SMEM_N_MAX run in their own launch, first.  One
+// realisation (n == 1) indexes its items by CTA.  A batch lists every job's (job, order
+// index, lag[, column block]) in `table` (device memory of realize_batch_table_bytes),
+// largest orders first across the jobs, after the jobs' parameter blocks.
+ssi_status realize_batch_launch(ssi_ctx* ctx, RealizePrep* const* preps, int n, void* table,
+                                size_t table_cap, cudaStream_t stream) {
+  SSI_CHECK(n >= 1, "realize: no realisation to launch");
+  int esmem_s = 0, esmem_b = 0, max_order = 0;
+  // items as (job, order index, lag, order); vector blocks as (job, order index, lag,
+  // column block), with their orders alongside for the sort
+  std::vector<int4> small, big, vec;
+  std::vector<int> vec_order;
+  for (int j = 0; j < n; ++j) {
+    const EigParams& ep = preps[j]->ep;
+    max_order = std::max(max_order, preps[j]->max_order);
+    for (int m = 0; m < ep.n_orders; ++m) {
+      const int o = ep.orders[m];
+      if (o > SMEM_N_MAX) esmem_b = std::max(esmem_b, eig_smem_floats(o));
+      else esmem_s = std::max(esmem_s, eig_smem_floats(o));
+      for (int t = 0; t < ep.lt.n_lags; ++t) {
+        (o > SMEM_N_MAX ? big : small).push_back(make_int4(j, m, t, o));
+        for (int q = 0; q < ep.vec_blocks[m]; ++q) {
+          vec.push_back(make_int4(j, m, t, q));
+          vec_order.push_back(o);
+        }
+      }
+    }
+  }
+  const int n_small = (int)small.size(), n_big = (int)big.size(), n_vec = (int)vec.size();
+  const EigParams* P = preps[0]->dev;
+  const int4 *t_eig = nullptr, *t_vec = nullptr;
+  if (n > 1) {
+    // largest orders first across the jobs (stable among equal orders)
+    auto by_order = [](const int4& a, const int4& b) { return a.w > b.w; };
+    std::stable_sort(small.begin(), small.end(), by_order);
+    std::stable_sort(big.begin(), big.end(), by_order);
+    std::vector<int> idx(vec.size());
+    for (size_t e = 0; e < idx.size(); ++e) idx[e] = (int)e;
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return vec_order[a] > vec_order[b]; });
+    // the batch's parameter blocks side by side, then the eig items (big, then small: one
+    // table serves both launches) and the vector blocks
+    const size_t need = realize_batch_table_bytes(preps, n);
+    SSI_CHECK(table && table_cap >= need, "realize: batch table too small");
+    std::vector<char> host(need);
+    size_t off = 0;
+    for (int j = 0; j < n; ++j, off += sizeof(EigParams))
+      std::memcpy(host.data() + off, &preps[j]->ep, sizeof(EigParams));
+    char* base = static_cast<char*>(table);
+    P = reinterpret_cast<const EigParams*>(base);
+    t_eig = reinterpret_cast<const int4*>(base + off);
+    for (const int4& v : big) { std::memcpy(host.data() + off, &v, sizeof(int4)); off += sizeof(int4); }
+    for (const int4& v : small) { std::memcpy(host.data() + off, &v, sizeof(int4)); off += sizeof(int4); }
+    t_vec = reinterpret_cast<const int4*>(base + off);
+    for (int e : idx) { std::memcpy(host.data() + off, &vec[e], sizeof(int4)); off += sizeof(int4); }
+    SSI_CUDA(cudaMemcpyAsync(table, host.data(), off, cudaMemcpyHostToDevice, stream));
+  }
+  SSI_CUDA(cudaFuncSetAttribute(k_eig<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(std::max(esmem_s, 1) * sizeof(float))));
+  SSI_CUDA(cudaFuncSetAttribute(k_eig<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(std::max(esmem_b, 1) * sizeof(float))));
   const size_t vsmem =
-      ((((size_t)r.max_order * XLD + 3) & ~size_t(3)) + ZRING * ZREC + VRING * N_MAX) * sizeof(float);
+      ((((size_t)max_order * XLD + 3) & ~size_t(3)) + ZRING * ZREC + VRING * N_MAX) * sizeof(float);
   SSI_CUDA(cudaFuncSetAttribute(k_eig_vectors, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vsmem));
   {
     ProfScope ps_eig(ctx, ST_EIG, stream);
     if (n_big > 0) {
       count_launches(ctx, 1);
-      k_eig<true><<<r.n_lags * n_big, EIG_THREADS, (size_t)esmem_b * sizeof(float), stream>>>(ep, 0);
+      k_eig<true><<<n_big, EIG_THREADS, (size_t)esmem_b * sizeof(float), stream>>>(P, t_eig, 0);
       SSI_CUDA(cudaGetLastError());
     }
-    if (n_big < r.n_orders) {
-      k_eig<false><<<r.n_lags * (r.n_orders - n_big), EIG_THREADS, (size_t)esmem_s * sizeof(float),
-                     stream>>>(ep, r.n_lags * n_big);
+    if (n_small > 0) {
+      count_launches(ctx, 1);
+      k_eig<false><<<n_small, EIG_THREADS, (size_t)esmem_s * sizeof(float), stream>>>(P, t_eig,
+                                                                                      n_big);
       SSI_CUDA(cudaGetLastError());
     }
   }
   ProfScope ps_vec(ctx, ST_EIG_VEC, stream);
-  k_eig_vectors<<<r.n_lags * vec_total, VEC_THREADS, vsmem, stream>>>(ep);
+  count_launches(ctx, 1);
+  k_eig_vectors<<<n_vec, VEC_THREADS, vsmem, stream>>>(P, t_vec);
   SSI_CUDA(cudaGetLastError());
   return SSI_OK;
 }
+
+size_t realize_batch_table_bytes(RealizePrep* const* preps, int n) {
+  size_t items = 0;
+  for (int j = 0; j < n; ++j) {
+    const EigParams& ep = preps[j]->ep;
+    for (int m = 0; m < ep.n_orders; ++m) items += (size_t)ep.lt.n_lags * (1 + ep.vec_blocks[m]);
+  }
+  return (size_t)n * sizeof(EigParams) + items * sizeof(int4);
+}
+
+void realize_prep_free(RealizePrep* p) { delete p; }
 
 }  // namespace ssi
 
