@@ -9,7 +9,7 @@ realisations of orders 2..200 step 2, hard and soft stability criteria.
 Lines printed (one JSON line on rank 0):
   value      solves/s with the record resident in HBM: CUDA events around K solves dealt
              round robin to --inflight independent solvers (own context, record copy and
-             stream each), so that one solve's latency-bound stages (the single-CTA Jacobi
+             stream each), so that one solve's latency-bound stages (the cluster Jacobi
              SVD, the tail of the per-order eigenproblems) overlap another's GEMMs
   serial     the same with one solve in flight (unloaded latency, per-stage times)
   e2e        the same through ssi_submit / ssi_poll with the record in pinned host memory
@@ -22,6 +22,8 @@ Lines printed (one JSON line on rank 0):
   small_fp64 the same pipeline with the K x K SVD, the least squares for A and eig(A) in
              FP64 (the split-BF16 GEMMs unchanged)
   diagram_3d the 3D stabilization diagram (lags 20..100 step 10) of the same record
+  batch      eight mixed-shape jobs in one ssi_solve_batch call (their eigen-decompositions
+             in one launch) against one ssi_solve after another
   serving_mix  p50/p99 latency of a heterogeneous job stream through the serving API
   cpu_baseline  one complete FP64 oracle solve of the workload on the host cores, timed
              (oracle/reference_solve.py, which also stores its result)
