@@ -467,6 +467,62 @@ __global__ void k_form_u(const float* __restrict__ Q, int ldq, const TU* __restr
   }
 }
 
+// The FP32 form of k_form_u as a tiled product: a CTA computes 64 rows x 64 columns of U
+// from 32-deep slabs of Q and Ut staged in shared memory, 4 x 4 outputs per thread.  Each
+// output is still one FMA chain over a = 0, 1, ..., K - 1 in order, so the result is the
+// same as the one-output-per-thread form; the slabs make every Q and Ut element serve 64
+// outputs instead of one.
+template <typename TO>
+__global__ void __launch_bounds__(256)
+    k_form_u_tiled(const float* __restrict__ Q, int ldq, const float* __restrict__ Ut, int K, int k,
+                   int l, int l_pad, int i, TO* __restrict__ U) {
+  constexpr int TA = 32;
+  __shared__ __align__(16) float As[TA][64 + 4];   // As[a][r] = Q[row of r0 + r][a0 + a]
+  __shared__ __align__(16) float Bs[TA][64 + 4];   // Bs[a][c] = Ut[a0 + a][j0 + c]
+  const int L = l * i;
+  const int j0 = blockIdx.x * 64, r0 = blockIdx.y * 64;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  float acc[4][4] = {};
+  for (int a0 = 0; a0 < K; a0 += TA) {
+    for (int e = tid; e < 64 * TA; e += 256) {
+      const int r = e / TA, a = e % TA;
+      const int rr = r0 + r;
+      float v = 0.f;
+      if (rr < L && a0 + a < K) {
+        const int b = rr / l, c = rr % l;
+        v = Q[(size_t)(b * l_pad + c) * ldq + a0 + a];
+      }
+      As[a][r] = v;
+    }
+    for (int e = tid; e < 64 * TA; e += 256) {
+      const int a = e / 64, c = e % 64;
+      Bs[a][c] = (a0 + a < K && j0 + c < k) ? Ut[(size_t)(a0 + a) * K + j0 + c] : 0.f;
+    }
+    __syncthreads();
+    const int na = min(TA, K - a0);
+    for (int a = 0; a < na; ++a) {
+      const float4 qa = *reinterpret_cast<const float4*>(&As[a][ty * 4]);
+      const float4 ub = *reinterpret_cast<const float4*>(&Bs[a][tx * 4]);
+      const float q4[4] = {qa.x, qa.y, qa.z, qa.w}, u4[4] = {ub.x, ub.y, ub.z, ub.w};
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(q4[x], u4[y], acc[x][y]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int x = 0; x < 4; ++x) {
+    const int rr = r0 + ty * 4 + x;
+    if (rr >= L) continue;
+#pragma unroll
+    for (int y = 0; y < 4; ++y) {
+      const int j = j0 + tx * 4 + y;
+      if (j < k) U[(size_t)rr * k + j] = (TO)acc[x][y];
+    }
+  }
+}
+
 template <typename TI, typename TO>
 __global__ void k_convert(const TI* __restrict__ x, long long n, TO* __restrict__ y) {
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
@@ -744,19 +800,20 @@ ssi_status toeplitz_rsvd_ws(ssi_ctx* ctx, Workspace& ws, const RsvdPlan& r, cons
   }
   ProfScope ps_u(ctx, ST_OTHER, stream);
   const int gu = grid_1d((long long)r.L * r.k, 256, nsm), gs = grid_1d(r.k, 256, nsm);
+  const dim3 gt((unsigned)ceil_div(r.k, 64), (unsigned)ceil_div(r.L, 64));
   if (small64) {
     k_form_u<double, double><<<gu, 256, 0, stream>>>(Qs, r.Kp, Ut64, r.K, r.k, r.l, r.l_pad, r.i,
                                                      static_cast<double*>(U));
     SSI_CUDA(cudaGetLastError());
     SSI_CUDA(cudaMemcpyAsync(S, sig64, sizeof(double) * r.k, cudaMemcpyDeviceToDevice, stream));
   } else if (out64) {
-    k_form_u<float, double><<<gu, 256, 0, stream>>>(Qs, r.Kp, Ut, r.K, r.k, r.l, r.l_pad, r.i,
-                                                    static_cast<double*>(U));
+    k_form_u_tiled<double><<<gt, 256, 0, stream>>>(Qs, r.Kp, Ut, r.K, r.k, r.l, r.l_pad, r.i,
+                                                   static_cast<double*>(U));
     SSI_CUDA(cudaGetLastError());
     k_convert<float, double><<<gs, 256, 0, stream>>>(sig, r.k, static_cast<double*>(S));
   } else {
-    k_form_u<float, float><<<gu, 256, 0, stream>>>(Qs, r.Kp, Ut, r.K, r.k, r.l, r.l_pad, r.i,
-                                                   static_cast<float*>(U));
+    k_form_u_tiled<float><<<gt, 256, 0, stream>>>(Qs, r.Kp, Ut, r.K, r.k, r.l, r.l_pad, r.i,
+                                                  static_cast<float*>(U));
     SSI_CUDA(cudaGetLastError());
     SSI_CUDA(cudaMemcpyAsync(S, sig, sizeof(float) * r.k, cudaMemcpyDeviceToDevice, stream));
   }
