@@ -933,6 +933,10 @@ def main():
             "gpu_launches": launches,
             "autotune": tuning,
             "modes_found": f"{found}/{len(f_true)}",
+            # the same rate per realisation (one eig(A_n) per lag and order) and per pole
+            # slot (n/2 per realisation of order n)
+            "realisations_per_s": value * len(w["lags"]) * len(w["orders"]),
+            "pole_slots_per_s": value * len(w["lags"]) * sum(o // 2 for o in w["orders"]),
         }
         if not args.no_clocks:
             out["clocks"] = clocks.summary()
