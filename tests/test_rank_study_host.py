@@ -63,3 +63,39 @@ def test_damping_differences_report_matched_modes():
     cand = _modes([1.0, 2.0], [0.011, 0.020], ph)
     d = RS.damping_differences(ref, cand, np.array([1.0, 2.0]))
     assert np.allclose(d, [0.001 / 0.011, 0.0])
+
+
+def test_minimum_rank_search_bookkeeping(monkeypatch):
+    """The search over the grid with a stand-in identification: K = ceil(pct T / 100)
+    (at least the largest order), the first matching percentage is returned, the reference
+    is identified at K = T, and the trace records each step."""
+    ph = _shapes(2)
+    ref = _modes([1.0, 2.0], [0.01, 0.02], ph)
+    calls = []
+
+    def fake_identify(ctx, Y, fs, jb, orders, K, **kw):
+        calls.append(K)
+        if K >= 10 * jb:                 # the reference (full width)
+            return ref
+        xi = 0.0201 if K >= 300 else 0.03   # damping within 1 % from K = 300 on
+        return _modes([1.0, 2.0], [0.01, xi], ph)
+
+    monkeypatch.setattr(RS, "identify", fake_identify)
+
+    class _Y:
+        shape = (10, 1000)
+
+    kbar, r, trace = RS.minimum_rank(None, _Y(), 200.0, 100, list(range(10, 101, 2)),
+                                     RS.rank_grid(2.5, 50.0, 2.5), f_names=[1.0, 2.0])
+    assert r is ref and calls[0] == 1000
+    assert kbar == 30.0                          # ceil(30 % of 1000) = 300
+    assert [t[1] for t in trace] == [100, 100, 100, 100, 125, 150, 175, 200, 225, 250, 275, 300]
+    assert [t[2] for t in trace] == [False] * 11 + [True]
+    # an identification that matches only at full width: K reaching T stops the search
+    # there (the reference matches itself), before the grid's end
+    monkeypatch.setattr(RS, "identify", lambda ctx, Y, fs, jb, orders, K, **kw:
+                        ref if K >= 10 * jb else _modes([1.0, 2.0], [0.01, 0.03], ph))
+    kbar, _, trace = RS.minimum_rank(None, _Y(), 200.0, 100, [10, 20], [50.0, 100.0, 150.0],
+                                     f_names=[1.0, 2.0])
+    assert kbar == 100.0 and len(trace) == 2
+    assert trace[-1][1] == 1000 and trace[-1][2]
